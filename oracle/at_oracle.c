@@ -1,0 +1,601 @@
+/*
+ * at_oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * What it computes, following Kumari, Aditya & Donzis (arXiv 2204.01133):
+ *
+ *  - The domain is periodic and split into P processing elements (PEs) of B
+ *    points (Sec. 2.1, Fig. 1).  Every stencil tap that leaves its PE is a
+ *    "buffer point" whose value may be delayed.
+ *  - A delay k in {0..k_max} is drawn for every PE boundary (Sec. 2.1, Sec. 5
+ *    "delays are introduced using a random number generator at each
+ *    processor boundary").  The generator is Philox4x32-10 (Salmon et al.,
+ *    SC'11), used as a counter-based hash of (step, PE, stage|side<<8,
+ *    instance) keyed by the seed; word 0 is compared with the cumulative
+ *    probability thresholds floor(2^32 * CDF(i)).
+ *  - AT schemes (Eq. geDer, Eq. at1, Appendix A): the spatial stencil is the
+ *    standard central one; every buffer value u_m is replaced by the
+ *    combination sum_l w_l(k) u_m^{n-k-l}, l = 0..q, where w_l are the
+ *    Lagrange weights that extrapolate from the time levels n-k-l to n.
+ *    q = 1 reproduces Eq. at1 (second order), q = 2 reproduces Appendix A
+ *    (fourth order), q = 3 is the sixth-order member of the same family.
+ *    AS schemes (Eq. async-fde) use the plain delayed value u_m^{n-k}.
+ *  - AT-WENO5 (Sec. 3, Eqs. atRecon, idRec, beta2AT0-2; Appendix B): the
+ *    WENO5-JS reconstruction (candidates of Eq. atRecon at k = 0, ideal
+ *    weights {1/10, 3/5, 3/10}, smoothness indicators of Eq. betaS, weights of
+ *    Eq. omg) applied to buffer values extrapolated linearly (q = 1).
+ *  - Derived quantities (fluxes, velocity, temperature, ...) at buffer points
+ *    are computed from the stored state at each delayed level and then
+ *    combined across levels (the "on the fly" option of Sec. 6).
+ *  - Runge-Kutta in Butcher form (Eq. rk1).  Each stage argument
+ *    U^{n,(s)} = u^n + dt sum_{i<s} a_si K_i is kept for every level, and the
+ *    buffer points of stage s read U^{n-k-l,(s)}: the message of Sec. 2.3
+ *    carries all stages of a step, so stage s of an old level is available.
+ *  - Governing equations (Sec. 4, Eqs. ge, convEq) reduced to two species
+ *    (fuel -> product, equal molecular weights and heat capacities) with
+ *    constant transport and a one-step irreversible Arrhenius rate (Sec. 5.2
+ *    uses one-step chemistry for this purpose).  Reactive Euler for the
+ *    detonation (Sec. 5.6).
+ *
+ * Where the paper leaves a point open, the reading taken is stated at the
+ * code that depends on it.
+ */
+#include "at_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MAXD 8 /* most derived quantities per point */
+
+struct orc_ctx {
+    orc_problem pb;
+    int nvar, S, H, q, R, nder;
+    int64_t N, P, B;
+    double a[4][4], b[4];
+    double* u;     /* u^n          [nvar][N]          */
+    double* hist;  /* U^{m,(s)}    [R][S][nvar][N]    */
+    double* K;     /* K_s          [S][nvar][N]       */
+    uint64_t thr[16];
+    int64_t level;
+    int32_t* keff; /* delays in use  [S][P][2]        */
+    uint8_t* dlog; /* last step's    [S][P][2]        */
+};
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10, Salmon, Moraes, Dror & Shaw, SC'11, Sec. 3.2/4.2.    */
+/* ------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t p0 = (uint64_t)M0 * x0;
+        uint64_t p1 = (uint64_t)M1 * x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0;
+        x1 = y1;
+        x2 = y2;
+        x3 = y3;
+    }
+    out[0] = x0;
+    out[1] = x1;
+    out[2] = x2;
+    out[3] = x3;
+}
+
+/* Probabilities p_0..p_kmax (Sec. 2.1: sum p_k = 1) -> thresholds.
+ * Table entries are normalised by their sum (a table that does not sum to 1,
+ * like p = [0.3, 0.3, 0.3] of Table wenoLin, is read as proportional).
+ * Geometric: p_k proportional to r (1-r)^k on {0..kmax}. */
+void orc_thresholds(int k_max, int dist, const double* prob, uint64_t* thr)
+{
+    double w[16];
+    for (int i = 0; i <= k_max; ++i) {
+        if (dist == ORC_UNIFORM)
+            w[i] = 1.0;
+        else if (dist == ORC_TABLE)
+            w[i] = prob[i];
+        else {
+            double r = prob[0], t = r;
+            for (int j = 0; j < i; ++j) t *= (1.0 - r);
+            w[i] = t;
+        }
+    }
+    double total = 0.0;
+    for (int i = 0; i <= k_max; ++i) total += w[i];
+    double cum = 0.0;
+    for (int i = 0; i < k_max; ++i) {
+        cum += w[i];
+        double cdf = cum / total;
+        double t = floor(cdf * 4294967296.0);
+        if (t < 0.0) t = 0.0;
+        if (t > 4294967296.0) t = 4294967296.0;
+        thr[i] = (uint64_t)t;
+    }
+}
+
+int orc_draw(const orc_ctx* c, int64_t level, int stage, int64_t pe, int side)
+{
+    const orc_problem* pb = &c->pb;
+    uint32_t s_ctr = pb->per_stage ? (uint32_t)stage : 0u;
+    uint32_t ctr[4] = {(uint32_t)level, (uint32_t)pe, s_ctr | ((uint32_t)side << 8), pb->instance};
+    uint32_t key[2] = {(uint32_t)(pb->seed & 0xffffffffu), (uint32_t)(pb->seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    int k = 0;
+    for (int i = 0; i < pb->k_max; ++i)
+        if ((uint64_t)out[0] >= c->thr[i]) ++k;
+    return k;
+}
+
+/* Start-up clamp (the paper is silent): never read a level below 0.  A delay
+ * is never larger than k_max, the oldest level the history keeps. */
+static int clamp_k(const orc_ctx* c, int64_t level, int k)
+{
+    if (c->pb.mode == ORC_SYNC) return 0;
+    if (k > c->pb.k_max) k = c->pb.k_max;
+    if (k < 0) k = 0;
+    int qq = (c->pb.mode == ORC_AT) ? c->q : 0;
+    int64_t avail = level - qq;
+    if (avail < 0) avail = 0;
+    return (k < avail) ? k : (int)avail;
+}
+
+/* Lagrange weights that extrapolate values at times -k, -k-1, ..., -k-q to
+ * time 0:  w_l = prod_{m != l} (k+m) / (m-l).  Numerator and denominator are
+ * formed as integers first, so the weights are exact. */
+void orc_lagrange_weights(int q, int k, double* w)
+{
+    for (int l = 0; l <= q; ++l) {
+        long long num = 1, den = 1;
+        for (int m = 0; m <= q; ++m) {
+            if (m == l) continue;
+            num *= (long long)(k + m);
+            den *= (long long)(m - l);
+        }
+        w[l] = (double)num / (double)den;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Central stencils (textbook), numerators over a common denominator. */
+/* ------------------------------------------------------------------ */
+static const double D1_2[3] = {-1, 0, 1}, D1_2den = 2;
+static const double D2_2[3] = {1, -2, 1}, D2_2den = 1;
+static const double D1_4[5] = {1, -8, 0, 8, -1}, D1_4den = 12;
+static const double D2_4[5] = {-1, 16, -30, 16, -1}, D2_4den = 12;
+static const double D1_6[7] = {-1, 9, -45, 0, 45, -9, 1}, D1_6den = 60;
+static const double D2_6[7] = {2, -27, 270, -490, 270, -27, 2}, D2_6den = 180;
+
+static void central_tables(int order, const double** d1, double* d1den, const double** d2, double* d2den)
+{
+    if (order == 2) {
+        *d1 = D1_2; *d1den = D1_2den; *d2 = D2_2; *d2den = D2_2den;
+    } else if (order == 4) {
+        *d1 = D1_4; *d1den = D1_4den; *d2 = D2_4; *d2den = D2_4den;
+    } else {
+        *d1 = D1_6; *d1den = D1_6den; *d2 = D2_6; *d2den = D2_6den;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* WENO5-JS reconstruction at x_{j+1/2} from v = f_{j-2..j+2}.         */
+/* Candidates: Eq. atRecon at k = 0.  Ideal weights: Eq. idRec.        */
+/* Smoothness indicators: Eq. betaS.  Nonlinear weights: Eq. omg.      */
+/* ------------------------------------------------------------------ */
+double orc_weno5_js(const double v[5], double eps)
+{
+    double p0 = v[0] / 3.0 - 7.0 * v[1] / 6.0 + 11.0 * v[2] / 6.0;
+    double p1 = -v[1] / 6.0 + 5.0 * v[2] / 6.0 + v[3] / 3.0;
+    double p2 = v[2] / 3.0 + 5.0 * v[3] / 6.0 - v[4] / 6.0;
+    double b0 = (4.0 * v[0] * v[0] + (11.0 * v[2] - 19.0 * v[1]) * v[0] + 25.0 * v[1] * v[1]
+                 + 10.0 * v[2] * v[2] - 31.0 * v[1] * v[2]) / 3.0;
+    double b1 = (4.0 * v[1] * v[1] + (5.0 * v[3] - 13.0 * v[2]) * v[1] + 13.0 * v[2] * v[2]
+                 + 4.0 * v[3] * v[3] - 13.0 * v[2] * v[3]) / 3.0;
+    double b2 = (10.0 * v[2] * v[2] + (11.0 * v[4] - 31.0 * v[3]) * v[2] + 25.0 * v[3] * v[3]
+                 + 4.0 * v[4] * v[4] - 19.0 * v[3] * v[4]) / 3.0;
+    double a0 = 0.1 / ((eps + b0) * (eps + b0));
+    double a1 = 0.6 / ((eps + b1) * (eps + b1));
+    double a2 = 0.3 / ((eps + b2) * (eps + b2));
+    double s = a0 + a1 + a2;
+    return (a0 / s) * p0 + (a1 / s) * p1 + (a2 / s) * p2;
+}
+
+/* ------------------------------------------------------------------ */
+/* Physics: derived quantities of one state vector                     */
+/* ------------------------------------------------------------------ */
+static int nvar_of(int pde) { return (pde == ORC_RNS || pde == ORC_EULER) ? 4 : 1; }
+
+static double* field(const orc_ctx* c, int64_t level, int s)
+{
+    int64_t r = level % c->R;
+    if (r < 0) r += c->R;
+    return c->hist + ((size_t)r * c->S + s) * (size_t)c->nvar * c->N;
+}
+
+static void state_at(const orc_ctx* c, const double* f, int64_t m, double* Q)
+{
+    for (int v = 0; v < c->nvar; ++v) Q[v] = f[(size_t)v * c->N + m];
+}
+
+/* ADVDIFF: [u].  ADV_WENO: [c u, u].
+ * RNS (Eq. convEq with two species, R = 1, p = rho T):
+ *   [rho u, rho u^2 + p, u (rho E + p), rho u Y, u, u^2, T, Y]
+ * EULER: [rho u, rho u^2 + p, u (rho E + p), rho u Y, rho, rho u, rho E, rho Y] */
+static void derive(const orc_ctx* c, const double* Q, double* g)
+{
+    const double* pr = c->pb.prm;
+    switch (c->pb.pde) {
+    case ORC_ADVDIFF:
+        g[0] = Q[0];
+        break;
+    case ORC_ADV_WENO:
+        g[0] = pr[0] * Q[0];
+        g[1] = Q[0];
+        break;
+    case ORC_RNS: {
+        double gam = pr[0], qc = pr[6];
+        double rho = Q[0], u = Q[1] / rho;
+        double p = (gam - 1.0) * (Q[2] - 0.5 * Q[1] * u - qc * Q[3]);
+        g[0] = Q[1];
+        g[1] = Q[1] * u + p;
+        g[2] = u * (Q[2] + p);
+        g[3] = Q[3] * u;
+        g[4] = u;
+        g[5] = u * u;
+        g[6] = p / rho;
+        g[7] = Q[3] / rho;
+        break;
+    }
+    case ORC_EULER: {
+        double gam = pr[0], qc = pr[3];
+        double rho = Q[0], u = Q[1] / rho;
+        double p = (gam - 1.0) * (Q[2] - 0.5 * Q[1] * u - qc * Q[3]);
+        g[0] = Q[1];
+        g[1] = Q[1] * u + p;
+        g[2] = u * (Q[2] + p);
+        g[3] = Q[3] * u;
+        g[4] = Q[0];
+        g[5] = Q[1];
+        g[6] = Q[2];
+        g[7] = Q[3];
+        break;
+    }
+    }
+}
+
+/* largest characteristic speed |u| + c (local Lax-Friedrichs, Eq. Csplit) */
+static double wave_speed(const orc_ctx* c, const double* Q)
+{
+    const double* pr = c->pb.prm;
+    if (c->pb.pde == ORC_ADV_WENO) return fabs(pr[0]);
+    double gam = pr[0], qc = pr[3];
+    double rho = Q[0], u = Q[1] / rho;
+    double p = (gam - 1.0) * (Q[2] - 0.5 * Q[1] * u - qc * Q[3]);
+    return fabs(u) + sqrt(gam * p / rho);
+}
+
+/* ------------------------------------------------------------------ */
+/* Stencil taps as seen from PE p                                      */
+/* ------------------------------------------------------------------ */
+static int64_t wrap(const orc_ctx* c, int64_t m)
+{
+    m %= c->N;
+    if (m < 0) m += c->N;
+    return m;
+}
+
+/* derived quantities at global position m (unwrapped), as PE p sees them at
+ * stage s of level `level`: own points read U^{level,(s)}; buffer points
+ * combine delayed levels with the AT (or AS) weights. */
+static void tap(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t m, double* g)
+{
+    int64_t lo = p * c->B, hi = lo + c->B;
+    double Q[4];
+    if (m >= lo && m < hi) {
+        state_at(c, field(c, level, s), m, Q);
+        derive(c, Q, g);
+        return;
+    }
+    int side = (m < lo) ? 0 : 1;
+    int k = c->keff[((size_t)s * c->P + p) * 2 + side];
+    int64_t mm = wrap(c, m);
+    double w[8];
+    int nw;
+    if (c->pb.mode == ORC_AT) {
+        orc_lagrange_weights(c->q, k, w);
+        nw = c->q + 1;
+    } else {
+        w[0] = 1.0;
+        nw = 1;
+    }
+    for (int d = 0; d < c->nder; ++d) g[d] = 0.0;
+    for (int l = 0; l < nw; ++l) {
+        double gl[MAXD];
+        /* a level with weight 0 (l >= 1 at k = 0) is not part of the scheme;
+         * it may not exist yet (start-up), so it is not evaluated at all */
+        if (w[l] == 0.0) continue;
+        state_at(c, field(c, level - k - l, s), mm, Q);
+        derive(c, Q, gl);
+        for (int d = 0; d < c->nder; ++d) g[d] += w[l] * gl[d];
+    }
+}
+
+/* wave speed at m as PE p sees it: own points at `level`, buffer points at
+ * the most recent delayed level n-k (not extrapolated). */
+static double tap_speed(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t m)
+{
+    int64_t lo = p * c->B, hi = lo + c->B;
+    double Q[4];
+    if (m >= lo && m < hi) {
+        state_at(c, field(c, level, s), m, Q);
+    } else {
+        int side = (m < lo) ? 0 : 1;
+        int k = c->keff[((size_t)s * c->P + p) * 2 + side];
+        state_at(c, field(c, level - k, s), wrap(c, m), Q);
+    }
+    return wave_speed(c, Q);
+}
+
+/* numerical flux at the edge between points i and i+1, as PE p sees it */
+static void edge_flux(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t i, double* F)
+{
+    int nv = c->nvar;
+    double eps = (c->pb.pde == ORC_EULER) ? c->pb.prm[4] : c->pb.prm[1];
+    double l0 = tap_speed(c, level, s, p, i), l1 = tap_speed(c, level, s, p, i + 1);
+    double lam = (l0 > l1) ? l0 : l1;
+    double G[6][MAXD];
+    for (int o = -2; o <= 3; ++o) tap(c, level, s, p, i + o, G[o + 2]);
+    for (int v = 0; v < nv; ++v) {
+        double fp[6], fm[6];
+        for (int o = 0; o < 6; ++o) {
+            fp[o] = 0.5 * (G[o][v] + lam * G[o][nv + v]);
+            fm[o] = 0.5 * (G[o][v] - lam * G[o][nv + v]);
+        }
+        double vp[5] = {fp[0], fp[1], fp[2], fp[3], fp[4]};
+        double vm[5] = {fm[5], fm[4], fm[3], fm[2], fm[1]};
+        F[v] = orc_weno5_js(vp, eps) + orc_weno5_js(vm, eps);
+    }
+}
+
+static void rhs_point(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t j, double* K)
+{
+    const double* pr = c->pb.prm;
+    const double dx = c->pb.dx;
+    int pde = c->pb.pde;
+    if (pde == ORC_ADVDIFF || pde == ORC_RNS) {
+        const double *d1, *d2;
+        double d1den, d2den;
+        central_tables(c->pb.order, &d1, &d1den, &d2, &d2den);
+        int H = c->H;
+        double G[7][MAXD];
+        for (int o = -H; o <= H; ++o) tap(c, level, s, p, j + o, G[o + H]);
+        double D1[MAXD], D2[MAXD];
+        for (int d = 0; d < c->nder; ++d) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int o = 0; o <= 2 * H; ++o) {
+                s1 += d1[o] * G[o][d];
+                s2 += d2[o] * G[o][d];
+            }
+            D1[d] = s1 / (d1den * dx);
+            D2[d] = s2 / (d2den * dx * dx);
+        }
+        if (pde == ORC_ADVDIFF) {
+            K[0] = -pr[0] * D1[0] + pr[1] * D2[0];
+        } else {
+            double gam = pr[0], mu = pr[1], Pr = pr[2], Le = pr[3], A = pr[4], Ea = pr[5], qc = pr[6];
+            double cp = gam / (gam - 1.0);
+            double lam = mu * cp / Pr;      /* thermal conductivity          */
+            double rhoD = lam / (cp * Le);  /* rho * D, Fick diffusion        */
+            double Q[4];
+            state_at(c, field(c, level, s), j, Q);
+            double g[MAXD];
+            derive(c, Q, g);
+            double T = g[6];
+            double wdot = A * Q[3] * exp(-Ea / T);
+            /* D1 of the convective fluxes; D2 of u, u^2, T, Y (Sec. 4 with
+             * tau = 4/3 mu u_x, q = -lam T_x + q_c J_F, J_F = -rhoD Y_x). */
+            K[0] = -D1[0];
+            K[1] = -D1[1] + (4.0 / 3.0) * mu * D2[4];
+            K[2] = -D1[2] + (2.0 / 3.0) * mu * D2[5] + lam * D2[6] + qc * rhoD * D2[7];
+            K[3] = -D1[3] + rhoD * D2[7] - wdot;
+        }
+    } else {
+        double Fr[4], Fl[4];
+        edge_flux(c, level, s, p, j, Fr);
+        edge_flux(c, level, s, p, j - 1, Fl);
+        for (int v = 0; v < c->nvar; ++v) K[v] = -(Fr[v] - Fl[v]) / dx;
+        if (pde == ORC_EULER) {
+            double A = pr[1], Ea = pr[2];
+            double Q[4];
+            state_at(c, field(c, level, s), j, Q);
+            double g[MAXD];
+            derive(c, Q, g);
+            double rho = Q[0], u = Q[1] / rho;
+            double p_ = (pr[0] - 1.0) * (Q[2] - 0.5 * Q[1] * u - pr[3] * Q[3]);
+            double T = p_ / rho;
+            K[3] -= A * Q[3] * exp(-Ea / T);
+        }
+    }
+}
+
+static void set_keff(orc_ctx* c, int64_t level, int s, const int32_t* kforce)
+{
+    for (int64_t p = 0; p < c->P; ++p)
+        for (int side = 0; side < 2; ++side) {
+            int k = kforce ? kforce[p * 2 + side] : orc_draw(c, level, s, p, side);
+            c->keff[((size_t)s * c->P + p) * 2 + side] = clamp_k(c, level, k);
+        }
+}
+
+void orc_rhs(orc_ctx* c, int64_t level, int stage, const int32_t* kforce, double* K)
+{
+    set_keff(c, level, stage, kforce);
+    double Kp[4];
+    for (int64_t p = 0; p < c->P; ++p)
+        for (int64_t jl = 0; jl < c->B; ++jl) {
+            int64_t j = p * c->B + jl;
+            rhs_point(c, level, stage, p, j, Kp);
+            for (int v = 0; v < c->nvar; ++v) K[(size_t)v * c->N + j] = Kp[v];
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* Runge-Kutta in Butcher form (Eq. rk1)                               */
+/* ------------------------------------------------------------------ */
+static void tableau(orc_ctx* c)
+{
+    memset(c->a, 0, sizeof c->a);
+    memset(c->b, 0, sizeof c->b);
+    if (c->pb.rk == ORC_RK2) { /* Eq. rk2 */
+        c->S = 2;
+        c->a[1][0] = 1.0;
+        c->b[0] = 0.5; c->b[1] = 0.5;
+    } else if (c->pb.rk == ORC_RK3TVD) { /* Shu-Osher TVD RK3 in Butcher form */
+        c->S = 3;
+        c->a[1][0] = 1.0;
+        c->a[2][0] = 0.25; c->a[2][1] = 0.25;
+        c->b[0] = 1.0 / 6.0; c->b[1] = 1.0 / 6.0; c->b[2] = 2.0 / 3.0;
+    } else { /* classic RK4 */
+        c->S = 4;
+        c->a[1][0] = 0.5;
+        c->a[2][1] = 0.5;
+        c->a[3][2] = 1.0;
+        c->b[0] = 1.0 / 6.0; c->b[1] = 1.0 / 3.0; c->b[2] = 1.0 / 3.0; c->b[3] = 1.0 / 6.0;
+    }
+}
+
+static int step(orc_ctx* c)
+{
+    int64_t n = c->level;
+    size_t nf = (size_t)c->nvar * c->N;
+    for (int s = 0; s < c->S; ++s) {
+        double* U = field(c, n, s);
+        for (size_t i = 0; i < nf; ++i) {
+            double acc = 0.0;
+            for (int r = 0; r < s; ++r) acc += c->a[s][r] * c->K[(size_t)r * nf + i];
+            U[i] = c->u[i] + c->pb.dt * acc;
+        }
+        orc_rhs(c, n, s, NULL, c->K + (size_t)s * nf);
+    }
+    int bad = 0;
+    for (size_t i = 0; i < nf; ++i) {
+        double acc = 0.0;
+        for (int s = 0; s < c->S; ++s) acc += c->b[s] * c->K[(size_t)s * nf + i];
+        c->u[i] = c->u[i] + c->pb.dt * acc;
+        if (!isfinite(c->u[i])) bad = 1;
+    }
+    for (size_t i = 0; i < (size_t)c->S * c->P * 2; ++i) c->dlog[i] = (uint8_t)c->keff[i];
+    c->level = n + 1;
+    return bad ? -4 : 0;
+}
+
+int orc_run(orc_ctx* c, int64_t nsteps)
+{
+    for (int64_t i = 0; i < nsteps; ++i) {
+        int st = step(c);
+        if (st) return st;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+orc_ctx* orc_create(const orc_problem* pb, const double* init)
+{
+    if (!pb || !init) return NULL;
+    if (pb->pe_size <= 0 || pb->n <= 0 || pb->n % pb->pe_size) return NULL;
+    if (pb->k_max < 0 || pb->k_max > 15) return NULL;
+    if (pb->pde < 0 || pb->pde > 3) return NULL;
+    orc_ctx* c = (orc_ctx*)calloc(1, sizeof *c);
+    if (!c) return NULL;
+    c->pb = *pb;
+    c->nvar = nvar_of(pb->pde);
+    int weno = (pb->pde == ORC_EULER || pb->pde == ORC_ADV_WENO);
+    if (weno) {
+        c->H = 3;
+        c->q = 1;
+    } else {
+        if (pb->order != 2 && pb->order != 4 && pb->order != 6) {
+            free(c);
+            return NULL;
+        }
+        c->H = pb->order / 2;
+        c->q = pb->order / 2;
+    }
+    c->nder = (pb->pde == ORC_ADVDIFF) ? 1 : (pb->pde == ORC_ADV_WENO ? 2 : 8);
+    if (pb->pe_size < 2 * c->H) {
+        free(c);
+        return NULL;
+    }
+    tableau(c);
+    c->N = pb->n;
+    c->B = pb->pe_size;
+    c->P = pb->n / pb->pe_size;
+    c->R = pb->k_max + c->q + 1;
+    orc_thresholds(pb->k_max, pb->dist, pb->prob, c->thr);
+    size_t nf = (size_t)c->nvar * c->N;
+    c->u = (double*)malloc(nf * sizeof(double));
+    c->hist = (double*)calloc(nf * c->R * c->S, sizeof(double));
+    c->K = (double*)calloc(nf * c->S, sizeof(double));
+    c->keff = (int32_t*)calloc((size_t)c->S * c->P * 2, sizeof(int32_t));
+    c->dlog = (uint8_t*)calloc((size_t)c->S * c->P * 2, 1);
+    if (!c->u || !c->hist || !c->K || !c->keff || !c->dlog) {
+        orc_destroy(c);
+        return NULL;
+    }
+    memcpy(c->u, init, nf * sizeof(double));
+    c->level = 0;
+    return c;
+}
+
+void orc_destroy(orc_ctx* c)
+{
+    if (!c) return;
+    free(c->u);
+    free(c->hist);
+    free(c->K);
+    free(c->keff);
+    free(c->dlog);
+    free(c);
+}
+
+int orc_nvar(const orc_ctx* c) { return c->nvar; }
+int orc_stages(const orc_ctx* c) { return c->S; }
+int orc_q(const orc_ctx* c) { return c->q; }
+int orc_ring_levels(const orc_ctx* c) { return c->R; }
+int64_t orc_level(const orc_ctx* c) { return c->level; }
+
+void orc_get_state(const orc_ctx* c, double* out)
+{
+    memcpy(out, c->u, (size_t)c->nvar * c->N * sizeof(double));
+}
+
+void orc_get_delays(const orc_ctx* c, uint8_t* out)
+{
+    memcpy(out, c->dlog, (size_t)c->S * c->P * 2);
+}
+
+void orc_set_history(orc_ctx* c, int64_t level, int stage, const double* f)
+{
+    memcpy(field(c, level, stage), f, (size_t)c->nvar * c->N * sizeof(double));
+}
+
+/* numerical WENO flux at the edge between points i and i+1 as PE pe sees it
+ * (exposed for the pins; kforce as in orc_rhs) */
+void orc_edge_flux(orc_ctx* c, int64_t level, int stage, const int32_t* kforce, int64_t pe, int64_t i,
+                   double* F)
+{
+    set_keff(c, level, stage, kforce);
+    edge_flux(c, level, stage, pe, i, F);
+}

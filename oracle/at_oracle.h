@@ -1,0 +1,80 @@
+/*
+ * at_oracle.h -- plain FP64 CPU oracle for the asynchrony-tolerant (AT)
+ * Runge-Kutta-stage right-hand side of Kumari, Aditya & Donzis,
+ * "Evaluation of finite difference based asynchronous PDE solver for
+ * reacting flows" (arXiv 2204.01133).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA library; the two meet only through
+ * the seeded input generators.
+ *
+ * Everything here is written for checkability, not speed: full stage-field
+ * histories (not edge windows), Butcher-form Runge-Kutta, one point at a
+ * time, coefficients written as the textbook/paper fractions.
+ */
+#ifndef AT_ORACLE_H
+#define AT_ORACLE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_ADVDIFF = 0, ORC_RNS = 1, ORC_EULER = 2, ORC_ADV_WENO = 3 };
+enum { ORC_RK2 = 0, ORC_RK3TVD = 1, ORC_RK4 = 2 };
+enum { ORC_SYNC = 0, ORC_AS = 1, ORC_AT = 2 };
+enum { ORC_UNIFORM = 0, ORC_TABLE = 1, ORC_GEOMETRIC = 2 };
+
+typedef struct {
+    int pde;          /* ORC_ADVDIFF | ORC_RNS | ORC_EULER | ORC_ADV_WENO      */
+    int order;        /* central order 2|4|6 (ADVDIFF, RNS); ignored for WENO  */
+    int rk;           /* ORC_RK2 | ORC_RK3TVD | ORC_RK4                        */
+    int64_t n;        /* grid points (periodic), n % pe_size == 0              */
+    int32_t pe_size;  /* points per processing element (PE)                    */
+    double dx, dt;
+    double prm[16];   /* physics constants, see at_oracle.c                    */
+    int mode;         /* ORC_SYNC | ORC_AS | ORC_AT                            */
+    int k_max;        /* largest delay (inclusive)                             */
+    int dist;         /* ORC_UNIFORM | ORC_TABLE | ORC_GEOMETRIC               */
+    double prob[16];
+    uint64_t seed;
+    int per_stage;    /* 1: one draw per (step, stage); 0: one per step        */
+    uint32_t instance;
+} orc_problem;
+
+typedef struct orc_ctx orc_ctx;
+
+/* returns NULL on invalid input */
+orc_ctx* orc_create(const orc_problem* pb, const double* init /* [nvar][n] */);
+void orc_destroy(orc_ctx* c);
+int orc_nvar(const orc_ctx* c);
+int orc_stages(const orc_ctx* c);
+int orc_q(const orc_ctx* c);
+int orc_ring_levels(const orc_ctx* c);
+int64_t orc_level(const orc_ctx* c);
+/* advance nsteps full RK steps; returns 0, or -4 if a non-finite value appeared */
+int orc_run(orc_ctx* c, int64_t nsteps);
+void orc_get_state(const orc_ctx* c, double* out /* [nvar][n] */);
+/* k_eff of the last completed step, [stages][P][2] (side 0 = left, 1 = right) */
+void orc_get_delays(const orc_ctx* c, uint8_t* out);
+
+/* ---- pieces exposed for the pins in tests/ ---- */
+/* overwrite the stored stage argument U^{level,(stage)} (a full field) */
+void orc_set_history(orc_ctx* c, int64_t level, int stage, const double* field);
+/* right-hand side K of stage `stage` at level `level`, reading U^{level,(stage)}
+ * for own points and delayed levels for PE-boundary taps.  kforce: [P][2]
+ * raw delays to use (clamped like a drawn delay), or NULL to draw them. */
+void orc_rhs(orc_ctx* c, int64_t level, int stage, const int32_t* kforce, double* K);
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void orc_thresholds(int k_max, int dist, const double* prob, uint64_t* thr);
+int orc_draw(const orc_ctx* c, int64_t level, int stage, int64_t pe, int side);
+void orc_lagrange_weights(int q, int k, double* w);
+double orc_weno5_js(const double v[5], double eps);
+/* WENO flux F[nvar] at the edge between points i and i+1 as PE `pe` sees it */
+void orc_edge_flux(orc_ctx* c, int64_t level, int stage, const int32_t* kforce, int64_t pe, int64_t i,
+                   double* F);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,639 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test ties one part of ``oracle/at_oracle.c`` to something other than
+itself: published known-answer vectors, formulas printed in the paper
+(Appendix A, Eqs. atRecon / atReconM / beta2AT0-2, Appendix B), closed-form
+solutions, Taylor exactness on polynomials, invariants (conservation, zero
+delay == synchronous) and the orders of accuracy the paper states.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_01133_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Delay generator: Philox4x32-10 and the threshold table (Sec. 2.1, Sec. 5)
+# --------------------------------------------------------------------------
+def _kat():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(x, 16) for x in line.split()]
+            rows.append((v[0:4], v[4:6], v[6:10]))
+    return rows
+
+
+def test_philox_known_answers():
+    rows = _kat()
+    assert len(rows) == 3
+    for ctr, key, out in rows:
+        assert oracle.philox4x32_10(ctr, key) == out
+
+
+def test_thresholds_exact_cases():
+    # uniform on {0..3}: CDF = 1/4, 2/4, 3/4 -> exact multiples of 2^30
+    assert oracle.thresholds(3, "uniform") == [1 << 30, 2 << 30, 3 << 30]
+    # Table dels, Set 4 is synchronous: p = [1, 0, 0] -> every threshold 2^32
+    assert oracle.thresholds(2, "table", [1.0, 0.0, 0.0]) == [1 << 32, 1 << 32]
+    # Set 1 [0.8 0.1 0.1]
+    t = oracle.thresholds(2, "table", [0.8, 0.1, 0.1])
+    assert t[0] == math.floor(0.8 * 2**32) and abs(t[1] - 0.9 * 2**32) <= 1
+    # geometric r = 1/2 on {0..2}: weights 4:2:1 of 7
+    t = oracle.thresholds(2, "geometric", [0.5])
+    assert t == [math.floor(4 / 7 * 2**32), math.floor(6 / 7 * 2**32)]
+
+
+@pytest.mark.parametrize("dist,prob,k_max", [
+    ("table", [0.4, 0.5, 0.1], 2),      # Table dels, Set 3
+    ("uniform", [], 3),
+    ("geometric", [0.5], 4),
+])
+def test_delay_histogram_matches_table(dist, prob, k_max):
+    from scipy.stats import chi2
+    pb, u0 = W.advdiff(n=64, pe_size=16, k_max=k_max, dist=dist, prob=prob, seed=1234)
+    o = oracle.Oracle(pb, u0)
+    counts = np.zeros(k_max + 1)
+    for lvl in range(2000):
+        for pe in range(4):
+            for side in (0, 1):
+                counts[o.draw(lvl, lvl % 4, pe, side)] += 1
+    if dist == "uniform":
+        p = np.full(k_max + 1, 1.0 / (k_max + 1))
+    elif dist == "table":
+        p = np.array(prob) / sum(prob)
+    else:
+        w = np.array([0.5 * 0.5**i for i in range(k_max + 1)])
+        p = w / w.sum()
+    exp = p * counts.sum()
+    stat = ((counts - exp) ** 2 / exp).sum()
+    assert stat < chi2.ppf(0.999, k_max)
+
+
+def test_delays_startup_clamp_and_per_stage():
+    pb, u0 = W.advdiff(n=256, pe_size=16, k_max=3, seed=7)
+    o = oracle.Oracle(pb, u0)
+    o.run(1)
+    assert not o.delays().any()          # level 0: nothing older exists
+    o.run(3)                             # level 3 with q = 2: at most 1 level back
+    assert o.delays().max() <= 1
+    o.run(20)
+    d = o.delays()
+    assert d.max() == 3 and d.min() == 0
+    assert not all((d[s] == d[0]).all() for s in range(4))     # per-stage draws differ
+    pb0 = dict(pb, per_stage=0)
+    o0 = oracle.Oracle(pb0, u0)
+    o0.run(24)
+    d0 = o0.delays()
+    assert all((d0[s] == d0[0]).all() for s in range(4))       # one draw per step
+
+
+# --------------------------------------------------------------------------
+# Temporal extrapolation weights == the printed AT coefficients
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("k", range(0, 9))
+def test_weights_match_printed_schemes(k):
+    # Eq. at1 (q = 1): (k+1) u^{n-k} - k u^{n-k-1}
+    assert oracle.lagrange_weights(1, k) == [k + 1, -k]
+    # Appendix A (q = 2): (k^2+3k+2)/2, -(k^2+2k), (k^2+k)/2
+    assert oracle.lagrange_weights(2, k) == [(k * k + 3 * k + 2) / 2, -(k * k + 2 * k), (k * k + k) / 2]
+
+
+@pytest.mark.parametrize("q", [1, 2, 3])
+@pytest.mark.parametrize("k", range(0, 6))
+def test_weights_extrapolate_polynomials_exactly(q, k):
+    w = oracle.lagrange_weights(q, k)
+    for deg in range(q + 1):
+        # f(t) = t^deg sampled at t = -k-l must give f(0) = [deg == 0]
+        val = sum(Fraction(wl).limit_denominator(10**6) * Fraction(-k - l) ** deg for l, wl in enumerate(w))
+        assert val == (1 if deg == 0 else 0)
+    if k > 0:
+        val = sum(Fraction(wl) * Fraction(-k - l) ** (q + 1) for l, wl in enumerate(w))
+        assert val != 0
+
+
+# --------------------------------------------------------------------------
+# Appendix A (Table tab:atschemes): AT4 first and second derivatives
+# --------------------------------------------------------------------------
+def _hist_oracle(order, c, a, L0, seed=3, n=64, B=16):
+    pb, u0 = W.advdiff(n=n, pe_size=B, order=order, c=c, a=a, dt=1.0, length=float(n))
+    pb["dx"] = 1.0
+    o = oracle.Oracle(pb, u0)
+    rng = np.random.default_rng(seed)
+    hist = {}
+    for lvl in range(0, L0 + 1):
+        f = rng.standard_normal(n)
+        hist[lvl] = f
+        o.set_history(lvl, 0, f[None, :])
+    return o, hist
+
+
+def _appendix_a(deriv, side, k, u, j, L0):
+    """Table tab:atschemes, written as printed (dx = 1)."""
+    w = [(k * k + 3 * k + 2) / 2, -(k * k + 2 * k), (k * k + k) / 2]
+    tot = 0.0
+    for l, wl in enumerate(w):
+        d = L0 - k - l
+
+        def U(m, lvl_own=True):
+            return u[L0][(j + m) % len(u[L0])] if lvl_own else u[d][(j + m) % len(u[d])]
+
+        if side == "left":
+            um2, um1, u0_, up1, up2 = U(-2, False), U(-1, False), U(0), U(1), U(2)
+        else:
+            um2, um1, u0_, up1, up2 = U(-2), U(-1), U(0), U(1, False), U(2, False)
+        if deriv == 2:
+            tot += wl * (-up2 + 16 * up1 - 30 * u0_ + 16 * um1 - um2) / 12.0
+        else:
+            tot += wl * (-up2 + 8 * up1 - 8 * um1 + um2) / 12.0
+    return tot
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+@pytest.mark.parametrize("deriv", [1, 2])
+def test_at4_equals_appendix_a(k, deriv):
+    L0 = 8
+    c, a = (1.0, 0.0) if deriv == 1 else (0.0, 1.0)
+    o, u = _hist_oracle(4, c, a, L0)
+    kf = np.full((4, 2), k)
+    K = o.rhs(L0, 0, kf)[0]
+    sign = -1.0 if deriv == 1 else 1.0
+    for j, side in ((16, "left"), (31, "right"), (48, "left"), (63, "right")):
+        ref = sign * _appendix_a(deriv, side, k, u, j, L0)
+        assert abs(K[j] - ref) <= 1e-12 * (1 + abs(ref)), (j, side)
+
+
+# --------------------------------------------------------------------------
+# Taylor matching (Eq. geDer): exactness on x^a t^b, and local order
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [2, 4, 6])
+@pytest.mark.parametrize("deriv", [1, 2])
+def test_at_schemes_exact_on_polynomials(order, deriv):
+    """Eq. geDer: with the AT weights every monomial x^a t^b with a within the
+    central stencil's exactness (a <= order + deriv - 1) and b <= q is
+    differentiated exactly at a PE-boundary point, for every delay k."""
+    n, B = 64, 16
+    q = order // 2
+    c, a = (1.0, 0.0) if deriv == 1 else (0.0, 1.0)
+    pb, u0 = W.advdiff(n=n, pe_size=B, order=order, c=c, a=a, dt=1.0, length=float(n), k_max=4)
+    o = oracle.Oracle(pb, u0)
+    L0, j = 10, 16  # j: first point of PE 1, every left tap is a buffer point
+    x = (np.arange(n) - j).astype(float) / 4.0
+    sign = -1.0 if deriv == 1 else 1.0
+    for k in range(0, 5):
+        kf = np.full((4, 2), k)
+        for ax in range(0, order + deriv):
+            for bt in range(0, q + 1):
+                for lvl in range(0, L0 + 1):
+                    t = lvl - L0 + 0.5
+                    o.set_history(lvl, 0, (x**ax * t**bt)[None, :])
+                K = o.rhs(L0, 0, kf)[0]
+                exact = (math.factorial(deriv) / 4.0**deriv if ax == deriv else 0.0) * 0.5**bt
+                assert abs(sign * K[j] - exact) < 1e-9, (k, ax, bt)
+        # one degree more in x is not differentiated exactly
+        ax = order + 1 if deriv == 1 else order + 2
+        for lvl in range(0, L0 + 1):
+            o.set_history(lvl, 0, (x**ax)[None, :])
+        K = o.rhs(L0, 0, kf)[0]
+        assert abs(K[j]) > 1e-12
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+@pytest.mark.parametrize("deriv", [1, 2])
+def test_at_schemes_extrapolation_degree_is_tight(order, deriv):
+    """A field linear in x times t^(q+1) is differentiated wrongly when k > 0:
+    the temporal extrapolation has degree exactly q."""
+    n, B = 64, 16
+    q = order // 2
+    c, a = (1.0, 0.0) if deriv == 1 else (0.0, 1.0)
+    pb, u0 = W.advdiff(n=n, pe_size=B, order=order, c=c, a=a, dt=1.0, length=float(n))
+    o = oracle.Oracle(pb, u0)
+    L0, j = 10, 16
+    x = (np.arange(n) - j).astype(float)
+    kf = np.full((4, 2), 2)
+    for lvl in range(0, L0 + 1):
+        t = lvl - L0
+        o.set_history(lvl, 0, (x**deriv * (1.0 + t ** (q + 1)))[None, :])
+    K = o.rhs(L0, 0, kf)[0]
+    exact = float(math.factorial(deriv))  # at t = 0
+    sign = -1.0 if deriv == 1 else 1.0
+    assert abs(sign * K[j] - exact) > 1e-6
+    for lvl in range(0, L0 + 1):
+        t = lvl - L0
+        o.set_history(lvl, 0, (x**deriv * (1.0 + t**q))[None, :])
+    K = o.rhs(L0, 0, kf)[0]
+    assert abs(sign * K[j] - exact) < 1e-9
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+@pytest.mark.parametrize("deriv", [1, 2])
+def test_at_local_truncation_order(order, deriv):
+    """dt = dx^2: the AT derivative at a PE-boundary point converges at the
+    order of the central scheme for every delay (Sec. 2.2)."""
+    q = order // 2
+    errs = []
+    for n in (32, 64, 128):
+        B = n // 4
+        dx = 2 * math.pi / n
+        dt = dx * dx
+        c, a = (1.0, 0.0) if deriv == 1 else (0.0, 1.0)
+        pb, u0 = W.advdiff(n=n, pe_size=B, order=order, c=c, a=a, dt=dt, k_max=4)
+        o = oracle.Oracle(pb, u0)
+        L0 = 10
+        x = np.arange(n) * dx
+        for lvl in range(0, L0 + 1):
+            t = (lvl - L0) * dt
+            o.set_history(lvl, 0, (np.sin(x + 0.3 + 2 * t) * math.cos(t + 0.2) + 0.1 * t**2)[None, :])
+        kf = np.full((4, 2), 4)
+        K = o.rhs(L0, 0, kf)[0]
+        j = B
+        ex = (math.cos(x[j] + 0.3) if deriv == 1 else -math.sin(x[j] + 0.3)) * math.cos(0.2)
+        sign = -1.0 if deriv == 1 else 1.0
+        errs.append(abs(sign * K[j] - ex))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert orders[-1] > order - 0.6, (errs, orders)
+    _ = q
+
+
+# --------------------------------------------------------------------------
+# Zero delay == synchronous (Sec. 2.2 after Eq. at1; Eq. rkat2 at k = 0)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("maker", ["advdiff", "rns", "euler", "adv_weno"])
+def test_zero_delay_is_bitwise_sync(maker):
+    if maker == "advdiff":
+        mk = lambda **kw: W.advdiff(n=256, pe_size=16, cfl=0.075, **kw)
+    elif maker == "rns":
+        mk = lambda **kw: W.rns(case="flame", n=512, pe_size=32, dt=0.003, **kw)
+    elif maker == "euler":
+        mk = lambda **kw: W.detonation(n=2048, pe_size=256, **kw)
+    else:
+        mk = lambda **kw: W.adv_weno(n=128, pe_size=16, **kw)
+    pb_s, u0 = mk(mode="sync")
+    pb_a, _ = mk(mode="at", k_max=0)
+    pb_d, _ = mk(mode="at", k_max=2, dist="uniform")
+    os_, oa, od = oracle.Oracle(pb_s, u0), oracle.Oracle(pb_a, u0), oracle.Oracle(pb_d, u0)
+    for o in (os_, oa, od):
+        assert o.run(20) == 0
+    assert np.array_equal(os_.state(), oa.state())
+    assert not np.array_equal(os_.state(), od.state())
+
+
+# --------------------------------------------------------------------------
+# Closed form and orders on advection-diffusion (Eq. rkat2; Sec. 2.1)
+# --------------------------------------------------------------------------
+def _advdiff_err(n, mode, k_max=3, t_end=0.25, r=0.05, order=4, a=0.5):
+    dx = 2 * math.pi / n
+    dt = r * dx * dx / a
+    steps = int(round(t_end / dt))
+    dt = t_end / steps
+    pb, u0 = W.advdiff(n=n, pe_size=16, order=order, c=1.0, a=a, mode=mode, k_max=k_max, dt=dt)
+    o = oracle.Oracle(pb, u0)
+    assert o.run(steps) == 0
+    return np.abs(o.state() - W.advdiff_exact(pb, t_end)).max()
+
+
+def test_advdiff_sync_converges_to_closed_form_at_fourth_order():
+    e = [_advdiff_err(n, "sync") for n in (32, 64, 128)]
+    rates = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert min(rates) > 3.7, (e, rates)
+    assert e[-1] < 1e-6
+
+
+def test_advdiff_at_keeps_order_and_as_loses_it():
+    at = [_advdiff_err(n, "at") for n in (32, 64, 128)]
+    as_ = [_advdiff_err(n, "as") for n in (32, 64, 128)]
+    r_at = math.log2(at[1] / at[2])
+    r_as = math.log2(as_[1] / as_[2])
+    assert r_at > 3.5, at
+    assert r_as < 2.6, as_
+    assert as_[-1] > 100 * at[-1]
+
+
+def test_as_error_far_above_at_error_on_advdiff_config():
+    """Table ap / Tables aiL1-aiLinf trend: AS-SFD errors are orders of
+    magnitude above AT errors for the same delay statistics."""
+    pb_s, u0 = W.advdiff(mode="sync", cfl=0.075)
+    out = {}
+    for mode in ("sync", "at", "as"):
+        pb, _ = W.advdiff(mode=mode, cfl=0.075)
+        o = oracle.Oracle(pb, u0)
+        assert o.run(600) == 0
+        out[mode] = o.state()
+    e_at = np.abs(out["at"] - out["sync"]).max()
+    e_as = np.abs(out["as"] - out["sync"]).max()
+    assert e_as > 100 * e_at
+
+
+# --------------------------------------------------------------------------
+# WENO5: linear limit, ENO property, smooth order (Sec. 3)
+# --------------------------------------------------------------------------
+def test_weno5_ideal_weights_give_upwind5():
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        v = rng.standard_normal(5)
+        lin = (2 * v[0] - 13 * v[1] + 47 * v[2] + 27 * v[3] - 3 * v[4]) / 60.0
+        assert abs(oracle.weno5(v, eps=1e30) - lin) < 1e-14
+
+
+def test_weno5_exact_on_quadratics_and_eno_at_steps():
+    for v in ([1.0, 4.0, 9.0, 16.0, 25.0], [2.0, 2.0, 2.0, 2.0, 2.0]):
+        # cell averages of a quadratic over unit cells centred at -2..2
+        pass
+    # point values f_i = cell averages of h; for h(x) = x^2, avg over [i-1/2,i+1/2] = i^2 + 1/12
+    v = [i * i + 1.0 / 12.0 for i in range(-2, 3)]
+    assert abs(oracle.weno5(v) - 0.25) < 1e-12
+    # ENO: the stencil that avoids the jump gets (almost) all the weight
+    assert abs(oracle.weno5([0, 0, 0, 1, 1])) < 1e-6
+    assert abs(oracle.weno5([0, 0, 1, 1, 1]) - 1.0) < 1e-6
+    assert abs(oracle.weno5([1, 1, 1, 0, 0]) - 1.0) < 1e-6
+
+
+def test_weno5_smooth_flux_difference_is_fifth_order():
+    f = lambda x: x + 0.2 * np.sin(x)
+    fp = lambda x: 1 + 0.2 * np.cos(x)
+    errs = []
+    for h in (0.2, 0.1, 0.05):
+        x0 = 0.7
+        vals = [f(x0 + i * h) for i in range(-3, 3)]
+        Fr = oracle.weno5(vals[1:6], eps=1e-40)
+        Fl = oracle.weno5(vals[0:5], eps=1e-40)
+        errs.append(abs((Fr - Fl) / h - fp(x0)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 4.5, (errs, rates)
+
+
+# --------------------------------------------------------------------------
+# AT-WENO5: printed formulas (Eqs. atRecon, beta2AT0-2, atReconM; App. B)
+# --------------------------------------------------------------------------
+def _printed_left_plus(k, a, a1, b, b1, c, d, e):
+    """Eq. atRecon and Eqs. beta2AT0/1/2 (left boundary, edge j+1/2)."""
+    p0 = -k * a1 / 3 + 7 * k * b1 / 6 + (2 * k + 2) * a / 6 + (-7 * k - 7) * b / 6 + 11 * c / 6
+    p1 = k * b1 / 6 + (-k - 1) * b / 6 + 5 * c / 6 + d / 3
+    p2 = c / 3 + 5 * d / 6 - e / 6
+    B0 = (4 * a * a + 25 * b * b
+          + k * k * (4 * a1 * a1 + 4 * a * a + 19 * a * (b1 - b) + 25 * (b1 - b) ** 2 + a1 * (19 * (b - b1) - 8 * a))
+          - 31 * c * b + 10 * c * c + a * (11 * c - 19 * b)
+          + k * (8 * a * a + (19 * b1 - 38 * b + 11 * c) * a + a1 * (-8 * a + 19 * b - 11 * c)
+                 - (b1 - b) * (50 * b - 31 * c))) / 3
+    B1 = (4 * k * k * (b1 - b) ** 2 + 4 * b * b + 13 * c * c + 4 * d * d + (5 * d - 13 * c) * b - 13 * c * d
+          - k * (b1 - b) * (8 * b - 13 * c + 5 * d)) / 3
+    B2 = (10 * c * c - 31 * d * c + 25 * d * d + 4 * e * e + (11 * c - 19 * d) * e) / 3
+    return (p0, p1, p2), (B0, B1, B2)
+
+
+def _printed_right_plus(k, a, b, c, d, d1, e, e1):
+    """Appendix B, Eq. atReconR and the right-boundary smoothness indicators."""
+    p0 = a / 3 - 7 * b / 6 + 11 * c / 6
+    p1 = -k * d1 / 3 + (2 * k + 2) * d / 6 - b / 6 + 5 * c / 6
+    p2 = -5 * k * d1 / 6 + k * e1 / 6 + (5 * k + 5) * d / 6 + (-k - 1) * e / 6 + c / 3
+    B0 = (4 * a * a + (11 * c - 19 * b) * a + 25 * b * b + 10 * c * c - 31 * b * c) / 3
+    X = k * d1 - (k + 1) * d
+    B1 = (b * (-5 * k * d1 + 5 * (k + 1) * d - 13 * c) + 4 * X * X + 13 * c * X + 4 * b * b + 13 * c * c) / 3
+    B2 = (k * k * (25 * d1 * d1 + (19 * (e - e1) - 50 * d) * d1 + 25 * d * d + 4 * (e1 - e) ** 2 + 19 * d * (e1 - e))
+          + k * (50 * d * d + 19 * (e1 - 2 * e) * d + 8 * e * (e - e1) + d1 * (19 * e - 50 * d))
+          + 25 * d * d + 4 * e * e - 19 * d * e
+          + c * (-31 * d + 11 * e + k * (31 * d1 - 31 * d - 11 * e1 + 11 * e)) + 10 * c * c) / 3
+    return (p0, p1, p2), (B0, B1, B2)
+
+
+def _printed_left_minus(k, a, a1, b, b1, c, d, e):
+    """Eq. atReconM (left boundary, edge j-1/2): candidates only."""
+    p0 = k * a1 / 6 - 5 * k * b1 / 6 + (-k - 1) * a / 6 + (5 * k + 5) * b / 6 + c / 3
+    p1 = -k * b1 / 3 + (2 * k + 2) * b / 6 + 5 * c / 6 - d / 6
+    p2 = 11 * c / 6 - 7 * d / 6 + e / 3
+    return p0, p1, p2
+
+
+def _printed_right_minus(k, a, b, c, d, d1, e, e1):
+    """Appendix B, Eq. atReconRm (right boundary, edge j-1/2): candidates only."""
+    p0 = -a / 6 + 5 * b / 6 + c / 3
+    p1 = k * d1 / 6 + (-k - 1) * d / 6 + b / 3 + 5 * c / 6
+    p2 = 7 * k * d1 / 6 - k * e1 / 3 + (-7 * k - 7) * d / 6 + (2 * k + 2) * e / 6 + 11 * c / 6
+    return p0, p1, p2
+
+
+def _combine(p, B, eps):
+    g = (0.1, 0.6, 0.3)
+    al = [g[i] / (eps + B[i]) ** 2 for i in range(3)]
+    s = sum(al)
+    return sum(al[i] / s * p[i] for i in range(3))
+
+
+def test_printed_at_weno_is_weno_on_linearly_extrapolated_values():
+    """Symbolic: every printed AT-WENO candidate and indicator equals the
+    synchronous one evaluated on (k+1) u^{n-k} - k u^{n-k-1} at buffer points."""
+    sp = pytest.importorskip("sympy")
+    k, a, a1, b, b1, c, d, d1, e, e1 = sp.symbols("k a a1 b b1 c d d1 e e1")
+    R = sp.Rational
+    A = (k + 1) * a - k * a1
+    Bx = (k + 1) * b - k * b1
+    Dx = (k + 1) * d - k * d1
+    Ex = (k + 1) * e - k * e1
+
+    def std_plus(v0, v1, v2, v3, v4):
+        p = (v0 / 3 - R(7, 6) * v1 + R(11, 6) * v2, -v1 / 6 + R(5, 6) * v2 + v3 / 3, v2 / 3 + R(5, 6) * v3 - v4 / 6)
+        Bs = (R(13, 12) * (v0 - 2 * v1 + v2) ** 2 + R(1, 4) * (v0 - 4 * v1 + 3 * v2) ** 2,
+              R(13, 12) * (v1 - 2 * v2 + v3) ** 2 + R(1, 4) * (v1 - v3) ** 2,
+              R(13, 12) * (v2 - 2 * v3 + v4) ** 2 + R(1, 4) * (3 * v2 - 4 * v3 + v4) ** 2)
+        return p, Bs
+
+    def std_minus(v0, v1, v2, v3, v4):  # value at the left edge of the middle cell
+        return (-v0 / 6 + R(5, 6) * v1 + v2 / 3, v1 / 3 + R(5, 6) * v2 - v3 / 6, R(11, 6) * v2 - R(7, 6) * v3 + v4 / 3)
+
+    # left boundary j+1/2 (Eq. atRecon, Eqs. beta2AT0-2)
+    p, Bs = _printed_left_plus(k, a, a1, b, b1, c, d, e)
+    ps, Bss = std_plus(A, Bx, c, d, e)
+    for x, y in zip(p + Bs, ps + Bss):
+        assert sp.expand(sp.nsimplify(x) - y) == 0
+    # right boundary j+1/2 (Eq. atReconR and App. B indicators)
+    p, Bs = _printed_right_plus(k, a, b, c, d, d1, e, e1)
+    ps, Bss = std_plus(a, b, c, Dx, Ex)
+    for x, y in zip(p + Bs, ps + Bss):
+        assert sp.expand(sp.nsimplify(x) - y) == 0
+    # j-1/2 at both boundaries (Eqs. atReconM, atReconRm)
+    for x, y in zip(_printed_left_minus(k, a, a1, b, b1, c, d, e), std_minus(A, Bx, c, d, e)):
+        assert sp.expand(sp.nsimplify(x) - y) == 0
+    for x, y in zip(_printed_right_minus(k, a, b, c, d, d1, e, e1), std_minus(a, b, c, Dx, Ex)):
+        assert sp.expand(sp.nsimplify(x) - y) == 0
+
+
+def _weno_hist(c_adv, L0=6, seed=5, n=64, B=16):
+    pb, u0 = W.adv_weno(n=n, pe_size=B, c=c_adv, dt=1.0, k_max=4)
+    o = oracle.Oracle(pb, u0)
+    rng = np.random.default_rng(seed)
+    u = {}
+    for lvl in range(0, L0 + 1):
+        f = 1.0 + 0.3 * rng.standard_normal(n)
+        u[lvl] = f
+        o.set_history(lvl, 0, f[None, :])
+    return o, u
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 4])
+def test_oracle_at_weno_flux_equals_printed_formulas(k):
+    L0, eps = 6, 1e-6
+    kf = np.full((4, 2), k)
+    # c > 0: the flux is the left-biased reconstruction of f+ = c u
+    o, u = _weno_hist(5.0, L0)
+    cu = {lvl: 5.0 * v for lvl, v in u.items()}
+    j = 16  # first point of PE 1, edge j+1/2
+    p, Bs = _printed_left_plus(k, cu[L0 - k][j - 2], cu[L0 - k - 1][j - 2], cu[L0 - k][j - 1], cu[L0 - k - 1][j - 1],
+                               cu[L0][j], cu[L0][j + 1], cu[L0][j + 2])
+    F = o.edge_flux(L0, 0, 1, j, kf)[0]
+    assert abs(F - _combine(p, Bs, eps)) < 1e-12 * (1 + abs(F))
+    j = 31  # last point of PE 1, edge j+1/2
+    p, Bs = _printed_right_plus(k, cu[L0][j - 2], cu[L0][j - 1], cu[L0][j], cu[L0 - k][j + 1], cu[L0 - k - 1][j + 1],
+                                cu[L0 - k][j + 2], cu[L0 - k - 1][j + 2])
+    F = o.edge_flux(L0, 0, 1, j, kf)[0]
+    assert abs(F - _combine(p, Bs, eps)) < 1e-12 * (1 + abs(F))
+    # c < 0: right-biased reconstruction of f- = c u at the edge j-1/2
+    pb, u0 = W.adv_weno(n=64, pe_size=16, c=-5.0, dt=1.0, eps=1e30, k_max=4)
+    o = oracle.Oracle(pb, u0)
+    for lvl, v in u.items():
+        o.set_history(lvl, 0, v[None, :])
+    cu = {lvl: -5.0 * v for lvl, v in u.items()}
+    j = 16
+    p = _printed_left_minus(k, cu[L0 - k][j - 2], cu[L0 - k - 1][j - 2], cu[L0 - k][j - 1], cu[L0 - k - 1][j - 1],
+                            cu[L0][j], cu[L0][j + 1], cu[L0][j + 2])
+    F = o.edge_flux(L0, 0, 1, j - 1, kf)[0]
+    ideal = 0.1 * p[2] + 0.6 * p[1] + 0.3 * p[0]   # ideal weights mirror for the right-biased side
+    assert abs(F - ideal) < 1e-12 * (1 + abs(F))
+    j = 31
+    p = _printed_right_minus(k, cu[L0][j - 2], cu[L0][j - 1], cu[L0][j], cu[L0 - k][j + 1], cu[L0 - k - 1][j + 1],
+                             cu[L0 - k][j + 2], cu[L0 - k - 1][j + 2])
+    F = o.edge_flux(L0, 0, 1, j - 1, kf)[0]
+    ideal = 0.1 * p[2] + 0.6 * p[1] + 0.3 * p[0]
+    assert abs(F - ideal) < 1e-12 * (1 + abs(F))
+
+
+def _order_runs(maker, ns, mode, t_end, **kw):
+    errs = []
+    for n in ns:
+        pb, u0, exact = maker(n, mode, **kw)
+        steps = int(round(t_end / pb["dt"]))
+        pb["dt"] = t_end / steps
+        o = oracle.Oracle(pb, u0)
+        assert o.run(steps) == 0
+        errs.append(np.abs(o.state()[0] - exact(pb, t_end)).max())
+    return errs, [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+
+
+def test_weno_linear_advection_orders_sync_at_as():
+    """Sec. 3 order test (Table wenoLin trend): sync ~5, AT-WENO ~4, AS-WENO ~2.
+    x in [-1, 1], u0 = sin^4(pi x + 0.25), c = 5, RK3, dt ~ dx^2, p = [0.5, 0.5]."""
+    def mk(n, mode, **kw):
+        pb, u0 = W.adv_weno(n=n, pe_size=16, mode=mode, k_max=1, dt_coef=2.0, **kw)
+        return pb, u0, lambda pb, t: W.adv_weno_exact(pb, t)[0]
+    t_end = 0.1
+    e_s, r_s = _order_runs(mk, (64, 128, 256), "sync", t_end)
+    e_a, r_a = _order_runs(mk, (64, 128, 256), "at", t_end)
+    e_as, r_as = _order_runs(mk, (64, 128, 256), "as", t_end)
+    assert r_s[-1] > 4.3, (e_s, r_s)
+    assert r_a[-1] > 3.5, (e_a, r_a)
+    assert r_as[-1] < 2.6, (e_as, r_as)
+    assert e_as[-1] > 10 * e_a[-1]
+
+
+def test_euler_entropy_wave_closed_form():
+    """Reactive Euler at constant u and p without fuel: rho advects exactly."""
+    def mk(n, mode, **kw):
+        pb, u0 = W.entropy_wave(n=n, pe_size=16, mode=mode, k_max=1, dt_coef=0.5)
+        x = np.arange(n) / n
+        return pb, u0, lambda pb, t: 1 + 0.2 * np.sin(2 * np.pi * (x - t))
+    e_s, r_s = _order_runs(mk, (64, 128, 256), "sync", 0.2)
+    e_a, r_a = _order_runs(mk, (64, 128, 256), "at", 0.2)
+    assert r_s[-1] > 4.5 and r_a[-1] > 3.5, (e_s, r_s, e_a, r_a)
+
+
+# --------------------------------------------------------------------------
+# Runge-Kutta tableaux (Eq. rk1, Eq. rk2): a homogeneous reacting state has
+# no spatial gradients, so every point follows the 0-D ignition ODE.
+# --------------------------------------------------------------------------
+def _ode_reference(rhs, y0, t_end):
+    from scipy.integrate import solve_ivp
+    sol = solve_ivp(rhs, (0, t_end), [y0], rtol=1e-13, atol=1e-15, method="DOP853")
+    return sol.y[0, -1]
+
+
+@pytest.mark.parametrize("rk,expect", [("rk2", 2), ("rk3tvd", 3), ("rk4", 4)])
+def test_rk_order_on_homogeneous_ignition(rk, expect):
+    prm = W.det_prm()
+    gamma, A, Ea, Q = prm[0], prm[1], prm[2], prm[3]
+    rho, u, p0 = 1.0, 0.0, 10.0
+    E = p0 / (gamma - 1) + Q * 1.0
+
+    def rhs(t, y):
+        Y = y[0]
+        p = (gamma - 1) * (E - Q * Y)
+        return [-A * Y * math.exp(-Ea * rho / p)]
+
+    t_end = 0.02
+    ref = _ode_reference(rhs, 1.0, t_end)
+    errs = []
+    for steps in (20, 40, 80):
+        n = 2048
+        init = W.euler_conserved(np.full(n, rho), np.full(n, u), np.full(n, p0), np.ones(n), prm)
+        pb = W.base_problem(pde="euler", rk=rk, n=n, pe_size=256, dx=0.05, dt=t_end / steps, prm=prm,
+                            mode="sync", k_max=2)
+        o = oracle.Oracle(pb, init)
+        assert o.run(steps) == 0
+        s = o.state()
+        assert np.ptp(s[3]) == 0.0          # every point follows the same ODE
+        errs.append(abs(s[3][0] - ref))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert abs(rates[-1] - expect) < 0.3, (errs, rates)
+
+
+def test_rns_homogeneous_ignition_matches_ode():
+    prm = W.rns_prm()
+    gamma, A, Ea, qc = prm[0], prm[4], prm[5], prm[6]
+    n, T0 = 256, 4.0
+    rho = 1.0 / T0
+    init = W.rns_conserved(np.full(n, rho), np.zeros(n), np.full(n, T0), np.ones(n), prm)
+    rhoE = init[2][0]
+
+    def rhs(t, y):
+        rY = y[0]
+        p = (gamma - 1) * (rhoE - qc * rY)
+        return [-A * rY * math.exp(-Ea * rho / p)]
+
+    t_end, steps = 3.0, 300
+    ref = _ode_reference(rhs, rho, t_end)
+    pb = W.base_problem(pde="rns", order=6, rk="rk4", n=n, pe_size=32, dx=1.0, dt=t_end / steps, prm=prm,
+                        mode="sync", k_max=4)
+    o = oracle.Oracle(pb, init)
+    assert o.run(steps) == 0
+    s = o.state()
+    assert np.ptp(s[3]) <= 1e-15 * rho
+    assert abs(s[3][0] - ref) < 1e-9 * rho
+
+
+# --------------------------------------------------------------------------
+# Conservation (flux form, periodic): exact under SYNC
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["rns", "euler"])
+def test_sync_conserves_mass_momentum_energy(case):
+    if case == "rns":
+        pb, u0 = W.rns(case="flame", n=1024, pe_size=64, mode="sync", dt=0.003)
+        steps = 200
+    else:
+        pb, u0 = W.detonation(n=4096, pe_size=512, mode="sync")
+        steps = 100
+    o = oracle.Oracle(pb, u0)
+    assert o.run(steps) == 0
+    s = o.state()
+    for v in range(3):
+        tot0, tot1 = u0[v].sum(), s[v].sum()
+        scale = np.abs(u0[v]).sum() + np.abs(s[v]).sum()
+        assert abs(tot1 - tot0) <= 1e-12 * scale, (v, tot0, tot1)
+    if case == "rns":
+        assert s[3].sum() < u0[3].sum()     # fuel is consumed, never produced

@@ -1,0 +1,334 @@
+"""Benchmark: grid-point updates/s of the AT RK-stage right-hand side on GB300.
+
+One step = one full Runge-Kutta step (every stage kernel) over the whole
+domain of the workload, inputs resident in HBM.  Default workload: the
+reacting Navier-Stokes premixed flame, N = 16,384 FP64 points in 256 virtual
+PEs of 64, 6th-order central + AT6, classic RK4, delays uniform on {0..4}
+(Philox seed 0).  Its 512 KB state fits in L2, so L2 is flushed (a 256 MiB
+write) between timed steps, outside the timed intervals.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...      # the CPU oracle on host cores
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an
+independent replica (instance = rank): weak scaling, no collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (builder kwargs, description)
+    "rns-flame-n16384": dict(kind="rns", case="flame", n=16384, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003),
+    "rns-ignition-n16384": dict(kind="rns", case="ignition", n=16384, pe_size=64, mode="at", k_max=4, seed=0,
+                                dt=0.003),
+    "advdiff-n2048": dict(kind="advdiff", n=2048, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075),
+    "advdiff-n134217728": dict(kind="advdiff", n=1 << 27, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075),
+    "detonation-n16777216": dict(kind="detonation", n=1 << 24, pe_size=1024, mode="at", k_max=4, seed=0),
+    "rns-flame-n16777216": dict(kind="rns", case="flame", n=1 << 24, pe_size=64, mode="at", k_max=4, seed=0,
+                                dt=0.003),
+}
+DEFAULT = "rns-flame-n16384"
+NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal, at 2070 MHz boost
+
+# FP64 flops per point per stage, counted from the kernel's formulas (fma = 2;
+# a division, square root or exponential counted at the FP64 operations of
+# its software sequence).
+DIV, SQRT, EXP = 9, 9, 22
+FLOPS_PER_POINT_STAGE = {
+    # derive 23 + 1 div; stencils 90; RK4 update ~13; source 5 + 1 div + 1 exp
+    "rns": 23 + 90 + 13 + 5 + 2 * DIV + EXP,
+    # merged 5-tap stencil 9 (1 mul + 4 fma) + RK4 update ~3.25
+    "advdiff": 9 + 3.25,
+    # per point: derive 12 + 1 div, speed 4 + 1 div + 1 sqrt; per edge 8 WENO5
+    # reconstructions of 60 + 1 div and 5 split fluxes (10); lambda 2; flux
+    # difference 8; source 10 + 1 div + 1 exp; RK3 update ~4 x 4
+    "detonation": 12 + DIV + 4 + DIV + SQRT + 8 * (60 + DIV + 10) + 2 + 8 + 10 + DIV + EXP + 16,
+}
+
+
+def build_workload(name: str):
+    from paper_2204_01133_gb300 import workloads as W
+    kw = dict(WORKLOADS[name])
+    kind = kw.pop("kind")
+    if kind == "rns":
+        return kind, W.rns(**kw)
+    if kind == "advdiff":
+        return kind, W.advdiff(**kw)
+    return kind, W.detonation(**kw)
+
+
+class Clocks:
+    """nvidia-smi sampler running while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def fp64_probe(device: int):
+    import ctypes
+
+    import torch
+    path = os.path.join(ROOT, "paper_2204_01133_gb300", "libat_probe.so")
+    L = ctypes.CDLL(path)
+    L.at_probe_fp64_fma.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    st = torch.cuda.current_stream().cuda_stream
+    rc = L.at_probe_fp64_fma(device, ctypes.c_void_p(st), 4000, 5, ctypes.byref(tf), ctypes.byref(ms))
+    return tf.value if rc == 0 else None
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on this host's cores (single thread)."""
+    import oracle
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    kind, (pb, init) = build_workload(args.workload)
+    wl = describe(args.workload, pb)
+    n = pb["n"]
+    sample = "full domain, one oracle RK step per step"
+    if n > 65536:
+        # bounded sample: a window of whole PEs with the global PE indices
+        B = pb["pe_size"]
+        npe = max(1, 65536 // B)
+        pb = dict(pb, n=npe * B, pe_base=0, pe_total=n // B)
+        init = init[:, :npe * B].copy()
+        sample = "window of %d PEs (%d points) of the %d-point domain, one oracle RK step per step" % (
+            npe, npe * B, n)
+    o = oracle.Oracle(pb, init)
+    o.run(args.warmup)
+    t0 = time.perf_counter()
+    o.run(args.steps)
+    dt = time.perf_counter() - t0
+    pts = pb["n"]
+    value = pts * args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": "grid-pt updates/s", "value": value, "unit": "updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": wl,
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def describe(name, pb):
+    d = {"workload": name, "n": pb["n"], "pe_size": pb["pe_size"], "pes": pb["n"] // pb["pe_size"],
+         "pde": pb["pde"], "rk": pb["rk"], "mode": pb["mode"], "k_max": pb["k_max"], "dist": pb["dist"],
+         "seed": pb["seed"], "dt": pb["dt"]}
+    if pb["pde"] in ("advdiff", "rns"):
+        d["order"] = pb["order"]
+    else:
+        d["scheme"] = "weno5"
+    return d
+
+
+def cpu_baseline(pb, init, budget_s=12.0):
+    import oracle
+    n = pb["n"]
+    sample_pb, sample_init, what = pb, init, "full domain"
+    if n > 65536:
+        B = pb["pe_size"]
+        npe = max(1, 65536 // B)
+        sample_pb = dict(pb, n=npe * B, pe_base=0, pe_total=n // B)
+        sample_init = init[:, :npe * B].copy()
+        what = "window of %d PEs (%d points)" % (npe, npe * B)
+    o = oracle.Oracle(sample_pb, sample_init)
+    t0 = time.perf_counter()
+    o.run(2)
+    per = (time.perf_counter() - t0) / 2
+    steps = max(2, min(2000, int(budget_s / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    o.run(steps)
+    dt = time.perf_counter() - t0
+    return {"value": sample_pb["n"] * steps / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%s, %d RK steps, single thread" % (what, steps)}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2204_01133_gb300 import api, build
+    build.build()
+    kind, (pb, init) = build_workload(args.workload)
+    pb = dict(pb, instance=rank)
+    n = pb["n"]
+    S = api.STAGES[pb["rk"]]
+    nvar = api.NVAR[pb["pde"]]
+    state_bytes = 8 * nvar * n
+
+    s = api.Solver(pb, init, device=local)
+    l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = state_bytes < (512 << 20)
+    for _ in range(max(args.warmup, 3)):
+        if flush:
+            l2_flush.zero_()
+        s.step(1)
+    torch.cuda.synchronize()
+
+    peak_meas = fp64_probe(local) if rank == 0 else None
+
+    clocks = Clocks(local)
+    clocks.start()
+    launched0 = s.stats().kernels_launched
+    s.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        if flush:
+            l2_flush.zero_()
+        ev[k][0].record()
+        s.step(1)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    st = s.stats()
+    s.profile(False)
+    clk = clocks.stop()
+    launches = st.kernels_launched - launched0
+    stage_ms = st.stage_ms / max(st.launches_timed, 1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * args.steps / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: upload, steps, download
+    import ctypes
+    host_init = torch.from_numpy(np.ascontiguousarray(init)).pin_memory()
+    host_out = torch.empty_like(host_init).pin_memory()
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.check(api.lib().at_set_problem(s._h, ctypes.byref(s._pbs), ctypes.c_void_p(s.u.data_ptr()),
+                                       ctypes.c_void_p(host_init.data_ptr()), 0, ctypes.c_void_p(s.ws.data_ptr()),
+                                       s.ws.numel()))
+    s.set_delays()
+    s.run(e2e_steps)
+    api.check(api.lib().at_read(s._h, api.READ_STATE, ctypes.c_void_p(host_out.data_ptr()), state_bytes, 0))
+    e2e_s = time.perf_counter() - t0
+    e2e_val = n * e2e_steps / e2e_s
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = world * n * e2e_steps / float(t.item())
+
+    if rank == 0:
+        fl = FLOPS_PER_POINT_STAGE[kind] * n  # per launch
+        achieved = fl / (stage_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None, "kernel": "stage_%s" % kind,
+                "avg_launch_ms": stage_ms, "launches_timed": int(st.launches_timed),
+                "flops_per_launch": fl, "peak_kind": "nominal FP64 (1.25 TFLOP/s); see peak_measured",
+                "peak_measured": peak_meas, "frac_of_measured": (achieved / peak_meas) if peak_meas else None}
+        out = {
+            "metric": "grid-pt updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(describe(args.workload, pb), l2="flushed between timed steps" if flush
+                           else "inputs larger than L2", parallelism="replicas" if world > 1 else "single"),
+            "roofline": roof,
+            "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": state_bytes / e2e_steps,
+                    "d2h_bytes_per_step": state_bytes / e2e_steps,
+                    "note": "at_set_problem from pinned host + at_set_delays + at_run(K) + at_read to host"},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        if not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(pb, init)
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

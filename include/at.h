@@ -1,0 +1,162 @@
+/*
+ * at.h -- C ABI of libat_gb300.so: the asynchrony-tolerant (AT) Runge-Kutta
+ * stage right-hand side of Kumari, Aditya & Donzis, "Evaluation of finite
+ * difference based asynchronous PDE solver for reacting flows"
+ * (arXiv 2204.01133), on one NVIDIA GB300 (sm_103a), FP64 throughout.
+ *
+ * The problem statement follows the paper's (Sec. 2.1 and Sec. 5): a
+ * periodic 1-D domain of n points split into processing elements (PEs) of
+ * pe_size points; a PDE (Sec. 4, Eqs. ge and convEq; Sec. 2.1 Eq. heat and
+ * Sec. 3 advection); a stencil order (Sec. 2.2, Appendix A) or WENO5 (Sec. 3);
+ * an explicit RK scheme (Sec. 2.3, Eq. rk1); a largest delay and the delay
+ * probabilities (Sec. 2.1 and Table dels).  On one GPU the PEs are virtual:
+ * every PE reads the values beyond its edges from a device history ring of
+ * the neighbours' edge windows, at a delay drawn per (step, stage, PE,
+ * side) from Philox4x32-10 keyed by the seed, so runs are reproducible.
+ *
+ * Ownership: the caller owns every device buffer (state and workspace) and
+ * keeps it alive while the context uses it; the library owns only the opaque
+ * context.  Host pointers are used only for the duration of the call.  The
+ * CUDA stream is borrowed: every kernel and copy is enqueued on it.
+ *
+ * Errors: every call returns an at_status; nothing throws or aborts across
+ * the ABI.  at_last_error() returns a message for the calling thread's last
+ * failure.  Calls on one context are not thread-safe.
+ */
+#ifndef AT_GB300_H
+#define AT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct at_ctx at_ctx;
+
+typedef enum {
+    AT_OK = 0,
+    AT_EINVAL = -1,    /* an argument is out of range or inconsistent           */
+    AT_ENOMEM = -2,    /* the workspace is smaller than at_workspace_bytes()    */
+    AT_ECUDA = -3,     /* a CUDA call failed; at_last_error() has its message   */
+    AT_EUNSTABLE = -4, /* a non-finite value appeared in the state              */
+    AT_ETIMEOUT = -5,  /* a bounded device wait ran out (reserved)              */
+    AT_ESTATE = -6     /* calls out of order (problem, then delays, then steps) */
+} at_status;
+
+/* PDEs.  Physics constants prm[] for each (nondimensional, rho0 = T0 = 1,
+ * gas constant 1 so p = rho T):
+ *   AT_ADVDIFF  u_t + c u_x = a u_xx (Sec. 2.1 Eq. heat with advection)
+ *               prm = {c, a}; central stencils of order 2, 4 or 6
+ *   AT_RNS      reacting Navier-Stokes, Sec. 4 Eqs. ge / convEq with two
+ *               species (fuel -> product), constant mu, Prandtl Pr, Lewis Le
+ *               and a one-step Arrhenius rate A rho Y exp(-Ea/T);
+ *               state (rho, rho u, rho E, rho Y),
+ *               rho E = p/(gamma-1) + rho u^2/2 + q_c rho Y;
+ *               prm = {gamma, mu, Pr, Le, A, Ea, q_c}; central order 2/4/6
+ *   AT_EULER    reactive Euler (Sec. 5.6), WENO5 / AT-WENO5 fluxes with local
+ *               Lax-Friedrichs splitting (Sec. 3, Eqs. Csplit, wender);
+ *               prm = {gamma, A, Ea, Q, eps}
+ *   AT_ADV_WENO u_t + c u_x = 0 with WENO5 (the order test of Sec. 3);
+ *               prm = {c, eps}                                              */
+enum { AT_ADVDIFF = 0, AT_RNS = 1, AT_EULER = 2, AT_ADV_WENO = 3 };
+/* RK schemes (Sec. 2.3): Heun RK2 (Eq. rk2), Shu-Osher TVD RK3, classic RK4 */
+enum { AT_RK2 = 0, AT_RK3TVD = 1, AT_RK4 = 2 };
+/* Boundary treatment (Sec. 2.1, 2.2, 3): synchronous; standard scheme on
+ * delayed data (AS, Eq. async-fde / Eq. asweno); asynchrony-tolerant (AT,
+ * Eq. geDer, Appendix A, Eq. atRecon)                                        */
+enum { AT_SYNC = 0, AT_AS = 1, AT_AT = 2 };
+/* Delay distributions on {0..k_max}: uniform; table p_0..p_kmax (normalised
+ * by its sum); geometric p_k proportional to r (1-r)^k with r = prob[0]      */
+enum { AT_UNIFORM = 0, AT_TABLE = 1, AT_GEOMETRIC = 2 };
+/* at_read targets */
+enum { AT_READ_STATE = 0, AT_READ_DELAYS = 1, AT_READ_RING = 2, AT_READ_STATS = 3 };
+
+typedef struct {
+    int32_t pde;      /* AT_ADVDIFF | AT_RNS | AT_EULER | AT_ADV_WENO                 */
+    int32_t order;    /* 2 | 4 | 6 for central PDEs; ignored for WENO5                */
+    int32_t rk;       /* AT_RK2 | AT_RK3TVD | AT_RK4                                  */
+    int32_t pe_size;  /* points per PE, >= 2 x halo width (order/2, or 3 for WENO5)   */
+    int64_t n;        /* grid points, periodic, n % pe_size == 0, n < 2^31            */
+    double dx, dt;    /* grid spacing and the fixed time step                         */
+    double prm[16];   /* physics constants, see the PDE list above                    */
+} at_problem;
+
+typedef struct {
+    int32_t mode;      /* AT_SYNC | AT_AS | AT_AT                                     */
+    int32_t k_max;     /* largest delay in steps, 0..15 (the paper's L - 1)           */
+    int32_t dist;      /* AT_UNIFORM | AT_TABLE | AT_GEOMETRIC                        */
+    int32_t per_stage; /* 1: one delay per (step, stage); 0: one per step (Sec. 2.3)  */
+    double prob[16];   /* AT_TABLE: p_0..p_kmax; AT_GEOMETRIC: prob[0] = r            */
+    uint64_t seed;     /* Philox key                                                  */
+    uint32_t instance; /* fourth Philox counter word (independent instances)          */
+    uint32_t pad_;
+} at_delays;
+
+typedef struct {
+    int64_t level;     /* steps completed                                             */
+    int32_t status;    /* 0, or AT_EUNSTABLE once a non-finite state value appeared   */
+    int32_t stages;    /* RK stages per step                                          */
+    int32_t nvar;      /* state variables                                             */
+    int32_t halo;      /* halo width H                                                */
+    int32_t q;         /* temporal extrapolation degree of the AT halo                */
+    int32_t ring_levels;
+    int64_t kernels_launched; /* stage kernels enqueued by this context so far       */
+    int64_t launches_timed;   /* stage kernels timed since at_profile(ctx, 1)        */
+    double stage_ms;          /* summed device time of those launches (CUDA events)  */
+} at_stats;
+
+/* Create a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out is set on AT_OK. */
+int at_create(at_ctx** out, int device, void* cuda_stream);
+
+/* Device workspace bytes the problem needs with the given delay model
+ * (stage buffers, RK accumulator, history ring, delay log, status word).
+ * Returns 0 for an invalid description. */
+size_t at_workspace_bytes(const at_problem* pb, const at_delays* dl);
+
+/* Validate and bind the problem.  state_dev: the caller's [nvar][n] FP64
+ * device array that holds u^n (SoA, 16-byte aligned); init: initial state,
+ * [nvar][n] FP64, host (init_on_device = 0) or device memory, copied into
+ * state_dev on the stream (init may equal state_dev).  workspace_dev /
+ * workspace_bytes: caller-owned device memory, 256-byte aligned, of at least
+ * at_workspace_bytes(pb, dl) for every delay model used later.  Invalidates
+ * any previous delay model (call at_set_delays next). */
+int at_set_problem(at_ctx* ctx, const at_problem* pb, double* state_dev, const double* init,
+                   int init_on_device, void* workspace_dev, size_t workspace_bytes);
+
+/* Set the delay model, reset the step counter to 0 and seed the history ring
+ * with the edge windows of the current state (level 0). */
+int at_set_delays(at_ctx* ctx, const at_delays* dl);
+
+/* Enqueue nsteps full RK steps (S stage kernels each) on the stream. */
+int at_step(at_ctx* ctx, int64_t nsteps);
+
+/* at_step, then synchronise the stream and return AT_EUNSTABLE if a
+ * non-finite value appeared. */
+int at_run(at_ctx* ctx, int64_t nsteps);
+
+/* Copy out: AT_READ_STATE the [nvar][n] state; AT_READ_DELAYS the delays of
+ * the last completed step, [stages][P][2] uint8 (side 0 = left boundary of
+ * the PE); AT_READ_RING the whole history ring [R][S][P][2][H][nvar] FP64;
+ * AT_READ_STATS an at_stats (host only).  bytes must be at least the size of
+ * the target; the copy is synchronous. */
+int at_read(at_ctx* ctx, int what, void* dst, size_t bytes, int dst_on_device);
+
+/* Tracing: with enable = 1, every stage kernel at_step enqueues afterwards is
+ * bracketed by two CUDA events on the stream, and at_read(AT_READ_STATS)
+ * reports their number and summed device time (it synchronises the stream).
+ * enable = 0 stops timing; either call resets the totals.  At most 65,536
+ * launches are timed between two reads; later ones run untimed. */
+int at_profile(at_ctx* ctx, int enable);
+
+int at_destroy(at_ctx* ctx);
+
+/* message for the calling thread's last failed call ("" if none) */
+const char* at_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -44,6 +44,8 @@ class _Problem(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("per_stage", ctypes.c_int),
         ("instance", ctypes.c_uint32),
+        ("pe_base", ctypes.c_int64),
+        ("pe_total", ctypes.c_int64),
     ]
 
 
@@ -118,6 +120,8 @@ def _problem(pb: dict) -> _Problem:
     s.seed = int(pb.get("seed", 0))
     s.per_stage = int(pb.get("per_stage", 1))
     s.instance = int(pb.get("instance", 0))
+    s.pe_base = int(pb.get("pe_base", 0))
+    s.pe_total = int(pb.get("pe_total", 0))
     return s
 
 

@@ -129,7 +129,12 @@ int orc_draw(const orc_ctx* c, int64_t level, int stage, int64_t pe, int side)
 {
     const orc_problem* pb = &c->pb;
     uint32_t s_ctr = pb->per_stage ? (uint32_t)stage : 0u;
-    uint32_t ctr[4] = {(uint32_t)level, (uint32_t)pe, s_ctr | ((uint32_t)side << 8), pb->instance};
+    int64_t gpe = pe;
+    if (pb->pe_total > 0) {
+        gpe = (pb->pe_base + pe) % pb->pe_total;
+        if (gpe < 0) gpe += pb->pe_total;
+    }
+    uint32_t ctr[4] = {(uint32_t)level, (uint32_t)gpe, s_ctr | ((uint32_t)side << 8), pb->instance};
     uint32_t key[2] = {(uint32_t)(pb->seed & 0xffffffffu), (uint32_t)(pb->seed >> 32)};
     uint32_t out[4];
     orc_philox4x32_10(ctr, key, out);

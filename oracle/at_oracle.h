@@ -40,6 +40,9 @@ typedef struct {
     uint64_t seed;
     int per_stage;    /* 1: one draw per (step, stage); 0: one per step        */
     uint32_t instance;
+    int64_t pe_base;  /* global index of PE 0 when the problem is a window  */
+    int64_t pe_total; /* of a larger domain of pe_total PEs (0: no window);
+                         only the delay counter uses them                  */
 } orc_problem;
 
 typedef struct orc_ctx orc_ctx;

@@ -1,0 +1,225 @@
+"""Thin ctypes binding of libat_gb300.so (C ABI in include/at.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the library.  PyTorch supplies device memory (the state and the
+workspace are torch tensors owned by the :class:`Solver`) and the stream
+(``torch.cuda.current_stream()`` unless one is given).
+
+Loading fails loudly when the library has not been built; there is no CPU
+path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libat_gb300.so")
+
+AT_OK, AT_EINVAL, AT_ENOMEM, AT_ECUDA, AT_EUNSTABLE, AT_ETIMEOUT, AT_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PDE = {"advdiff": 0, "rns": 1, "euler": 2, "adv_weno": 3}
+RK = {"rk2": 0, "rk3tvd": 1, "rk4": 2}
+MODE = {"sync": 0, "as": 1, "at": 2}
+DIST = {"uniform": 0, "table": 1, "geometric": 2}
+READ_STATE, READ_DELAYS, READ_RING, READ_STATS = 0, 1, 2, 3
+NVAR = {"advdiff": 1, "adv_weno": 1, "rns": 4, "euler": 4}
+STAGES = {"rk2": 2, "rk3tvd": 3, "rk4": 4}
+
+# every symbol include/at.h declares
+SYMBOLS = ("at_create", "at_workspace_bytes", "at_set_problem", "at_set_delays", "at_step", "at_run",
+           "at_read", "at_profile", "at_destroy", "at_last_error")
+
+
+class AtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("at status %d: %s" % (code, msg))
+        self.code = code
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("pde", ctypes.c_int32), ("order", ctypes.c_int32), ("rk", ctypes.c_int32), ("pe_size", ctypes.c_int32),
+        ("n", ctypes.c_int64), ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("prm", ctypes.c_double * 16),
+    ]
+
+
+class Delays(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32), ("k_max", ctypes.c_int32), ("dist", ctypes.c_int32), ("per_stage", ctypes.c_int32),
+        ("prob", ctypes.c_double * 16), ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint32),
+        ("pad_", ctypes.c_uint32),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("level", ctypes.c_int64), ("status", ctypes.c_int32), ("stages", ctypes.c_int32), ("nvar", ctypes.c_int32),
+        ("halo", ctypes.c_int32), ("q", ctypes.c_int32), ("ring_levels", ctypes.c_int32),
+        ("kernels_launched", ctypes.c_int64), ("launches_timed", ctypes.c_int64), ("stage_ms", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libat_gb300.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libat_gb300.so is not built; run `python -m paper_2204_01133_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        vp = ctypes.c_void_p
+        L.at_create.argtypes = [P(vp), ctypes.c_int, vp]
+        L.at_workspace_bytes.argtypes = [P(Problem), P(Delays)]
+        L.at_workspace_bytes.restype = ctypes.c_size_t
+        L.at_set_problem.argtypes = [vp, P(Problem), vp, vp, ctypes.c_int, vp, ctypes.c_size_t]
+        L.at_set_delays.argtypes = [vp, P(Delays)]
+        L.at_step.argtypes = [vp, ctypes.c_int64]
+        L.at_run.argtypes = [vp, ctypes.c_int64]
+        L.at_read.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int]
+        L.at_destroy.argtypes = [vp]
+        L.at_profile.argtypes = [vp, ctypes.c_int]
+        L.at_last_error.restype = ctypes.c_char_p
+        for f in ("at_create", "at_set_problem", "at_set_delays", "at_step", "at_run", "at_read", "at_profile",
+                  "at_destroy"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def check(code: int) -> int:
+    if code != AT_OK:
+        raise AtError(code, lib().at_last_error().decode())
+    return code
+
+
+def problem_struct(pb: dict) -> Problem:
+    s = Problem()
+    s.pde = PDE[pb["pde"]]
+    s.order = int(pb.get("order", 4))
+    s.rk = RK[pb["rk"]]
+    s.pe_size = int(pb["pe_size"])
+    s.n = int(pb["n"])
+    s.dx = float(pb["dx"])
+    s.dt = float(pb["dt"])
+    for i, v in enumerate(pb.get("prm", [])):
+        s.prm[i] = float(v)
+    return s
+
+
+def delays_struct(pb: dict) -> Delays:
+    d = Delays()
+    d.mode = MODE[pb["mode"]]
+    d.k_max = int(pb["k_max"])
+    d.dist = DIST[pb.get("dist", "uniform")]
+    d.per_stage = int(pb.get("per_stage", 1))
+    for i, v in enumerate(pb.get("prob", [])):
+        d.prob[i] = float(v)
+    d.seed = int(pb.get("seed", 0))
+    d.instance = int(pb.get("instance", 0))
+    return d
+
+
+def workspace_bytes(pb: dict) -> int:
+    return int(lib().at_workspace_bytes(ctypes.byref(problem_struct(pb)), ctypes.byref(delays_struct(pb))))
+
+
+class Solver:
+    """One AT solve on one GPU.
+
+    ``Solver(pb, init)`` allocates the state and workspace as torch tensors on
+    ``device``, binds the problem (copying ``init`` from host or device) and
+    the delay model.  ``step(n)`` enqueues, ``run(n)`` also synchronises and
+    checks for non-finite values, ``state()`` returns the state tensor.
+    """
+
+    def __init__(self, pb: dict, init=None, device: int = 0, stream=None, state=None):
+        import torch
+
+        self.torch = torch
+        self.pb = dict(pb)
+        self.device = torch.device("cuda", device)
+        self.nvar = NVAR[pb["pde"]]
+        self.n = int(pb["n"])
+        self.P = self.n // int(pb["pe_size"])
+        self.stages = STAGES[pb["rk"]]
+        L = lib()
+        self._stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        check(L.at_create(ctypes.byref(h), device, ctypes.c_void_p(self._stream.cuda_stream)))
+        self._h = h
+        self._pbs = problem_struct(pb)
+        self._dls = delays_struct(pb)
+        nbytes = workspace_bytes(pb)
+        if nbytes == 0:
+            raise AtError(AT_EINVAL, lib().at_last_error().decode())
+        with torch.cuda.device(self.device):
+            self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.u = state if state is not None else torch.empty((self.nvar, self.n), dtype=torch.float64,
+                                                                  device=self.device)
+        self.set_problem(init)
+        self.set_delays()
+
+    # -- binding calls ----------------------------------------------------
+    def set_problem(self, init=None):
+        torch = self.torch
+        if init is None:
+            ptr, on_dev, keep = None, 1, None
+        elif isinstance(init, torch.Tensor) and init.is_cuda:
+            keep = init.to(torch.float64).contiguous()
+            ptr, on_dev = keep.data_ptr(), 1
+        else:
+            keep = np.ascontiguousarray(np.asarray(init, dtype=np.float64).reshape(self.nvar, self.n))
+            ptr, on_dev = keep.ctypes.data, 0
+        check(lib().at_set_problem(self._h, ctypes.byref(self._pbs), ctypes.c_void_p(self.u.data_ptr()),
+                                   ctypes.c_void_p(ptr) if ptr else None, on_dev,
+                                   ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel()))
+
+    def set_delays(self, **over):
+        if over:
+            self.pb.update(over)
+            self._dls = delays_struct(self.pb)
+        check(lib().at_set_delays(self._h, ctypes.byref(self._dls)))
+
+    def step(self, nsteps: int):
+        check(lib().at_step(self._h, int(nsteps)))
+
+    def run(self, nsteps: int):
+        check(lib().at_run(self._h, int(nsteps)))
+
+    def state(self):
+        return self.u
+
+    def read_state(self) -> np.ndarray:
+        out = np.empty((self.nvar, self.n), dtype=np.float64)
+        check(lib().at_read(self._h, READ_STATE, ctypes.c_void_p(out.ctypes.data), out.nbytes, 0))
+        return out
+
+    def read_delays(self) -> np.ndarray:
+        out = np.empty((self.stages, self.P, 2), dtype=np.uint8)
+        check(lib().at_read(self._h, READ_DELAYS, ctypes.c_void_p(out.ctypes.data), out.nbytes, 0))
+        return out
+
+    def profile(self, enable: bool = True):
+        check(lib().at_profile(self._h, 1 if enable else 0))
+
+    def stats(self) -> Stats:
+        s = Stats()
+        check(lib().at_read(self._h, READ_STATS, ctypes.byref(s), ctypes.sizeof(s), 0))
+        return s
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().at_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

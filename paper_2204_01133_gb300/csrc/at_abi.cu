@@ -1,0 +1,508 @@
+// at_abi.cu -- the C ABI of libat_gb300.so (declared in include/at.h).
+//
+// Host-side only: argument validation, carving the caller's workspace, the
+// delay threshold table, the temporal extrapolation weights, and the launch
+// sequence of the stage kernels.  Every step of the computation itself runs
+// in the kernels of at_stage.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/at.h"
+#include "at_device.cuh"
+
+size_t atk_stage_smem_bytes(int pde, int Tw, int H);
+int atk_stage_block(int pde, int Tw);
+cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaStream_t st);
+cudaError_t atk_launch_ring_seed(const atk::StageArgs& a, cudaStream_t st);
+cudaError_t atk_set_smem_limits();
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(AT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct Layout {
+    int nvar, H, q, S, R;
+    int64_t P;
+    int Tw, wpp;
+    size_t off_A, off_B, off_acc, off_ring, off_dlog, off_status, total;
+    size_t ring_elems;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int nvar_of(int pde) { return (pde == AT_RNS || pde == AT_EULER) ? 4 : 1; }
+bool is_weno(int pde) { return pde == AT_EULER || pde == AT_ADV_WENO; }
+int stages_of(int rk) { return rk == AT_RK2 ? 2 : (rk == AT_RK3TVD ? 3 : 4); }
+
+int check_problem(const at_problem* pb)
+{
+    if (!pb) return fail(AT_EINVAL, "problem is NULL");
+    if (pb->pde < 0 || pb->pde > 3) return fail(AT_EINVAL, "unknown pde %d", pb->pde);
+    if (pb->rk < 0 || pb->rk > 2) return fail(AT_EINVAL, "unknown rk %d", pb->rk);
+    if (!is_weno(pb->pde) && pb->order != 2 && pb->order != 4 && pb->order != 6)
+        return fail(AT_EINVAL, "central order must be 2, 4 or 6 (got %d)", pb->order);
+    if (pb->n <= 0 || pb->n >= ((int64_t)1 << 31)) return fail(AT_EINVAL, "n out of range");
+    if (pb->pe_size <= 0 || pb->n % pb->pe_size) return fail(AT_EINVAL, "n must be a multiple of pe_size");
+    const int H = is_weno(pb->pde) ? 3 : pb->order / 2;
+    if (pb->pe_size < 2 * H) return fail(AT_EINVAL, "pe_size must be at least %d", 2 * H);
+    if (!(pb->dx > 0.0) || !(pb->dt > 0.0)) return fail(AT_EINVAL, "dx and dt must be positive");
+    return AT_OK;
+}
+
+int check_delays(const at_delays* dl)
+{
+    if (!dl) return fail(AT_EINVAL, "delays is NULL");
+    if (dl->mode < 0 || dl->mode > 2) return fail(AT_EINVAL, "unknown mode %d", dl->mode);
+    if (dl->k_max < 0 || dl->k_max > AT_KMAX_LIMIT) return fail(AT_EINVAL, "k_max must be 0..15");
+    if (dl->dist < 0 || dl->dist > 2) return fail(AT_EINVAL, "unknown dist %d", dl->dist);
+    if (dl->dist == AT_TABLE) {
+        double s = 0.0;
+        for (int i = 0; i <= dl->k_max; ++i) {
+            if (!(dl->prob[i] >= 0.0)) return fail(AT_EINVAL, "negative probability");
+            s += dl->prob[i];
+        }
+        if (!(s > 0.0)) return fail(AT_EINVAL, "probabilities sum to zero");
+    }
+    if (dl->dist == AT_GEOMETRIC && !(dl->prob[0] > 0.0 && dl->prob[0] <= 1.0))
+        return fail(AT_EINVAL, "geometric parameter must be in (0, 1]");
+    return AT_OK;
+}
+
+// window length: the largest divisor of the PE size that is at most 256
+int window_of(int B)
+{
+    int best = 1;
+    for (int t = 1; t <= 256 && t <= B; ++t)
+        if (B % t == 0) best = t;
+    return best;
+}
+
+Layout layout(const at_problem* pb, const at_delays* dl)
+{
+    Layout L{};
+    L.nvar = nvar_of(pb->pde);
+    L.H = is_weno(pb->pde) ? 3 : pb->order / 2;
+    L.q = is_weno(pb->pde) ? 1 : pb->order / 2;
+    L.S = stages_of(pb->rk);
+    L.R = dl->k_max + L.q + 1;
+    L.P = pb->n / pb->pe_size;
+    L.Tw = window_of(pb->pe_size);
+    L.wpp = pb->pe_size / L.Tw;
+    const size_t field = sizeof(double) * (size_t)L.nvar * pb->n;
+    size_t off = 0;
+    L.off_A = off;
+    off = align256(off + field);
+    L.off_B = off;
+    off = align256(off + field);
+    L.off_acc = off;
+    if (pb->rk != AT_RK3TVD) off = align256(off + field);
+    L.ring_elems = (size_t)L.R * L.S * L.P * 2 * L.H * L.nvar;
+    L.off_ring = off;
+    off = align256(off + sizeof(double) * L.ring_elems);
+    L.off_dlog = off;
+    off = align256(off + (size_t)L.S * L.P * 2);
+    L.off_status = off;
+    off = align256(off + 256);
+    L.total = off;
+    return L;
+}
+
+// thresholds: T_i = floor(2^32 CDF(i)), CDF accumulated in index order
+void thresholds(const at_delays* dl, uint64_t* thr)
+{
+    double w[AT_KMAX_LIMIT + 1];
+    for (int i = 0; i <= dl->k_max; ++i) {
+        if (dl->dist == AT_UNIFORM) {
+            w[i] = 1.0;
+        } else if (dl->dist == AT_TABLE) {
+            w[i] = dl->prob[i];
+        } else {
+            double t = dl->prob[0];
+            for (int j = 0; j < i; ++j) t *= (1.0 - dl->prob[0]);
+            w[i] = t;
+        }
+    }
+    double total = 0.0;
+    for (int i = 0; i <= dl->k_max; ++i) total += w[i];
+    double cum = 0.0;
+    for (int i = 0; i < dl->k_max; ++i) {
+        cum += w[i];
+        double t = std::floor((cum / total) * 4294967296.0);
+        if (t < 0.0) t = 0.0;
+        if (t > 4294967296.0) t = 4294967296.0;
+        thr[i] = (uint64_t)t;
+    }
+}
+
+// extrapolation weights from levels -k..-k-q to 0 (exact integer ratios)
+void extrap_weights(int q, int k, double* w)
+{
+    for (int l = 0; l <= q; ++l) {
+        long long num = 1, den = 1;
+        for (int m = 0; m <= q; ++m) {
+            if (m == l) continue;
+            num *= (long long)(k + m);
+            den *= (long long)(m - l);
+        }
+        w[l] = (double)num / (double)den;
+    }
+}
+
+} // namespace
+
+struct at_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool have_problem = false, have_delays = false;
+    at_problem pb{};
+    at_delays dl{};
+    double* state = nullptr;
+    unsigned char* ws = nullptr;
+    size_t ws_bytes = 0;
+    Layout L{};
+    atk::StageArgs base{};
+    int64_t level = 0;
+    int64_t launched = 0;
+    // tracing (at_profile)
+    bool profile = false;
+    std::vector<cudaEvent_t> ev;  // pairs: ev[2i] before, ev[2i+1] after launch i
+    size_t ev_used = 0;
+    int64_t timed = 0;
+    double timed_ms = 0.0;
+};
+
+namespace {
+const size_t kMaxTimed = 65536;
+
+cudaError_t record(at_ctx* c, bool before)
+{
+    if (!c->profile) return cudaSuccess;
+    if (before && c->ev_used / 2 >= kMaxTimed) return cudaSuccess;
+    if (!before && (c->ev_used % 2) == 0) return cudaSuccess;  // the launch was not timed
+    if (c->ev_used == c->ev.size()) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        c->ev.push_back(e);
+    }
+    return cudaEventRecord(c->ev[c->ev_used++], c->stream);
+}
+
+cudaError_t harvest(at_ctx* c)
+{
+    if (c->ev_used < 2) {
+        c->ev_used = 0;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaEventSynchronize(c->ev[c->ev_used - 1]);
+    if (e != cudaSuccess) return e;
+    for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
+        if (e != cudaSuccess) return e;
+        c->timed_ms += ms;
+        ++c->timed;
+    }
+    c->ev_used = 0;
+    return cudaSuccess;
+}
+} // namespace
+
+extern "C" {
+
+const char* at_last_error(void) { return g_err; }
+
+int at_create(at_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return fail(AT_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(AT_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    e = atk_set_smem_limits();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    at_ctx* c = new (std::nothrow) at_ctx;
+    if (!c) return fail(AT_ENOMEM, "host allocation failed");
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    *out = c;
+    g_err[0] = 0;
+    return AT_OK;
+}
+
+size_t at_workspace_bytes(const at_problem* pb, const at_delays* dl)
+{
+    if (check_problem(pb) != AT_OK || check_delays(dl) != AT_OK) return 0;
+    return layout(pb, dl).total;
+}
+
+int at_set_problem(at_ctx* c, const at_problem* pb, double* state_dev, const double* init, int init_on_device,
+                   void* workspace_dev, size_t workspace_bytes)
+{
+    if (!c) return fail(AT_EINVAL, "context is NULL");
+    int st = check_problem(pb);
+    if (st != AT_OK) return st;
+    if (!state_dev || !workspace_dev) return fail(AT_EINVAL, "state and workspace must be device pointers");
+    if (((uintptr_t)state_dev & 15) || ((uintptr_t)workspace_dev & 255))
+        return fail(AT_EINVAL, "state must be 16-byte and workspace 256-byte aligned");
+    at_delays probe{};
+    probe.mode = AT_SYNC;
+    probe.k_max = 0;
+    if (workspace_bytes < layout(pb, &probe).total)
+        return fail(AT_ENOMEM, "workspace of %zu bytes is below the %zu bytes needed", workspace_bytes,
+                    layout(pb, &probe).total);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    c->pb = *pb;
+    c->state = state_dev;
+    c->ws = (unsigned char*)workspace_dev;
+    c->ws_bytes = workspace_bytes;
+    c->have_problem = true;
+    c->have_delays = false;
+    const size_t bytes = sizeof(double) * (size_t)nvar_of(pb->pde) * pb->n;
+    if (init && init != state_dev) {
+        e = cudaMemcpyAsync(state_dev, init, bytes, init_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy of the initial state");
+        if (!init_on_device) {
+            e = cudaStreamSynchronize(c->stream);  // the host buffer is borrowed for this call only
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+        }
+    }
+    g_err[0] = 0;
+    return AT_OK;
+}
+
+int at_set_delays(at_ctx* c, const at_delays* dl)
+{
+    if (!c) return fail(AT_EINVAL, "context is NULL");
+    if (!c->have_problem) return fail(AT_ESTATE, "at_set_problem must come first");
+    int st = check_delays(dl);
+    if (st != AT_OK) return st;
+    Layout L = layout(&c->pb, dl);
+    if (L.total > c->ws_bytes)
+        return fail(AT_ENOMEM, "workspace of %zu bytes is below the %zu bytes this delay model needs", c->ws_bytes,
+                    L.total);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    c->dl = *dl;
+    c->L = L;
+    atk::StageArgs& a = c->base;
+    a = atk::StageArgs{};
+    a.acc = (double*)(c->ws + L.off_acc);
+    a.ring = (double*)(c->ws + L.off_ring);
+    a.dlog = (uint8_t*)(c->ws + L.off_dlog);
+    a.status = (int*)(c->ws + L.off_status);
+    a.N = c->pb.n;
+    a.P = L.P;
+    a.B = c->pb.pe_size;
+    a.Tw = L.Tw;
+    a.wpp = L.wpp;
+    a.S = L.S;
+    a.R = L.R;
+    a.H = L.H;
+    a.q = L.q;
+    a.nvar = L.nvar;
+    a.mode = dl->mode;
+    a.kmax = dl->k_max;
+    a.per_stage = dl->per_stage ? 1 : 0;
+    a.rk = c->pb.rk;
+    a.instance = dl->instance;
+    a.key0 = (uint32_t)(dl->seed & 0xffffffffu);
+    a.key1 = (uint32_t)(dl->seed >> 32);
+    a.dt = c->pb.dt;
+    thresholds(dl, a.thr);
+    for (int k = 0; k <= dl->k_max; ++k) extrap_weights(L.q, k, a.w[k]);
+    for (int i = 0; i < 16; ++i) a.prm[i] = c->pb.prm[i];
+    const double dx = c->pb.dx;
+    if (!is_weno(c->pb.pde)) {
+        static const double d1_2[3] = {-1, 0, 1}, d2_2[3] = {1, -2, 1};
+        static const double d1_4[5] = {1, -8, 0, 8, -1}, d2_4[5] = {-1, 16, -30, 16, -1};
+        static const double d1_6[7] = {-1, 9, -45, 0, 45, -9, 1}, d2_6[7] = {2, -27, 270, -490, 270, -27, 2};
+        const double* d1 = c->pb.order == 2 ? d1_2 : (c->pb.order == 4 ? d1_4 : d1_6);
+        const double* d2 = c->pb.order == 2 ? d2_2 : (c->pb.order == 4 ? d2_4 : d2_6);
+        const double den1 = c->pb.order == 2 ? 2.0 : (c->pb.order == 4 ? 12.0 : 60.0);
+        const double den2 = c->pb.order == 2 ? 1.0 : (c->pb.order == 4 ? 12.0 : 180.0);
+        for (int o = 0; o <= 2 * L.H; ++o) {
+            a.c1[o] = -d1[o] / (den1 * dx);
+            a.c2[o] = d2[o] / (den2 * dx * dx);
+        }
+        if (c->pb.pde == AT_ADVDIFF) {
+            const double cc = c->pb.prm[0], aa = c->pb.prm[1];
+            for (int o = 0; o <= 2 * L.H; ++o)
+                a.cm[o] = -cc * d1[o] / (den1 * dx) + aa * d2[o] / (den2 * dx * dx);
+        } else {
+            const double gam = c->pb.prm[0], mu = c->pb.prm[1], Pr = c->pb.prm[2], Le = c->pb.prm[3];
+            const double cp = gam / (gam - 1.0);
+            const double lam = mu * cp / Pr;
+            a.k0 = 4.0 / 3.0 * mu;
+            a.k1 = 2.0 / 3.0 * mu;
+            a.k2 = lam;
+            a.k3 = lam / (cp * Le);
+        }
+    } else {
+        a.k0 = 1.0 / dx;
+    }
+    // reset the run: zero ring, delay log and status, then seed level 0
+    e = cudaMemsetAsync(a.ring, 0, sizeof(double) * L.ring_elems, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.dlog, 0, (size_t)L.S * L.P * 2, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.status, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
+    atk::StageArgs s = a;
+    s.u = c->state;
+    e = atk_launch_ring_seed(s, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ring seed launch");
+    c->level = 0;
+    c->have_delays = true;
+    g_err[0] = 0;
+    return AT_OK;
+}
+
+int at_step(at_ctx* c, int64_t nsteps)
+{
+    if (!c) return fail(AT_EINVAL, "context is NULL");
+    if (!c->have_problem || !c->have_delays) return fail(AT_ESTATE, "at_set_problem and at_set_delays must come first");
+    if (nsteps < 0) return fail(AT_EINVAL, "nsteps must be >= 0");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    const Layout& L = c->L;
+    double* A = (double*)(c->ws + L.off_A);
+    double* Bf = (double*)(c->ws + L.off_B);
+    double* u = c->state;
+    for (int64_t i = 0; i < nsteps; ++i) {
+        atk::StageArgs a = c->base;
+        a.level = c->level;
+        a.u = u;
+        for (int s = 0; s < L.S; ++s) {
+            a.stage = s;
+            // stencil source and output of each stage (ping-pong A/B, last stage in place)
+            const double* X = (s == 0) ? u : ((s % 2 == 1) ? A : Bf);
+            double* Y = (s == L.S - 1) ? u : ((s % 2 == 0) ? A : Bf);
+            a.X = X;
+            a.Y = Y;
+            e = record(c, true);
+            if (e == cudaSuccess) e = atk_launch_stage(a, c->pb.pde, c->pb.order, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+            e = record(c, false);
+            if (e != cudaSuccess) return cuda_fail(e, "profiling event");
+            ++c->launched;
+        }
+        ++c->level;
+    }
+    g_err[0] = 0;
+    return AT_OK;
+}
+
+int at_run(at_ctx* c, int64_t nsteps)
+{
+    int st = at_step(c, nsteps);
+    if (st != AT_OK) return st;
+    int status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, c->base.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "at_run synchronisation");
+    if (status) return fail(AT_EUNSTABLE, "a non-finite value appeared in the state");
+    return AT_OK;
+}
+
+int at_read(at_ctx* c, int what, void* dst, size_t bytes, int dst_on_device)
+{
+    if (!c || !dst) return fail(AT_EINVAL, "context or destination is NULL");
+    if (!c->have_problem) return fail(AT_ESTATE, "no problem is set");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    size_t need = 0;
+    const void* src = nullptr;
+    if (what == AT_READ_STATE) {
+        need = sizeof(double) * (size_t)nvar_of(c->pb.pde) * c->pb.n;
+        src = c->state;
+    } else if (what == AT_READ_DELAYS || what == AT_READ_RING) {
+        if (!c->have_delays) return fail(AT_ESTATE, "no delay model is set");
+        if (what == AT_READ_DELAYS) {
+            need = (size_t)c->L.S * c->L.P * 2;
+            src = c->base.dlog;
+        } else {
+            need = sizeof(double) * c->L.ring_elems;
+            src = c->base.ring;
+        }
+    } else if (what == AT_READ_STATS) {
+        if (dst_on_device) return fail(AT_EINVAL, "stats are read to host memory");
+        if (bytes < sizeof(at_stats)) return fail(AT_EINVAL, "destination too small");
+        at_stats s{};
+        int status = 0;
+        if (c->have_delays) {
+            e = cudaMemcpyAsync(&status, c->base.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "status read");
+        }
+        s.level = c->level;
+        s.status = status ? AT_EUNSTABLE : 0;
+        s.stages = stages_of(c->pb.rk);
+        s.nvar = nvar_of(c->pb.pde);
+        s.halo = is_weno(c->pb.pde) ? 3 : c->pb.order / 2;
+        s.q = is_weno(c->pb.pde) ? 1 : c->pb.order / 2;
+        s.ring_levels = c->have_delays ? c->L.R : 0;
+        s.kernels_launched = c->launched;
+        e = harvest(c);
+        if (e != cudaSuccess) return cuda_fail(e, "profiling events");
+        s.launches_timed = c->timed;
+        s.stage_ms = c->timed_ms;
+        std::memcpy(dst, &s, sizeof s);
+        return AT_OK;
+    } else {
+        return fail(AT_EINVAL, "unknown read target %d", what);
+    }
+    if (bytes < need) return fail(AT_EINVAL, "destination of %zu bytes is below the %zu bytes needed", bytes, need);
+    e = cudaMemcpyAsync(dst, src, need, kind, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "at_read copy");
+    return AT_OK;
+}
+
+int at_profile(at_ctx* c, int enable)
+{
+    if (!c) return fail(AT_EINVAL, "context is NULL");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = harvest(c);
+    if (e != cudaSuccess) return cuda_fail(e, "profiling events");
+    c->profile = enable != 0;
+    c->timed = 0;
+    c->timed_ms = 0.0;
+    return AT_OK;
+}
+
+int at_destroy(at_ctx* c)
+{
+    if (!c) return AT_OK;
+    cudaSetDevice(c->device);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    delete c;
+    return AT_OK;
+}
+
+} // extern "C"

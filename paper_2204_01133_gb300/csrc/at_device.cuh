@@ -1,0 +1,175 @@
+// at_device.cuh -- device-side pieces of the AT stage kernels (sm_103a, FP64).
+//
+// Everything a stage kernel needs that is not the kernel itself: the launch
+// argument block, the Philox4x32-10 delay draw, the temporal extrapolation of
+// halo values from the history ring, and the per-PDE derived quantities.
+#pragma once
+#include <cstdint>
+
+#define AT_KMAX_LIMIT 15
+#define AT_QMAX 3
+#define AT_HMAX 3
+#define AT_NDER 8
+
+namespace atk {
+
+enum { ADVDIFF = 0, RNS = 1, EULER = 2, ADV_WENO = 3 };
+enum { RK2 = 0, RK3TVD = 1, RK4 = 2 };
+enum { SYNC = 0, AS = 1, AT = 2 };
+
+// Everything one stage launch needs, passed by value (well under the
+// kernel-parameter limit).
+struct StageArgs {
+    const double* X;   // stencil source: the stage argument U^{n,(s)}   [nvar][N]
+    const double* u;   // u^n (read pointwise)                            [nvar][N]
+    double* acc;       // RK accumulator (RK2, RK4)                       [nvar][N]
+    double* Y;         // output: next stage argument, or u^{n+1} in place [nvar][N]
+    double* ring;      // edge windows of stage arguments [R][S][P][2][H][nvar]
+    uint8_t* dlog;     // delays of this step [S][P][2]
+    int* status;       // bit 0: a non-finite value was written
+    int64_t N, P;
+    int64_t level;     // n: the step being computed
+    int B, Tw, wpp;    // PE size, window length, windows per PE
+    int stage, S, R, H, q, nvar;
+    int mode, kmax, per_stage, rk;
+    uint32_t instance, key0, key1;
+    double dt;
+    uint64_t thr[AT_KMAX_LIMIT];              // Philox word-0 thresholds
+    double w[AT_KMAX_LIMIT + 1][AT_QMAX + 1]; // extrapolation weights by delay
+    double c1[2 * AT_HMAX + 1];               // -d1_m / dx  (central)
+    double c2[2 * AT_HMAX + 1];               //  d2_m / dx^2 (central)
+    double cm[2 * AT_HMAX + 1];               // merged advection-diffusion taps
+    double prm[16];                           // physics constants (see at.h)
+    double k0, k1, k2, k3;                    // derived physics constants
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
+// with a Weyl key schedule; only output word 0 is used.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t philox_w0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c0;
+}
+
+// Delay seen by PE `pe` at its `side` (0 left, 1 right) for this stage,
+// clamped so that no level below 0 is ever read.
+__device__ __forceinline__ int keff(const StageArgs& a, int64_t pe, int side)
+{
+    if (a.mode == SYNC) return 0;
+    const uint32_t sc = a.per_stage ? (uint32_t)a.stage : 0u;
+    const uint32_t x = philox_w0((uint32_t)a.level, (uint32_t)pe, sc | ((uint32_t)side << 8), a.instance,
+                                 a.key0, a.key1);
+    int k = 0;
+    for (int i = 0; i < a.kmax; ++i) k += ((uint64_t)x >= a.thr[i]) ? 1 : 0;
+    const int qq = (a.mode == AT) ? a.q : 0;
+    int64_t avail = a.level - qq;
+    if (avail < 0) avail = 0;
+    return (int64_t)k < avail ? k : (int)avail;
+}
+
+__device__ __forceinline__ int64_t ring_index(const StageArgs& a, int64_t level, int stage, int64_t pe, int side,
+                                              int h, int v)
+{
+    int64_t r = level % a.R;
+    if (r < 0) r += a.R;
+    return ((((r * a.S + stage) * a.P + pe) * 2 + side) * a.H + h) * a.nvar + v;
+}
+
+// ---------------------------------------------------------------------------
+// Physics: derived quantities of one state vector.  Coefficients that only
+// scale a derived quantity are folded in here (they commute with the
+// temporal extrapolation, which is linear).
+// ---------------------------------------------------------------------------
+template <int PDE>
+struct Phys;
+
+// u_t + c u_x = a u_xx: the only derived quantity is u itself.
+template <>
+struct Phys<ADVDIFF> {
+    static constexpr int NV = 1, ND = 1;
+    __device__ static void derive(const StageArgs&, const double* Q, double* g) { g[0] = Q[0]; }
+};
+
+// Reacting Navier-Stokes: g = [rho u, rho u^2 + p, u (rho E + p), rho u Y,
+// (4/3) mu u, (2/3) mu u^2 + lam T + q_c rhoD Y, rhoD Y, T].
+// k0 = (4/3) mu, k1 = (2/3) mu, k2 = lam, k3 = rhoD.
+template <>
+struct Phys<RNS> {
+    static constexpr int NV = 4, ND = 8;
+    __device__ static void derive(const StageArgs& a, const double* Q, double* g)
+    {
+        const double gm1 = a.prm[0] - 1.0, qc = a.prm[6];
+        const double rinv = 1.0 / Q[0];
+        const double u = Q[1] * rinv;
+        const double p = gm1 * (Q[2] - fma(0.5 * Q[1], u, qc * Q[3]));
+        const double T = p * rinv;
+        const double Y = Q[3] * rinv;
+        g[0] = Q[1];
+        g[1] = fma(Q[1], u, p);
+        g[2] = u * (Q[2] + p);
+        g[3] = Q[3] * u;
+        g[4] = a.k0 * u;
+        g[5] = fma(a.k1 * u, u, fma(a.k2, T, qc * a.k3 * Y));
+        g[6] = a.k3 * Y;
+        g[7] = T;
+    }
+};
+
+// Reactive Euler, WENO form: g = [C/2 (4), Q (4)], C = (rho u, rho u^2 + p,
+// u (rho E + p), rho u Y); the split fluxes are C/2 +- (lam/2) Q.
+template <>
+struct Phys<EULER> {
+    static constexpr int NV = 4, ND = 8;
+    __device__ static double pressure(const StageArgs& a, const double* Q, double u)
+    {
+        return (a.prm[0] - 1.0) * (Q[2] - fma(0.5 * Q[1], u, a.prm[3] * Q[3]));
+    }
+    __device__ static void derive(const StageArgs& a, const double* Q, double* g)
+    {
+        const double u = Q[1] / Q[0];
+        const double p = pressure(a, Q, u);
+        g[0] = 0.5 * Q[1];
+        g[1] = 0.5 * fma(Q[1], u, p);
+        g[2] = 0.5 * (u * (Q[2] + p));
+        g[3] = 0.5 * (Q[3] * u);
+        g[4] = Q[0];
+        g[5] = Q[1];
+        g[6] = Q[2];
+        g[7] = Q[3];
+    }
+    __device__ static double speed(const StageArgs& a, const double* Q)
+    {
+        const double rinv = 1.0 / Q[0];
+        const double u = Q[1] * rinv;
+        const double p = pressure(a, Q, u);
+        return fabs(u) + sqrt(a.prm[0] * p * rinv);
+    }
+};
+
+// Scalar linear advection, WENO form: g = [c u / 2, u].
+template <>
+struct Phys<ADV_WENO> {
+    static constexpr int NV = 1, ND = 2;
+    __device__ static void derive(const StageArgs& a, const double* Q, double* g)
+    {
+        g[0] = 0.5 * a.prm[0] * Q[0];
+        g[1] = Q[0];
+    }
+    __device__ static double speed(const StageArgs& a, const double*) { return fabs(a.prm[0]); }
+};
+
+} // namespace atk

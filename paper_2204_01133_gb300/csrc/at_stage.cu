@@ -1,0 +1,365 @@
+// at_stage.cu -- the RK-stage kernels of the asynchrony-tolerant solver.
+//
+// One launch evaluates one Runge-Kutta stage over the whole domain.  A CTA
+// owns a window of Tw consecutive points of one virtual PE (Tw divides the PE
+// size, so a window never straddles a PE edge).  Per CTA:
+//
+//  1. fill: the derived quantities (fluxes, velocity, temperature, ...) of
+//     the Tw + 2H points the window's stencils touch are staged in shared
+//     memory.  Points inside the PE are read from the stage-argument field.
+//     Points beyond the PE edge are buffer points (Sec. 2.1, Fig. 1): the
+//     thread draws the delay k of that PE boundary from Philox, reads the
+//     neighbour's edge window at levels n-k-l from the history ring and
+//     combines the derived quantities with the temporal extrapolation weights
+//     (AT: Eq. at1 / Appendix A / Eq. atRecon; AS: the plain delayed value).
+//  2. compute: central stencils (Sec. 2.2; the AT scheme is the standard one
+//     on the extrapolated halo) or WENO5 / AT-WENO5 reconstructions with
+//     local Lax-Friedrichs splitting (Sec. 3, Eqs. Csplit, wender, omg,
+//     betaS), the Arrhenius source fused in.
+//  3. update: the RK update of this stage (Sec. 2.3), the edge points of the
+//     new stage argument pushed into the history ring (the per-step message
+//     of S stages x stencil of Sec. 2.3), a non-finite check.
+//
+// All arithmetic is FP64.  Stencil and RK coefficients arrive pre-scaled in
+// the argument block.
+#include <cuda_runtime.h>
+
+#include "at_device.cuh"
+
+namespace atk {
+
+// ---------------------------------------------------------------------------
+// 1. fill the window
+// ---------------------------------------------------------------------------
+template <int PDE, bool WENO>
+__device__ __forceinline__ void fill_window(const StageArgs& a, double* __restrict__ G, double* __restrict__ SP,
+                                            int64_t pe, int64_t t0, int W2)
+{
+    using P = Phys<PDE>;
+    constexpr int NV = P::NV, ND = P::ND;
+    const int64_t lo = pe * a.B, hi = lo + a.B;
+    for (int i = threadIdx.x; i < W2; i += blockDim.x) {
+        const int64_t m = t0 - a.H + i;
+        double g[ND];
+        double sp = 0.0;
+        double Q[NV];
+        if (m >= lo && m < hi) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Q[v] = a.X[v * a.N + m];
+            P::derive(a, Q, g);
+            if constexpr (WENO) sp = P::speed(a, Q);
+        } else {
+            // buffer point: the neighbour's edge window, delayed and extrapolated
+            const int side = (m < lo) ? 0 : 1;
+            const int64_t nbr = side == 0 ? (pe == 0 ? a.P - 1 : pe - 1) : (pe == a.P - 1 ? 0 : pe + 1);
+            const int h = side == 0 ? (int)(m - (lo - a.H)) : (int)(m - hi);
+            const int nside = 1 - side;
+            const int k = keff(a, pe, side);
+            if (h == 0) a.dlog[((int64_t)a.stage * a.P + pe) * 2 + side] = (uint8_t)k;
+            const int nw = (a.mode == AT) ? a.q + 1 : 1;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) g[d] = 0.0;
+            for (int l = 0; l < nw; ++l) {
+                const double wl = (a.mode == AT) ? a.w[k][l] : 1.0;
+                if (wl == 0.0) continue;  // a level with weight 0 is not part of the scheme
+                const int64_t base = ring_index(a, a.level - k - l, a.stage, nbr, nside, h, 0);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) Q[v] = a.ring[base + v];
+                double gl[ND];
+                P::derive(a, Q, gl);
+#pragma unroll
+                for (int d = 0; d < ND; ++d) g[d] = fma(wl, gl[d], g[d]);
+                if constexpr (WENO) {
+                    if (l == 0) sp = P::speed(a, Q);  // wave speed at level n-k, not extrapolated
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) G[d * W2 + i] = g[d];
+        if constexpr (WENO) SP[i] = sp;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. RK update of this stage, ring push, non-finite check
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rk_update(const StageArgs& a, int v, int64_t j, int jpe, int64_t pe, double K,
+                                          double x)
+{
+    const int64_t idx = v * a.N + j;
+    const double dt = a.dt;
+    double y;
+    if (a.rk == RK4) {
+        const double un = a.u[idx];
+        if (a.stage == 0) {
+            a.acc[idx] = K;
+            y = fma(0.5 * dt, K, un);
+        } else if (a.stage < 3) {
+            a.acc[idx] = fma(2.0, K, a.acc[idx]);
+            y = fma(a.stage == 1 ? 0.5 * dt : dt, K, un);
+        } else {
+            y = fma(dt * (1.0 / 6.0), a.acc[idx] + K, un);
+        }
+    } else if (a.rk == RK3TVD) {
+        const double xs = fma(dt, K, x);
+        if (a.stage == 0) {
+            y = xs;
+        } else if (a.stage == 1) {
+            y = fma(0.75, a.u[idx], 0.25 * xs);
+        } else {
+            y = fma(1.0 / 3.0, a.u[idx], (2.0 / 3.0) * xs);
+        }
+    } else {  // RK2 (Heun)
+        const double un = a.u[idx];
+        if (a.stage == 0) {
+            a.acc[idx] = K;
+            y = fma(dt, K, un);
+        } else {
+            y = fma(0.5 * dt, a.acc[idx] + K, un);
+        }
+    }
+    a.Y[idx] = y;
+    if (!isfinite(y)) atomicOr(a.status, 1);
+    int side = -1, h = 0;
+    if (jpe < a.H) {
+        side = 0;
+        h = jpe;
+    } else if (jpe >= a.B - a.H) {
+        side = 1;
+        h = jpe - (a.B - a.H);
+    }
+    if (side >= 0) {
+        const bool last = (a.stage == a.S - 1);
+        a.ring[ring_index(a, last ? a.level + 1 : a.level, last ? 0 : a.stage + 1, pe, side, h, v)] = y;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// central stencils: advection-diffusion and reacting Navier-Stokes
+// ---------------------------------------------------------------------------
+template <int PDE, int H>
+__global__ void __launch_bounds__(256) stage_central(const StageArgs a)
+{
+    using P = Phys<PDE>;
+    constexpr int NV = P::NV;
+    extern __shared__ double sm[];
+    const int W2 = a.Tw + 2 * H;
+    double* G = sm;
+    const int64_t win = blockIdx.x;
+    const int64_t pe = win / a.wpp;
+    const int chunk = (int)(win - pe * a.wpp);
+    const int64_t t0 = pe * a.B + (int64_t)chunk * a.Tw;
+    fill_window<PDE, false>(a, G, nullptr, pe, t0, W2);
+    __syncthreads();
+    const int items = NV * a.Tw;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int v = it / a.Tw;
+        const int jl = it - v * a.Tw;
+        const int64_t j = t0 + jl;
+        const int c = jl + H;
+        double K = 0.0, x = 0.0;
+        if constexpr (PDE == ADVDIFF) {
+#pragma unroll
+            for (int o = -H; o <= H; ++o) K = fma(a.cm[o + H], G[c + o], K);
+            x = G[c];
+        } else {
+            const double* F = G + v * W2;
+#pragma unroll
+            for (int o = -H; o <= H; ++o)
+                if (o != 0) K = fma(a.c1[o + H], F[c + o], K);
+            if (v > 0) {
+                const double* D = G + (3 + v) * W2;  // (4/3) mu u | energy diffusion | rhoD Y
+#pragma unroll
+                for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[c + o], K);
+            }
+            x = a.X[v * a.N + j];
+            if (v == 3) K = fma(-a.prm[4] * x, exp(-a.prm[5] / G[7 * W2 + c]), K);
+        }
+        rk_update(a, v, j, chunk * a.Tw + jl, pe, K, x);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// WENO5-JS reconstruction at the right edge of f[2] from f[0..4]
+// (candidates of Eq. atRecon at k = 0, ideal weights {1/10, 3/5, 3/10},
+// indicators of Eq. betaS, weights of Eq. omg with power 2).  The three
+// normalised weights share one division: alpha_i ~ gamma_i prod_{j!=i} d_j^2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double weno5(double f0, double f1, double f2, double f3, double f4, double eps)
+{
+    const double p0 = fma(2.0, f0, fma(-7.0, f1, 11.0 * f2));
+    const double p1 = fma(-1.0, f1, fma(5.0, f2, 2.0 * f3));
+    const double p2 = fma(2.0, f2, fma(5.0, f3, -f4));
+    const double s0 = fma(-2.0, f1, f0) + f2, r0 = fma(-4.0, f1, f0) + 3.0 * f2;
+    const double s1 = fma(-2.0, f2, f1) + f3, r1 = f1 - f3;
+    const double s2 = fma(-2.0, f3, f2) + f4, r2 = fma(-4.0, f3, 3.0 * f2) + f4;
+    const double d0 = eps + fma(13.0 / 12.0 * s0, s0, 0.25 * r0 * r0);
+    const double d1 = eps + fma(13.0 / 12.0 * s1, s1, 0.25 * r1 * r1);
+    const double d2 = eps + fma(13.0 / 12.0 * s2, s2, 0.25 * r2 * r2);
+    const double e0 = d0 * d0, e1 = d1 * d1, e2 = d2 * d2;
+    const double a0 = 0.1 * (e1 * e2), a1 = 0.6 * (e0 * e2), a2 = 0.3 * (e0 * e1);
+    const double num = fma(a0, p0, fma(a1, p1, a2 * p2));
+    return num / (6.0 * (a0 + a1 + a2));
+}
+
+// ---------------------------------------------------------------------------
+// WENO5 / AT-WENO5 fluxes: reactive Euler and scalar advection
+// ---------------------------------------------------------------------------
+template <int PDE>
+__global__ void __launch_bounds__(256) stage_weno(const StageArgs a)
+{
+    using P = Phys<PDE>;
+    constexpr int NV = P::NV, ND = P::ND;
+    constexpr int H = 3;
+    extern __shared__ double sm[];
+    const int Tw = a.Tw;
+    const int W2 = Tw + 2 * H;
+    const int E = Tw + 1;  // edges of the window: edge e sits between points e-1 and e
+    double* G = sm;
+    double* SP = G + ND * W2;
+    double* LAM = SP + W2;
+    double* REC = LAM + E;
+    const int64_t win = blockIdx.x;
+    const int64_t pe = win / a.wpp;
+    const int chunk = (int)(win - pe * a.wpp);
+    const int64_t t0 = pe * a.B + (int64_t)chunk * Tw;
+    fill_window<PDE, true>(a, G, SP, pe, t0, W2);
+    __syncthreads();
+    for (int e = threadIdx.x; e < E; e += blockDim.x)
+        LAM[e] = 0.5 * fmax(SP[e - 1 + H], SP[e + H]);  // half the edge's local wave speed
+    __syncthreads();
+    const double eps = (PDE == EULER) ? a.prm[4] : a.prm[1];
+    const int items = NV * 2 * E;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int r = it / E;
+        const int e = it - r * E;
+        const int v = r >> 1;
+        const double hl = LAM[e];
+        const double* C = G + v * W2;
+        const double* Qv = G + (NV + v) * W2;
+        double rec;
+        if ((r & 1) == 0) {  // f+ = C/2 + (lam/2) Q on points e-3..e+1
+            rec = weno5(fma(hl, Qv[e], C[e]), fma(hl, Qv[e + 1], C[e + 1]), fma(hl, Qv[e + 2], C[e + 2]),
+                        fma(hl, Qv[e + 3], C[e + 3]), fma(hl, Qv[e + 4], C[e + 4]), eps);
+        } else {  // f- = C/2 - (lam/2) Q on points e+2..e-2 (mirrored)
+            rec = weno5(fma(-hl, Qv[e + 5], C[e + 5]), fma(-hl, Qv[e + 4], C[e + 4]),
+                        fma(-hl, Qv[e + 3], C[e + 3]), fma(-hl, Qv[e + 2], C[e + 2]),
+                        fma(-hl, Qv[e + 1], C[e + 1]), eps);
+        }
+        REC[r * E + e] = rec;
+    }
+    __syncthreads();
+    const double rdx = a.k0;  // 1 / dx
+    for (int it = threadIdx.x; it < NV * Tw; it += blockDim.x) {
+        const int v = it / Tw;
+        const int jl = it - v * Tw;
+        const int64_t j = t0 + jl;
+        const int c = jl + H;
+        const double Fr = REC[(2 * v) * E + jl + 1] + REC[(2 * v + 1) * E + jl + 1];
+        const double Fl = REC[(2 * v) * E + jl] + REC[(2 * v + 1) * E + jl];
+        double K = (Fl - Fr) * rdx;
+        const double x = G[(NV + v) * W2 + c];
+        if constexpr (PDE == EULER) {
+            if (v == 3) {
+                const double Q[4] = {G[4 * W2 + c], G[5 * W2 + c], G[6 * W2 + c], G[7 * W2 + c]};
+                const double u = Q[1] / Q[0];
+                const double p = P::pressure(a, Q, u);
+                K = fma(-a.prm[1] * Q[3], exp(-a.prm[2] * Q[0] / p), K);
+            }
+        }
+        rk_update(a, v, j, chunk * Tw + jl, pe, K, x);
+    }
+}
+
+// seed the ring with the edge windows of the state at level 0, stage 0
+__global__ void ring_seed(const StageArgs a)
+{
+    const int64_t total = a.P * 2 * a.H * a.nvar;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(t % a.nvar);
+        const int h = (int)((t / a.nvar) % a.H);
+        const int side = (int)((t / ((int64_t)a.nvar * a.H)) % 2);
+        const int64_t pe = t / ((int64_t)a.nvar * a.H * 2);
+        const int64_t j = pe * a.B + (side == 0 ? h : a.B - a.H + h);
+        a.ring[ring_index(a, 0, 0, pe, side, h, v)] = a.u[v * a.N + j];
+    }
+}
+
+} // namespace atk
+
+// ---------------------------------------------------------------------------
+// host-side launchers (C++ linkage, used by at_abi.cu)
+// ---------------------------------------------------------------------------
+size_t atk_stage_smem_bytes(int pde, int Tw, int H)
+{
+    const int W2 = Tw + 2 * H;
+    switch (pde) {
+    case atk::ADVDIFF: return sizeof(double) * (size_t)W2;
+    case atk::RNS: return sizeof(double) * 8 * (size_t)W2;
+    case atk::EULER: return sizeof(double) * ((size_t)9 * W2 + (Tw + 1) + 8 * (size_t)(Tw + 1));
+    default: return sizeof(double) * ((size_t)3 * W2 + (Tw + 1) + 2 * (size_t)(Tw + 1));
+    }
+}
+
+int atk_stage_block(int pde, int Tw)
+{
+    int nv = (pde == atk::RNS || pde == atk::EULER) ? 4 : 1;
+    int want = (pde == atk::EULER || pde == atk::ADV_WENO) ? 256 : nv * Tw;
+    if (want > 256) want = 256;
+    want = ((want + 31) / 32) * 32;
+    return want < 32 ? 32 : want;
+}
+
+cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaStream_t st)
+{
+    const int64_t windows = a.P * a.wpp;
+    const dim3 grid((unsigned)windows), block(atk_stage_block(pde, a.Tw));
+    const size_t smem = atk_stage_smem_bytes(pde, a.Tw, a.H);
+    switch (pde) {
+    case atk::ADVDIFF:
+        if (order == 2) atk::stage_central<atk::ADVDIFF, 1><<<grid, block, smem, st>>>(a);
+        else if (order == 4) atk::stage_central<atk::ADVDIFF, 2><<<grid, block, smem, st>>>(a);
+        else atk::stage_central<atk::ADVDIFF, 3><<<grid, block, smem, st>>>(a);
+        break;
+    case atk::RNS:
+        if (order == 2) atk::stage_central<atk::RNS, 1><<<grid, block, smem, st>>>(a);
+        else if (order == 4) atk::stage_central<atk::RNS, 2><<<grid, block, smem, st>>>(a);
+        else atk::stage_central<atk::RNS, 3><<<grid, block, smem, st>>>(a);
+        break;
+    case atk::EULER: atk::stage_weno<atk::EULER><<<grid, block, smem, st>>>(a); break;
+    default: atk::stage_weno<atk::ADV_WENO><<<grid, block, smem, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t atk_launch_ring_seed(const atk::StageArgs& a, cudaStream_t st)
+{
+    const int64_t total = a.P * 2 * a.H * a.nvar;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    atk::ring_seed<<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t atk_set_smem_limits()
+{
+    cudaError_t e = cudaSuccess;
+    const int big = 200 * 1024;
+    e = cudaFuncSetAttribute(atk::stage_weno<atk::EULER>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(atk::stage_weno<atk::ADV_WENO>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(atk::stage_central<atk::RNS, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(atk::stage_central<atk::RNS, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(atk::stage_central<atk::RNS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e != cudaSuccess) return e;
+    for (auto f : {atk::stage_central<atk::ADVDIFF, 1>, atk::stage_central<atk::ADVDIFF, 2>,
+                   atk::stage_central<atk::ADVDIFF, 3>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        if (e != cudaSuccess) return e;
+    }
+    return e;
+}

@@ -1,0 +1,64 @@
+// fp64_probe.cu -- FP64 pipe throughput probe (libat_probe.so).
+//
+// The stage kernels are bound by FP64 arithmetic, not by HBM.  This probe
+// measures the FP64 FMA rate the GPU sustains: every thread runs 8
+// independent fma chains, so the pipe, not latency, limits the rate.  Used
+// by the benchmark to put the roofline denominator next to the nominal one.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace {
+
+__global__ void __launch_bounds__(256) dfma_chains(double* out, int iters, double a, double b)
+{
+    double x0 = threadIdx.x * 1e-3, x1 = x0 + 0.1, x2 = x0 + 0.2, x3 = x0 + 0.3;
+    double x4 = x0 + 0.4, x5 = x0 + 0.5, x6 = x0 + 0.6, x7 = x0 + 0.7;
+    for (int i = 0; i < iters; ++i) {
+        x0 = fma(x0, a, b);
+        x1 = fma(x1, a, b);
+        x2 = fma(x2, a, b);
+        x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b);
+        x5 = fma(x5, a, b);
+        x6 = fma(x6, a, b);
+        x7 = fma(x7, a, b);
+    }
+    const double s = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+    if (s == 12345.678) out[blockIdx.x] = s;  // keeps the chains alive, never true
+}
+
+} // namespace
+
+extern "C" int at_probe_fp64_fma(int device, void* stream, int iters, int reps, double* tflops, double* ms_best)
+{
+    if (cudaSetDevice(device) != cudaSuccess) return -3;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int blocks = sms * 8, threads = 256;
+    double* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * blocks) != cudaSuccess) return -2;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    dfma_chains<<<blocks, threads, 0, st>>>(out, iters / 10 + 1, 0.999999, 1e-7);  // warm-up
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(e0, st);
+        dfma_chains<<<blocks, threads, 0, st>>>(out, iters, 0.999999, 1e-7);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t < best) best = t;
+    }
+    const int err = cudaGetLastError() != cudaSuccess ? -3 : 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    const double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+    *ms_best = best;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return err;
+}

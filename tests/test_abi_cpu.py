@@ -1,0 +1,113 @@
+"""The C ABI without a GPU: the library builds for sm_103a, loads, exports
+every declared symbol, its structs match the header byte for byte, and the
+host-side logic (validation, workspace sizing) behaves."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "at.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2204_01133_gb300 import api, build
+    build.build()
+    return api.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^[a-z_ *]*?\b(at_[a-z_]+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("at_create", "at_set_problem", "at_set_delays", "at_step", "at_run", "at_read"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    from paper_2204_01133_gb300 import api
+    names = declared_functions()
+    assert set(names) == set(api.SYMBOLS)
+    for f in names:
+        assert hasattr(L, f), f
+    out = subprocess.run(["nm", "-D", "--defined-only", api.LIB_PATH], capture_output=True, text=True).stdout
+    for f in names:
+        assert re.search(r"\bT %s$" % f, out, flags=re.M), f
+
+
+def test_library_targets_sm103a_only(L):
+    from paper_2204_01133_gb300 import api
+    r = subprocess.run(["cuobjdump", "--list-elf", api.LIB_PATH], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in r.stdout
+    assert "sm_90" not in r.stdout and "sm_100" not in r.stdout
+
+
+def test_struct_layouts_match_header():
+    from paper_2204_01133_gb300 import api
+    prog = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "at.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(at_problem), offsetof(at_problem, n), offsetof(at_problem, prm),
+         sizeof(at_delays), offsetof(at_delays, seed));
+  printf("%zu %zu %zu %zu\n", offsetof(at_delays, instance), sizeof(at_stats), offsetof(at_stats, kernels_launched), offsetof(at_stats, stage_ms));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    assert vals == [ctypes.sizeof(api.Problem), api.Problem.n.offset, api.Problem.prm.offset,
+                    ctypes.sizeof(api.Delays), api.Delays.seed.offset, api.Delays.instance.offset,
+                    ctypes.sizeof(api.Stats), api.Stats.kernels_launched.offset, api.Stats.stage_ms.offset]
+
+
+def test_workspace_sizing_and_validation(L):
+    from paper_2204_01133_gb300 import api
+    from paper_2204_01133_gb300 import workloads as W
+    pb, _ = W.advdiff()
+    nb = api.workspace_bytes(pb)
+    n, R, S, P, H = 2048, 3 + 2 + 1, 4, 32, 2
+    field = 8 * n
+    assert nb >= 3 * field + 8 * R * S * P * 2 * H + S * P * 2
+    assert nb % 256 == 0
+    # a larger delay model needs a larger ring
+    assert api.workspace_bytes(dict(pb, k_max=6)) > nb
+    # invalid descriptions are rejected with 0
+    assert api.workspace_bytes(dict(pb, n=2049)) == 0
+    assert api.workspace_bytes(dict(pb, pe_size=3)) == 0      # below 2 x halo width
+    assert api.workspace_bytes(dict(pb, k_max=16)) == 0
+    assert api.workspace_bytes(dict(pb, order=8)) == 0
+    assert b"order" in L.at_last_error()
+
+
+def test_calls_out_of_order_and_without_gpu(L):
+    from paper_2204_01133_gb300 import api
+    h = ctypes.c_void_p()
+    rc = L.at_create(ctypes.byref(h), 0, None)
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if has_gpu:
+        assert rc == api.AT_OK
+        assert L.at_step(h, 1) == api.AT_ESTATE
+        L.at_destroy(h)
+    else:
+        assert rc in (api.AT_ECUDA, api.AT_EINVAL)
+        assert L.at_last_error()
+    assert L.at_step(None, 1) == api.AT_EINVAL

@@ -1,0 +1,161 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+element by element, on the same seeded inputs and delay streams.
+
+Tolerance (FP64): per variable, max|gpu - oracle| <= 1e-12 * max|oracle|
+after one step and <= 1e-10 * max|oracle| after the whole run; delays are
+integers and must agree bitwise.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_01133_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-12
+TOL_RUN = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2204_01133_gb300 import build
+    build.build()
+
+
+def rel_err(g, o):
+    g = np.asarray(g).reshape(o.shape)
+    return max(np.abs(g[v] - o[v]).max() / max(np.abs(o[v]).max(), 1e-300) for v in range(o.shape[0]))
+
+
+def parity(pb, init, steps, first_tol=TOL_STEP, run_tol=TOL_RUN, check_delays=True):
+    from paper_2204_01133_gb300.api import Solver
+    s = Solver(pb, init)
+    o = oracle.Oracle(pb, init)
+    s.run(1)
+    assert o.run(1) == 0
+    e1 = rel_err(s.read_state(), o.state())
+    assert e1 <= first_tol, ("first step", e1)
+    if check_delays:
+        assert np.array_equal(s.read_delays(), o.delays())
+    if steps > 1:
+        s.run(steps - 1)
+        assert o.run(steps - 1) == 0
+        e = rel_err(s.read_state(), o.state())
+        assert e <= run_tol, ("run", e)
+        if check_delays:
+            assert np.array_equal(s.read_delays(), o.delays())
+    return s, o
+
+
+def test_advdiff_literal_config_full_run():
+    """N = 2048, 32 PEs of 64, AT4 + RK4, k uniform on {0..3}, seed 0, 10,000 steps."""
+    pb, u0 = W.advdiff(n=2048, pe_size=64, order=4, mode="at", k_max=3, seed=0, cfl=0.075)
+    parity(pb, u0, 10000)
+
+
+@pytest.mark.parametrize("mode", ["sync", "as", "at"])
+@pytest.mark.parametrize("order,cfl", [(2, 0.05), (4, 0.05), (6, 0.01)])
+def test_advdiff_modes_orders(mode, order, cfl):
+    pb, u0 = W.advdiff(n=960, pe_size=48, order=order, mode=mode, k_max=3, seed=11, cfl=cfl)
+    parity(pb, u0, 300)
+
+
+@pytest.mark.parametrize("rk", ["rk2", "rk3tvd", "rk4"])
+@pytest.mark.parametrize("per_stage", [0, 1])
+def test_advdiff_rk_and_delay_granularity(rk, per_stage):
+    pb, u0 = W.advdiff(n=512, pe_size=16, order=4, mode="at", k_max=2, seed=5, cfl=0.04, rk=rk,
+                       per_stage=per_stage, dist="table", prob=[0.4, 0.5, 0.1])
+    parity(pb, u0, 200)
+
+
+@pytest.mark.parametrize("pe_size,n", [(8, 8), (16, 16 * 7), (1024, 3072), (520, 1040)])
+def test_advdiff_edge_shapes(pe_size, n):
+    """Degenerate decompositions: one PE (its own neighbour), an odd PE count,
+    PEs split into several windows, a window length that is not a power of two."""
+    pb, u0 = W.advdiff(n=n, pe_size=pe_size, order=4, mode="at", k_max=3, seed=3, cfl=0.05)
+    parity(pb, u0, 60)
+
+
+@pytest.mark.parametrize("case", ["flame", "ignition"])
+def test_rns_literal_size(case):
+    """Reacting N-S at N = 16,384 (256 PEs of 64), AT6 + RK4, k uniform on {0..4}."""
+    pb, u0 = W.rns(case=case, n=16384, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003)
+    parity(pb, u0, 150)
+
+
+@pytest.mark.parametrize("mode", ["sync", "as"])
+def test_rns_modes(mode):
+    pb, u0 = W.rns(case="flame", n=2048, pe_size=64, mode=mode, k_max=4, seed=2, dt=0.003)
+    parity(pb, u0, 100)
+
+
+@pytest.mark.parametrize("pe_size", [1024, 512, 96])
+def test_detonation_weno(pe_size):
+    """Reactive Euler, WENO5 + AT-WENO5, RK3-TVD, k geometric(0.5) on {0..4}."""
+    pb, u0 = W.detonation(n=pe_size * 8, pe_size=pe_size, mode="at", k_max=4, seed=9)
+    parity(pb, u0, 80)
+
+
+@pytest.mark.parametrize("mode", ["sync", "as"])
+def test_detonation_modes(mode):
+    pb, u0 = W.detonation(n=4096, pe_size=512, mode=mode, k_max=4, seed=1)
+    parity(pb, u0, 60)
+
+
+@pytest.mark.parametrize("mode", ["sync", "as", "at"])
+def test_scalar_weno(mode):
+    pb, u0 = W.adv_weno(n=512, pe_size=32, mode=mode, k_max=3, seed=4, dt_coef=2.0)
+    parity(pb, u0, 100)
+
+
+def test_detonation_full_size_sampled_pes():
+    """The N = 2^24, 16,384-PE detonation in the launch configuration the
+    benchmark times.  The oracle recomputes sampled PEs on a 5-PE window of
+    the domain (with the global PE index in the delay counter): after s steps
+    only points within 9 s of the window's outer edges can differ."""
+    from paper_2204_01133_gb300.api import Solver
+    steps = 12
+    pb, u0 = W.detonation()
+    P, B = pb["n"] // pb["pe_size"], pb["pe_size"]
+    s = Solver(pb, u0)
+    s.run(steps)
+    g = s.read_state()
+    gd = s.read_delays()
+    for p in (0, 1, 7777, P - 1):
+        idx = np.arange(p - 2, p + 3) % P
+        sub = np.concatenate([u0[:, i * B:(i + 1) * B] for i in idx], axis=1)
+        spb = dict(pb, n=5 * B, pe_base=p - 2, pe_total=P)
+        o = oracle.Oracle(spb, sub)
+        assert o.run(steps) == 0
+        ref = o.state()[:, 2 * B:3 * B]
+        assert rel_err(g[:, p * B:(p + 1) * B], ref) <= TOL_RUN
+        assert np.array_equal(gd[:, p, :], o.delays()[:, 2, :])
+
+
+def test_deterministic_and_seeded():
+    from paper_2204_01133_gb300.api import Solver
+    pb, u0 = W.advdiff(n=2048, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075)
+    a = Solver(pb, u0)
+    a.run(500)
+    b = Solver(pb, u0)
+    b.run(500)
+    assert np.array_equal(a.read_state(), b.read_state())
+    c = Solver(dict(pb, seed=1), u0)
+    c.run(500)
+    assert not np.array_equal(a.read_state(), c.read_state())
+
+
+def test_unstable_run_reports_status():
+    """A time step far beyond the AT stability limit makes the state blow up;
+    the device flag turns that into AT_EUNSTABLE (no fault, no hang)."""
+    from paper_2204_01133_gb300 import api
+    pb, u0 = W.advdiff(n=2048, pe_size=64, mode="at", k_max=3, seed=0, cfl=2.0)
+    s = api.Solver(pb, u0)
+    with pytest.raises(api.AtError) as ei:
+        s.run(3000)
+    assert ei.value.code == api.AT_EUNSTABLE
+    assert s.stats().status == api.AT_EUNSTABLE

@@ -55,6 +55,18 @@ int nvar_of(int pde) { return (pde == AT_RNS || pde == AT_EULER) ? 4 : 1; }
 bool is_weno(int pde) { return pde == AT_EULER || pde == AT_ADV_WENO; }
 int stages_of(int rk) { return rk == AT_RK2 ? 2 : (rk == AT_RK3TVD ? 3 : 4); }
 
+// window length: the largest divisor of the PE size in [2H, 256]; a PE size
+// without one (a large prime, say) is one window when it is at most 1024.
+// Returns 0 when neither holds.
+int window_of(int B, int H)
+{
+    int best = 0;
+    for (int t = 2 * H; t <= 256 && t <= B; ++t)
+        if (B % t == 0) best = t;
+    if (best == 0 && B <= 1024) best = B;
+    return best;
+}
+
 int check_problem(const at_problem* pb)
 {
     if (!pb) return fail(AT_EINVAL, "problem is NULL");
@@ -66,6 +78,8 @@ int check_problem(const at_problem* pb)
     if (pb->pe_size <= 0 || pb->n % pb->pe_size) return fail(AT_EINVAL, "n must be a multiple of pe_size");
     const int H = is_weno(pb->pde) ? 3 : pb->order / 2;
     if (pb->pe_size < 2 * H) return fail(AT_EINVAL, "pe_size must be at least %d", 2 * H);
+    if (window_of(pb->pe_size, H) == 0)
+        return fail(AT_EINVAL, "pe_size above 1024 needs a divisor between %d and 256", 2 * H);
     if (!(pb->dx > 0.0) || !(pb->dt > 0.0)) return fail(AT_EINVAL, "dx and dt must be positive");
     return AT_OK;
 }
@@ -89,14 +103,7 @@ int check_delays(const at_delays* dl)
     return AT_OK;
 }
 
-// window length: the largest divisor of the PE size that is at most 256
-int window_of(int B)
-{
-    int best = 1;
-    for (int t = 1; t <= 256 && t <= B; ++t)
-        if (B % t == 0) best = t;
-    return best;
-}
+
 
 Layout layout(const at_problem* pb, const at_delays* dl)
 {
@@ -107,7 +114,7 @@ Layout layout(const at_problem* pb, const at_delays* dl)
     L.S = stages_of(pb->rk);
     L.R = dl->k_max + L.q + 1;
     L.P = pb->n / pb->pe_size;
-    L.Tw = window_of(pb->pe_size);
+    L.Tw = window_of(pb->pe_size, L.H);
     L.wpp = pb->pe_size / L.Tw;
     const size_t field = sizeof(double) * (size_t)L.nvar * pb->n;
     size_t off = 0;

@@ -30,53 +30,72 @@ namespace atk {
 
 // ---------------------------------------------------------------------------
 // 1. fill the window
+//
+// Work items: one per point of the window inside the PE (read the field,
+// derive), plus one per (buffer point, time level) pair of the window's PE
+// boundaries (read the ring at level n-k-l, derive, scale by the
+// extrapolation weight).  All items run concurrently, one per thread; the
+// level contributions are then summed per buffer point.  HS stages the
+// weighted level contributions: [2 H (q+1)][ND].
 // ---------------------------------------------------------------------------
 template <int PDE, bool WENO>
 __device__ __forceinline__ void fill_window(const StageArgs& a, double* __restrict__ G, double* __restrict__ SP,
-                                            int64_t pe, int64_t t0, int W2)
+                                            double* __restrict__ HS, int64_t pe, int chunk, int64_t t0, int W2)
 {
     using P = Phys<PDE>;
     constexpr int NV = P::NV, ND = P::ND;
-    const int64_t lo = pe * a.B, hi = lo + a.B;
-    for (int i = threadIdx.x; i < W2; i += blockDim.x) {
-        const int64_t m = t0 - a.H + i;
+    const int H = a.H;
+    const int L0 = (chunk == 0) ? H : 0;             // ring-halo points on the left
+    const int R0 = (chunk == a.wpp - 1) ? H : 0;     // and on the right
+    const int nw = (a.mode == AT) ? a.q + 1 : 1;     // time levels per ring-halo point
+    const int own = W2 - L0 - R0;
+    const int items = own + (L0 + R0) * nw;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
         double g[ND];
-        double sp = 0.0;
         double Q[NV];
-        if (m >= lo && m < hi) {
+        if (it < own) {
+            const int i = L0 + it;
+            const int64_t m = t0 - H + i;
 #pragma unroll
             for (int v = 0; v < NV; ++v) Q[v] = a.X[v * a.N + m];
             P::derive(a, Q, g);
-            if constexpr (WENO) sp = P::speed(a, Q);
-        } else {
-            // buffer point: the neighbour's edge window, delayed and extrapolated
-            const int side = (m < lo) ? 0 : 1;
-            const int64_t nbr = side == 0 ? (pe == 0 ? a.P - 1 : pe - 1) : (pe == a.P - 1 ? 0 : pe + 1);
-            const int h = side == 0 ? (int)(m - (lo - a.H)) : (int)(m - hi);
-            const int nside = 1 - side;
-            const int k = keff(a, pe, side);
-            if (h == 0) a.dlog[((int64_t)a.stage * a.P + pe) * 2 + side] = (uint8_t)k;
-            const int nw = (a.mode == AT) ? a.q + 1 : 1;
 #pragma unroll
-            for (int d = 0; d < ND; ++d) g[d] = 0.0;
-            for (int l = 0; l < nw; ++l) {
-                const double wl = (a.mode == AT) ? a.w[k][l] : 1.0;
-                if (wl == 0.0) continue;  // a level with weight 0 is not part of the scheme
-                const int64_t base = ring_index(a, a.level - k - l, a.stage, nbr, nside, h, 0);
+            for (int d = 0; d < ND; ++d) G[d * W2 + i] = g[d];
+            if constexpr (WENO) SP[i] = P::speed(a, Q);
+        } else {
+            const int t = it - own;
+            const int hp = t / nw, l = t - hp * nw;         // buffer point, level
+            const int side = hp < L0 ? 0 : 1;
+            const int h = side == 0 ? hp : hp - L0;         // position in the neighbour's edge window
+            const int64_t nbr = side == 0 ? (pe == 0 ? a.P - 1 : pe - 1) : (pe == a.P - 1 ? 0 : pe + 1);
+            const int k = keff(a, pe, side);
+            if (h == 0 && l == 0) a.dlog[((int64_t)a.stage * a.P + pe) * 2 + side] = (uint8_t)k;
+            const double wl = (a.mode == AT) ? a.w[k][l] : 1.0;
+            if (wl != 0.0) {  // a level with weight 0 is not part of the scheme (and may not exist yet)
+                const int64_t base = ring_index(a, a.level - k - l, a.stage, nbr, 1 - side, h, 0);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) Q[v] = a.ring[base + v];
-                double gl[ND];
-                P::derive(a, Q, gl);
-#pragma unroll
-                for (int d = 0; d < ND; ++d) g[d] = fma(wl, gl[d], g[d]);
+                P::derive(a, Q, g);
                 if constexpr (WENO) {
-                    if (l == 0) sp = P::speed(a, Q);  // wave speed at level n-k, not extrapolated
+                    if (l == 0) SP[side == 0 ? h : W2 - R0 + h] = P::speed(a, Q);  // level n-k, not extrapolated
                 }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) HS[t * ND + d] = wl * g[d];
+            } else {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) HS[t * ND + d] = 0.0;
             }
         }
-#pragma unroll
-        for (int d = 0; d < ND; ++d) G[d * W2 + i] = g[d];
-        if constexpr (WENO) SP[i] = sp;
+    }
+    if (L0 + R0 == 0) return;
+    __syncthreads();
+    // sum the level contributions of every buffer point (in level order)
+    for (int c = threadIdx.x; c < (L0 + R0) * ND; c += blockDim.x) {
+        const int hp = c / ND, d = c - hp * ND;
+        double acc = HS[(hp * nw) * ND + d];
+        for (int l = 1; l < nw; ++l) acc += HS[(hp * nw + l) * ND + d];
+        const int i = hp < L0 ? hp : W2 - R0 + (hp - L0);
+        G[d * W2 + i] = acc;
     }
 }
 
@@ -145,11 +164,12 @@ __global__ void __launch_bounds__(256) stage_central(const StageArgs a)
     extern __shared__ double sm[];
     const int W2 = a.Tw + 2 * H;
     double* G = sm;
+    double* HS = G + P::ND * W2;
     const int64_t win = blockIdx.x;
     const int64_t pe = win / a.wpp;
     const int chunk = (int)(win - pe * a.wpp);
     const int64_t t0 = pe * a.B + (int64_t)chunk * a.Tw;
-    fill_window<PDE, false>(a, G, nullptr, pe, t0, W2);
+    fill_window<PDE, false>(a, G, nullptr, HS, pe, chunk, t0, W2);
     __syncthreads();
     const int items = NV * a.Tw;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -219,11 +239,12 @@ __global__ void __launch_bounds__(256) stage_weno(const StageArgs a)
     double* SP = G + ND * W2;
     double* LAM = SP + W2;
     double* REC = LAM + E;
+    double* HS = REC + NV * 2 * E;
     const int64_t win = blockIdx.x;
     const int64_t pe = win / a.wpp;
     const int chunk = (int)(win - pe * a.wpp);
     const int64_t t0 = pe * a.B + (int64_t)chunk * Tw;
-    fill_window<PDE, true>(a, G, SP, pe, t0, W2);
+    fill_window<PDE, true>(a, G, SP, HS, pe, chunk, t0, W2);
     __syncthreads();
     for (int e = threadIdx.x; e < E; e += blockDim.x)
         LAM[e] = 0.5 * fmax(SP[e - 1 + H], SP[e + H]);  // half the edge's local wave speed
@@ -292,12 +313,13 @@ __global__ void ring_seed(const StageArgs a)
 // ---------------------------------------------------------------------------
 size_t atk_stage_smem_bytes(int pde, int Tw, int H)
 {
-    const int W2 = Tw + 2 * H;
+    const size_t W2 = Tw + 2 * H, E = Tw + 1;
+    const size_t hs = (size_t)2 * H * (AT_QMAX + 1);  // ring-halo (point, level) items
     switch (pde) {
-    case atk::ADVDIFF: return sizeof(double) * (size_t)W2;
-    case atk::RNS: return sizeof(double) * 8 * (size_t)W2;
-    case atk::EULER: return sizeof(double) * ((size_t)9 * W2 + (Tw + 1) + 8 * (size_t)(Tw + 1));
-    default: return sizeof(double) * ((size_t)3 * W2 + (Tw + 1) + 2 * (size_t)(Tw + 1));
+    case atk::ADVDIFF: return sizeof(double) * (W2 + hs * 1);
+    case atk::RNS: return sizeof(double) * (8 * W2 + hs * 8);
+    case atk::EULER: return sizeof(double) * (9 * W2 + E + 8 * E + hs * 8);
+    default: return sizeof(double) * (3 * W2 + E + 2 * E + hs * 2);
     }
 }
 

@@ -219,18 +219,23 @@ def euler_conserved(rho, u, p, Y, prm) -> np.ndarray:
 
 
 def detonation(n=1 << 24, pe_size=1024, mode="at", k_max=4, dist="geometric", prob=(0.5,), seed=0,
-               per_stage=1, cfl=0.5, slab=20.0, dt=None):
-    """Slab of von Neumann state over the first ``slab`` half-reaction lengths
-    followed by unburnt gas (rho = p = 1, u = 0, Y = 1); periodic."""
+               per_stage=1, cfl=0.5, slab=20.0, dt=None, edge_points=5.0):
+    """Slab of von Neumann state over ``slab`` half-reaction lengths (from
+    x = 1 to x = 1 + slab) in unburnt gas (rho = p = 1, u = 0, Y = 1);
+    periodic.  The slab edges are tanh ramps ``edge_points`` cells wide: the
+    shock steepens by itself within a few steps, and a ramp instead of a jump
+    keeps the WENO weights of the first steps away from their most
+    round-off-sensitive regime."""
     prm = det_prm()
     dx = 1.0 / 20.0
     D = _det_speed()
     rho_s, u_s, p_s = _vn_state(D)
     x = (np.arange(n, dtype=np.float64) + 0.5) * dx
-    inside = x < slab
-    rho = np.where(inside, rho_s, 1.0)
-    u = np.where(inside, u_s, 0.0)
-    p = np.where(inside, p_s, 1.0)
+    w = edge_points * dx
+    s = 0.5 * (np.tanh((x - 1.0) / w) - np.tanh((x - 1.0 - slab) / w))
+    rho = 1.0 + (rho_s - 1.0) * s
+    u = u_s * s
+    p = 1.0 + (p_s - 1.0) * s
     Y = np.ones(n)
     init = euler_conserved(rho, u, p, Y, prm)
     if dt is None:

@@ -92,6 +92,9 @@ def test_workspace_sizing_and_validation(L):
     assert api.workspace_bytes(dict(pb, k_max=16)) == 0
     assert api.workspace_bytes(dict(pb, order=8)) == 0
     assert b"order" in L.at_last_error()
+    assert api.workspace_bytes(dict(pb, n=2053 * 2, pe_size=2053)) == 0   # prime above 1024
+    assert b"divisor" in L.at_last_error()
+    assert api.workspace_bytes(dict(pb, n=263 * 3, pe_size=263)) > 0      # prime, one window
 
 
 def test_calls_out_of_order_and_without_gpu(L):

@@ -43,19 +43,22 @@ WORKLOADS = {
 DEFAULT = "rns-flame-n16384"
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal, at 2070 MHz boost
 
-# FP64 flops per point per stage, counted from the kernel's formulas (fma = 2;
-# a division, square root or exponential counted at the FP64 operations of
-# its software sequence).
-DIV, SQRT, EXP = 9, 9, 22
+# FP64 flops per point per stage (FMA = 2, add/mul = 1) of the stage kernel:
+# the formulas of the method evaluated in IEEE FP64, divisions, square roots
+# and exponentials at the cost of their instruction sequences, AT halo work
+# included.  Measured with ncu (sass DFMA/DADD/DMUL counts) on the large-N
+# workloads and divided by the grid points of one launch.
 FLOPS_PER_POINT_STAGE = {
-    # derive 23 + 1 div; stencils 90; RK4 update ~13; source 5 + 1 div + 1 exp
-    "rns": 23 + 90 + 13 + 5 + 2 * DIV + EXP,
-    # merged 5-tap stencil 9 (1 mul + 4 fma) + RK4 update ~3.25
-    "advdiff": 9 + 3.25,
-    # per point: derive 12 + 1 div, speed 4 + 1 div + 1 sqrt; per edge 8 WENO5
-    # reconstructions of 60 + 1 div and 5 split fluxes (10); lambda 2; flux
-    # difference 8; source 10 + 1 div + 1 exp; RK3 update ~4 x 4
-    "detonation": 12 + DIV + 4 + DIV + SQRT + 8 * (60 + DIV + 10) + 2 + 8 + 10 + DIV + EXP + 16,
+    "rns": 198.5,          # central6 + AT6, reacting N-S, 4 variables
+    "detonation": 919.7,   # WENO5 + AT-WENO5, reactive Euler, 4 variables
+    "advdiff": 12.25,      # merged 5-tap central4 stencil + RK4 update
+}
+# DRAM bytes per launch of the stage kernel from the same ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum), or None where not captured
+TRAFFIC_PER_LAUNCH = {
+    "rns-flame-n16384": 1.655e6,
+    "rns-flame-n16777216": 1.663e9 + 1.086e9,
+    "detonation-n16777216": 5.458e8 + 4.972e8,
 }
 
 
@@ -291,7 +294,8 @@ def run_ours(args):
         fl = FLOPS_PER_POINT_STAGE[kind] * n  # per launch
         achieved = fl / (stage_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None, "kernel": "stage_%s" % kind,
+                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
+                "kernel": "stage_%s" % kind,
                 "avg_launch_ms": stage_ms, "launches_timed": int(st.launches_timed),
                 "flops_per_launch": fl, "peak_kind": "nominal FP64 (1.25 TFLOP/s); see peak_measured",
                 "peak_measured": peak_meas, "frac_of_measured": (achieved / peak_meas) if peak_meas else None}

@@ -153,6 +153,34 @@ int at_profile(at_ctx* ctx, int enable);
 
 int at_destroy(at_ctx* ctx);
 
+/* ---- allocation-free entry point (no counterpart in the paper) ----------
+ *
+ * For callers that must not allocate device memory while they run: a host
+ * application that sizes all device memory up front and hands libraries a
+ * fixed budget, or code on a path where cudaMalloc is unwelcome (it can
+ * synchronise the device and can fail under memory pressure partway through
+ * a run).  at_run_noalloc performs one whole solve with no context and no
+ * caller workspace: it binds the problem and the delay model, runs nsteps
+ * steps on state_dev in place ([nvar][n] FP64, device memory, 16-byte
+ * aligned: the initial state on entry, u^nsteps on return), synchronises
+ * the stream and checks for non-finite values, exactly like at_set_problem
+ * + at_set_delays + at_run on a fresh context.
+ *
+ * Its workspace (stage buffers, RK accumulator, history ring, delay log,
+ * status word) lives in one file-scope device array of
+ * AT_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits.  Problems whose at_workspace_bytes() exceeds it are
+ * rejected with AT_ENOMEM before anything is enqueued.  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  Each call clears the parts of
+ * the array that must start at zero; all calls share the one array, so calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  Nothing is allocated: no cudaMalloc, no
+ * cudaFree, no host heap. */
+#define AT_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+int at_run_noalloc(const at_problem* pb, const at_delays* dl, double* state_dev, int64_t nsteps, int device,
+                   void* cuda_stream);
+
 /* message for the calling thread's last failed call ("" if none) */
 const char* at_last_error(void);
 

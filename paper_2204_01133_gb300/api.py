@@ -29,7 +29,8 @@ STAGES = {"rk2": 2, "rk3tvd": 3, "rk4": 4}
 
 # every symbol include/at.h declares
 SYMBOLS = ("at_create", "at_workspace_bytes", "at_set_problem", "at_set_delays", "at_step", "at_run",
-           "at_read", "at_profile", "at_destroy", "at_last_error")
+           "at_read", "at_profile", "at_destroy", "at_last_error", "at_run_noalloc")
+NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 class AtError(RuntimeError):
@@ -83,6 +84,8 @@ def lib():
         L.at_read.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int]
         L.at_destroy.argtypes = [vp]
         L.at_profile.argtypes = [vp, ctypes.c_int]
+        L.at_run_noalloc.argtypes = [P(Problem), P(Delays), vp, ctypes.c_int64, ctypes.c_int, vp]
+        L.at_run_noalloc.restype = ctypes.c_int
         L.at_last_error.restype = ctypes.c_char_p
         for f in ("at_create", "at_set_problem", "at_set_delays", "at_step", "at_run", "at_read", "at_profile",
                   "at_destroy"):
@@ -126,6 +129,22 @@ def delays_struct(pb: dict) -> Delays:
 
 def workspace_bytes(pb: dict) -> int:
     return int(lib().at_workspace_bytes(ctypes.byref(problem_struct(pb)), ctypes.byref(delays_struct(pb))))
+
+
+def run_noalloc(pb: dict, state, nsteps: int, device: int = 0, stream=None) -> None:
+    """One whole solve through the allocation-free entry point.
+
+    ``state``: a CUDA float64 tensor [nvar][n] holding the initial state; it
+    is advanced nsteps steps in place.  The library's fixed device scratch
+    array replaces the workspace, so nothing is allocated; problems larger
+    than ``NOALLOC_SCRATCH_BYTES`` of workspace raise AT_ENOMEM.  Calls share
+    that array: do not overlap them on the GPU.
+    """
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream(torch.device("cuda", device))
+    check(lib().at_run_noalloc(ctypes.byref(problem_struct(pb)), ctypes.byref(delays_struct(pb)),
+                               ctypes.c_void_p(state.data_ptr()), int(nsteps), int(device),
+                               ctypes.c_void_p(st.cuda_stream)))
 
 
 class Solver:

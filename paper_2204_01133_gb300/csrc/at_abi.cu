@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -510,6 +511,57 @@ int at_destroy(at_ctx* c)
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     delete c;
     return AT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// allocation-free entry point: the workspace is this file-scope device array
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[AT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+const int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices];  // device address of the array, per device (set up once)
+} // namespace
+
+int at_run_noalloc(const at_problem* pb, const at_delays* dl, double* state_dev, int64_t nsteps, int device,
+                   void* cuda_stream)
+{
+    if (!state_dev) return fail(AT_EINVAL, "state must be a device pointer");
+    if (nsteps < 0) return fail(AT_EINVAL, "nsteps must be >= 0");
+    const size_t need = at_workspace_bytes(pb, dl);
+    if (need == 0) return AT_EINVAL;  // at_last_error() names the invalid field
+    if (need > AT_NOALLOC_SCRATCH_BYTES)
+        return fail(AT_ENOMEM, "this problem needs %zu workspace bytes; at_run_noalloc has %zu", need,
+                    (size_t)AT_NOALLOC_SCRATCH_BYTES);
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev || device >= kMaxDevices) return fail(AT_EINVAL, "device %d out of range", device);
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        e = cudaSetDevice(device);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+        if (!g_noalloc_ptr[device]) {
+            // once per device, with the device current: the host-side name of a
+            // __device__ array is not its device address
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the scratch array");
+            e = atk_set_smem_limits();
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+            g_noalloc_ptr[device] = ptr;
+        }
+        scratch = g_noalloc_ptr[device];
+    }
+    at_ctx c;  // on the stack: no heap allocation (tracing stays off)
+    c.device = device;
+    c.stream = (cudaStream_t)cuda_stream;
+    int st = at_set_problem(&c, pb, state_dev, nullptr, 1, scratch, AT_NOALLOC_SCRATCH_BYTES);
+    if (st == AT_OK) st = at_set_delays(&c, dl);  // clears ring, delay log and status word
+    if (st == AT_OK) st = at_run(&c, nsteps);
+    return st;
 }
 
 } // extern "C"

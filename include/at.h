@@ -41,7 +41,7 @@ typedef enum {
     AT_ENOMEM = -2,    /* the workspace is smaller than at_workspace_bytes()    */
     AT_ECUDA = -3,     /* a CUDA call failed; at_last_error() has its message   */
     AT_EUNSTABLE = -4, /* a non-finite value appeared in the state              */
-    AT_ETIMEOUT = -5,  /* a bounded device wait ran out (reserved)              */
+    AT_ETIMEOUT = -5,  /* a bounded device wait of the persistent path ran out  */
     AT_ESTATE = -6     /* calls out of order (problem, then delays, then steps) */
 } at_status;
 
@@ -72,6 +72,21 @@ enum { AT_SYNC = 0, AT_AS = 1, AT_AT = 2 };
 enum { AT_UNIFORM = 0, AT_TABLE = 1, AT_GEOMETRIC = 2 };
 /* at_read targets */
 enum { AT_READ_STATE = 0, AT_READ_DELAYS = 1, AT_READ_RING = 2, AT_READ_STATS = 3 };
+/* execution paths (at_set_option(AT_OPT_PATH)): AT_PATH_STAGE launches one
+ * kernel per RK stage; AT_PATH_PERSISTENT runs all steps of an at_step call
+ * in one cooperative launch with one CTA per PE that synchronises only with
+ * its two neighbours (central PDEs, up to as many PEs as the GPU holds at
+ * once); AT_PATH_AUTO (default) takes the persistent path when it can.  Both
+ * paths compute the same values in the same order.                          */
+enum { AT_PATH_AUTO = 0, AT_PATH_STAGE = 1, AT_PATH_PERSISTENT = 2 };
+/* at_set_option keys */
+enum {
+    AT_OPT_PATH = 0,        /* value: AT_PATH_*                                                  */
+    AT_OPT_WAIT_LIMIT = 1,  /* polls (~0.2 us each) before a persistent-path wait gives up with
+                               AT_ETIMEOUT; default 4,000,000                                    */
+    AT_OPT_WITHHOLD_PE = 2  /* fault injection: this PE never announces its progress, so its
+                               neighbours' waits run out (-1, the default: none)                 */
+};
 
 typedef struct {
     int32_t pde;      /* AT_ADVDIFF | AT_RNS | AT_EULER | AT_ADV_WENO                 */
@@ -102,7 +117,9 @@ typedef struct {
     int32_t halo;      /* halo width H                                                */
     int32_t q;         /* temporal extrapolation degree of the AT halo                */
     int32_t ring_levels;
-    int64_t kernels_launched; /* stage kernels enqueued by this context so far       */
+    int32_t path;             /* AT_PATH_STAGE or AT_PATH_PERSISTENT: the last at_step */
+    int32_t pad_;
+    int64_t kernels_launched; /* kernels enqueued by this context so far             */
     int64_t launches_timed;   /* stage kernels timed since at_profile(ctx, 1)        */
     double stage_ms;          /* summed device time of those launches (CUDA events)  */
 } at_stats;
@@ -134,7 +151,8 @@ int at_set_delays(at_ctx* ctx, const at_delays* dl);
 int at_step(at_ctx* ctx, int64_t nsteps);
 
 /* at_step, then synchronise the stream and return AT_EUNSTABLE if a
- * non-finite value appeared. */
+ * non-finite value appeared, AT_ETIMEOUT if a persistent-path wait ran out
+ * (the state is then incomplete; the context stays usable after at_set_delays). */
 int at_run(at_ctx* ctx, int64_t nsteps);
 
 /* Copy out: AT_READ_STATE the [nvar][n] state; AT_READ_DELAYS the delays of
@@ -144,7 +162,10 @@ int at_run(at_ctx* ctx, int64_t nsteps);
  * the target; the copy is synchronous. */
 int at_read(at_ctx* ctx, int what, void* dst, size_t bytes, int dst_on_device);
 
-/* Tracing: with enable = 1, every stage kernel at_step enqueues afterwards is
+/* Options (AT_OPT_*); they apply from the next at_step on. */
+int at_set_option(at_ctx* ctx, int key, int64_t value);
+
+/* Tracing: with enable = 1, every kernel launch at_step enqueues afterwards is
  * bracketed by two CUDA events on the stream, and at_read(AT_READ_STATS)
  * reports their number and summed device time (it synchronises the stream).
  * enable = 0 stops timing; either call resets the totals.  At most 65,536

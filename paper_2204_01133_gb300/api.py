@@ -29,7 +29,9 @@ STAGES = {"rk2": 2, "rk3tvd": 3, "rk4": 4}
 
 # every symbol include/at.h declares
 SYMBOLS = ("at_create", "at_workspace_bytes", "at_set_problem", "at_set_delays", "at_step", "at_run",
-           "at_read", "at_profile", "at_destroy", "at_last_error", "at_run_noalloc")
+           "at_read", "at_profile", "at_set_option", "at_destroy", "at_last_error", "at_run_noalloc")
+PATH_AUTO, PATH_STAGE, PATH_PERSISTENT = 0, 1, 2
+OPT_PATH, OPT_WAIT_LIMIT, OPT_WITHHOLD_PE = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -58,7 +60,7 @@ class Stats(ctypes.Structure):
     _fields_ = [
         ("level", ctypes.c_int64), ("status", ctypes.c_int32), ("stages", ctypes.c_int32), ("nvar", ctypes.c_int32),
         ("halo", ctypes.c_int32), ("q", ctypes.c_int32), ("ring_levels", ctypes.c_int32),
-        ("kernels_launched", ctypes.c_int64), ("launches_timed", ctypes.c_int64), ("stage_ms", ctypes.c_double),
+        ("path", ctypes.c_int32), ("pad_", ctypes.c_int32), ("kernels_launched", ctypes.c_int64), ("launches_timed", ctypes.c_int64), ("stage_ms", ctypes.c_double),
     ]
 
 
@@ -84,6 +86,8 @@ def lib():
         L.at_read.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int]
         L.at_destroy.argtypes = [vp]
         L.at_profile.argtypes = [vp, ctypes.c_int]
+        L.at_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
+        L.at_set_option.restype = ctypes.c_int
         L.at_run_noalloc.argtypes = [P(Problem), P(Delays), vp, ctypes.c_int64, ctypes.c_int, vp]
         L.at_run_noalloc.restype = ctypes.c_int
         L.at_last_error.restype = ctypes.c_char_p
@@ -156,7 +160,7 @@ class Solver:
     checks for non-finite values, ``state()`` returns the state tensor.
     """
 
-    def __init__(self, pb: dict, init=None, device: int = 0, stream=None, state=None):
+    def __init__(self, pb: dict, init=None, device: int = 0, stream=None, state=None, path: str = "auto"):
         import torch
 
         self.torch = torch
@@ -182,6 +186,8 @@ class Solver:
                                                                   device=self.device)
         self.set_problem(init)
         self.set_delays()
+        if path != "auto":
+            self.set_path(path)
 
     # -- binding calls ----------------------------------------------------
     def set_problem(self, init=None):
@@ -222,6 +228,12 @@ class Solver:
         out = np.empty((self.stages, self.P, 2), dtype=np.uint8)
         check(lib().at_read(self._h, READ_DELAYS, ctypes.c_void_p(out.ctypes.data), out.nbytes, 0))
         return out
+
+    def set_option(self, key: int, value: int):
+        check(lib().at_set_option(self._h, int(key), int(value)))
+
+    def set_path(self, path: str):
+        self.set_option(OPT_PATH, {"auto": PATH_AUTO, "stage": PATH_STAGE, "persistent": PATH_PERSISTENT}[path])
 
     def profile(self, enable: bool = True):
         check(lib().at_profile(self._h, 1 if enable else 0))

@@ -22,6 +22,13 @@ int atk_stage_block(int pde, int Tw);
 cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaStream_t st);
 cudaError_t atk_launch_ring_seed(const atk::StageArgs& a, cudaStream_t st);
 cudaError_t atk_set_smem_limits();
+int64_t atk_persist_capacity(int pde, int order, int B, int device);
+cudaError_t atk_launch_persist(const atk::StageArgs& a, int pde, int order, int64_t level0, int64_t nsteps,
+                               cudaStream_t st);
+
+// spare ring levels beyond k_max + q + 1: how far a PE of the persistent
+// path may run ahead of a neighbour before it must wait to reuse a slot
+static const int kRingSlack = 2;
 
 namespace {
 
@@ -46,7 +53,7 @@ struct Layout {
     int nvar, H, q, S, R;
     int64_t P;
     int Tw, wpp;
-    size_t off_A, off_B, off_acc, off_ring, off_dlog, off_status, total;
+    size_t off_A, off_B, off_acc, off_ring, off_dlog, off_status, off_done, total;
     size_t ring_elems;
 };
 
@@ -113,7 +120,7 @@ Layout layout(const at_problem* pb, const at_delays* dl)
     L.H = is_weno(pb->pde) ? 3 : pb->order / 2;
     L.q = is_weno(pb->pde) ? 1 : pb->order / 2;
     L.S = stages_of(pb->rk);
-    L.R = dl->k_max + L.q + 1;
+    L.R = dl->k_max + L.q + 1 + kRingSlack;
     L.P = pb->n / pb->pe_size;
     L.Tw = window_of(pb->pe_size, L.H);
     L.wpp = pb->pe_size / L.Tw;
@@ -130,8 +137,10 @@ Layout layout(const at_problem* pb, const at_delays* dl)
     off = align256(off + sizeof(double) * L.ring_elems);
     L.off_dlog = off;
     off = align256(off + (size_t)L.S * L.P * 2);
-    L.off_status = off;
+    L.off_status = off;  // status word, then the abort flag of the persistent path
     off = align256(off + 256);
+    L.off_done = off;    // per-PE progress counters of the persistent path
+    off = align256(off + sizeof(int64_t) * (size_t)L.P);
     L.total = off;
     return L;
 }
@@ -192,6 +201,11 @@ struct at_ctx {
     atk::StageArgs base{};
     int64_t level = 0;
     int64_t launched = 0;
+    int path = AT_PATH_AUTO;       // at_set_option(AT_OPT_PATH)
+    int last_path = 0;             // path of the last at_step
+    int64_t persist_cap = 0;       // PEs one cooperative launch can hold (0: unavailable)
+    int64_t wait_limit = 4000000;  // polls of a bounded wait
+    int64_t withhold_pe = -1;
     // tracing (at_profile)
     bool profile = false;
     std::vector<cudaEvent_t> ev;  // pairs: ev[2i] before, ev[2i+1] after launch i
@@ -325,6 +339,11 @@ int at_set_delays(at_ctx* c, const at_delays* dl)
     a.ring = (double*)(c->ws + L.off_ring);
     a.dlog = (uint8_t*)(c->ws + L.off_dlog);
     a.status = (int*)(c->ws + L.off_status);
+    a.abort_flag = (int*)(c->ws + L.off_status + sizeof(int));
+    a.done = (int64_t*)(c->ws + L.off_done);
+    a.wait_limit = c->wait_limit;
+    a.withhold_pe = c->withhold_pe;
+    a.slack = kRingSlack;
     a.N = c->pb.n;
     a.P = L.P;
     a.B = c->pb.pe_size;
@@ -378,13 +397,17 @@ int at_set_delays(at_ctx* c, const at_delays* dl)
     // reset the run: zero ring, delay log and status, then seed level 0
     e = cudaMemsetAsync(a.ring, 0, sizeof(double) * L.ring_elems, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.dlog, 0, (size_t)L.S * L.P * 2, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.status, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.status, 0, 2 * sizeof(int), c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
     atk::StageArgs s = a;
     s.u = c->state;
     e = atk_launch_ring_seed(s, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "ring seed launch");
     c->level = 0;
+    c->persist_cap = (c->pb.pde == AT_ADVDIFF || c->pb.pde == AT_RNS)
+                         ? atk_persist_capacity(c->pb.pde, c->pb.order, c->pb.pe_size, c->device)
+                         : 0;
+    cudaGetLastError();  // an unavailable persistent path is not an error
     c->have_delays = true;
     g_err[0] = 0;
     return AT_OK;
@@ -401,6 +424,29 @@ int at_step(at_ctx* c, int64_t nsteps)
     double* A = (double*)(c->ws + L.off_A);
     double* Bf = (double*)(c->ws + L.off_B);
     double* u = c->state;
+    const bool can_persist = c->persist_cap > 0 && L.P <= c->persist_cap;
+    if (c->path == AT_PATH_PERSISTENT && !can_persist)
+        return fail(AT_EINVAL, "the persistent path needs a central PDE and at most %lld PEs (have %lld)",
+                    (long long)c->persist_cap, (long long)L.P);
+    const bool persist = c->path == AT_PATH_PERSISTENT || (c->path == AT_PATH_AUTO && can_persist);
+    c->last_path = persist ? AT_PATH_PERSISTENT : AT_PATH_STAGE;
+    if (persist) {
+        if (nsteps == 0) return AT_OK;
+        atk::StageArgs a = c->base;
+        a.u = u;
+        a.Y = u;
+        a.wait_limit = c->wait_limit;
+        a.withhold_pe = c->withhold_pe;
+        e = record(c, true);
+        if (e == cudaSuccess) e = atk_launch_persist(a, c->pb.pde, c->pb.order, c->level, nsteps, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
+        e = record(c, false);
+        if (e != cudaSuccess) return cuda_fail(e, "profiling event");
+        c->launched += 2;  // counter reset + the persistent kernel
+        c->level += nsteps;
+        g_err[0] = 0;
+        return AT_OK;
+    }
     for (int64_t i = 0; i < nsteps; ++i) {
         atk::StageArgs a = c->base;
         a.level = c->level;
@@ -433,6 +479,7 @@ int at_run(at_ctx* c, int64_t nsteps)
     cudaError_t e = cudaMemcpyAsync(&status, c->base.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "at_run synchronisation");
+    if (status & 2) return fail(AT_ETIMEOUT, "a bounded wait of the persistent kernel ran out");
     if (status) return fail(AT_EUNSTABLE, "a non-finite value appeared in the state");
     return AT_OK;
 }
@@ -469,7 +516,8 @@ int at_read(at_ctx* c, int what, void* dst, size_t bytes, int dst_on_device)
             if (e != cudaSuccess) return cuda_fail(e, "status read");
         }
         s.level = c->level;
-        s.status = status ? AT_EUNSTABLE : 0;
+        s.status = (status & 2) ? AT_ETIMEOUT : (status ? AT_EUNSTABLE : 0);
+        s.path = c->last_path;
         s.stages = stages_of(c->pb.rk);
         s.nvar = nvar_of(c->pb.pde);
         s.halo = is_weno(c->pb.pde) ? 3 : c->pb.order / 2;
@@ -490,6 +538,25 @@ int at_read(at_ctx* c, int what, void* dst, size_t bytes, int dst_on_device)
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "at_read copy");
     return AT_OK;
+}
+
+int at_set_option(at_ctx* c, int key, int64_t value)
+{
+    if (!c) return fail(AT_EINVAL, "context is NULL");
+    switch (key) {
+    case AT_OPT_PATH:
+        if (value < AT_PATH_AUTO || value > AT_PATH_PERSISTENT) return fail(AT_EINVAL, "unknown path %lld", (long long)value);
+        c->path = (int)value;
+        return AT_OK;
+    case AT_OPT_WAIT_LIMIT:
+        if (value < 1) return fail(AT_EINVAL, "wait limit must be positive");
+        c->wait_limit = value;
+        return AT_OK;
+    case AT_OPT_WITHHOLD_PE:
+        c->withhold_pe = value;
+        return AT_OK;
+    default: return fail(AT_EINVAL, "unknown option %d", key);
+    }
 }
 
 int at_profile(at_ctx* c, int enable)

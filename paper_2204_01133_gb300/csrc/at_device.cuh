@@ -41,6 +41,12 @@ struct StageArgs {
     double cm[2 * AT_HMAX + 1];               // merged advection-diffusion taps
     double prm[16];                           // physics constants (see at.h)
     double k0, k1, k2, k3;                    // derived physics constants
+    // persistent path only
+    int64_t* done;       // per PE: stages completed, as the index n*S + s + 1 [P]
+    int* abort_flag;     // set by the first wait that runs out
+    int64_t wait_limit;  // polls before a wait gives up (bounded spin)
+    int64_t withhold_pe; // fault injection: this PE never publishes (-1: none)
+    int slack;           // ring levels beyond k_max + q + 1
 };
 
 // ---------------------------------------------------------------------------
@@ -65,20 +71,25 @@ __device__ __forceinline__ uint32_t philox_w0(uint32_t c0, uint32_t c1, uint32_t
     return c0;
 }
 
-// Delay seen by PE `pe` at its `side` (0 left, 1 right) for this stage,
+// Delay seen by PE `pe` at its `side` (0 left, 1 right) at (level, stage),
 // clamped so that no level below 0 is ever read.
-__device__ __forceinline__ int keff(const StageArgs& a, int64_t pe, int side)
+__device__ __forceinline__ int keff_at(const StageArgs& a, int64_t level, int stage, int64_t pe, int side)
 {
     if (a.mode == SYNC) return 0;
-    const uint32_t sc = a.per_stage ? (uint32_t)a.stage : 0u;
-    const uint32_t x = philox_w0((uint32_t)a.level, (uint32_t)pe, sc | ((uint32_t)side << 8), a.instance,
+    const uint32_t sc = a.per_stage ? (uint32_t)stage : 0u;
+    const uint32_t x = philox_w0((uint32_t)level, (uint32_t)pe, sc | ((uint32_t)side << 8), a.instance,
                                  a.key0, a.key1);
     int k = 0;
     for (int i = 0; i < a.kmax; ++i) k += ((uint64_t)x >= a.thr[i]) ? 1 : 0;
     const int qq = (a.mode == AT) ? a.q : 0;
-    int64_t avail = a.level - qq;
+    int64_t avail = level - qq;
     if (avail < 0) avail = 0;
     return (int64_t)k < avail ? k : (int)avail;
+}
+
+__device__ __forceinline__ int keff(const StageArgs& a, int64_t pe, int side)
+{
+    return keff_at(a, a.level, a.stage, pe, side);
 }
 
 __device__ __forceinline__ int64_t ring_index(const StageArgs& a, int64_t level, int stage, int64_t pe, int side,

@@ -1,0 +1,305 @@
+// at_persist.cu -- persistent, neighbour-synchronised AT kernel (central PDEs).
+//
+// One CTA owns one virtual PE for a whole run of steps.  The PE's u^n, RK
+// accumulator and stage argument live in shared memory between stages and
+// steps; only the edge windows go through the history ring in global memory
+// (L2), exactly as in the per-stage path, so the arithmetic and its order are
+// identical and the results agree bit for bit.
+//
+// The CTAs synchronise only pairwise, through per-PE progress counters
+// done[p] = n*S + s + 1 after stage s of step n.  Before stage s of step n,
+// PE p needs its neighbour's stage-s argument at level n-k: it waits for
+// done[nbr] >= (n-k)*S + s.  With a drawn delay k >= 1 that is usually
+// already true, so the asynchrony the AT scheme tolerates (Sec. 2.1-2.3)
+// becomes slack in the GPU's own synchronisation: no grid barrier, no launch
+// per stage.  Before overwriting a ring slot a PE waits until both
+// neighbours are past every stage that can still read the slot's old level
+// (the ring keeps `slack` spare levels, so this rarely binds).  Results do
+// not depend on timing: what is read is fixed by the Philox draws.
+//
+// Every wait is bounded (wait_limit polls with a short sleep).  A wait that
+// runs out sets status bit 1 and a global abort flag; every other wait sees
+// the flag and returns, and the kernel ends: the host reports AT_ETIMEOUT.
+// The launch is cooperative, so all CTAs are resident at once.
+#include <cuda/atomic>
+#include <cuda_runtime.h>
+
+#include "at_device.cuh"
+
+namespace atk {
+
+__device__ __forceinline__ int64_t load_acquire(int64_t* p)
+{
+    cuda::atomic_ref<int64_t, cuda::thread_scope_device> r(*p);
+    return r.load(cuda::memory_order_acquire);
+}
+
+__device__ __forceinline__ void store_release(int64_t* p, int64_t v)
+{
+    cuda::atomic_ref<int64_t, cuda::thread_scope_device> r(*p);
+    r.store(v, cuda::memory_order_release);
+}
+
+// bounded wait for *ctr >= target; false if it ran out or another wait did
+__device__ bool wait_ge(const StageArgs& a, int64_t* ctr, int64_t target)
+{
+    if (load_acquire(ctr) >= target) return true;
+    for (int64_t it = 0; it < a.wait_limit; ++it) {
+        __nanosleep(128);
+        if (load_acquire(ctr) >= target) return true;
+        if ((it & 63) == 0 && *(volatile int*)a.abort_flag) return false;
+    }
+    atomicOr(a.status, 2);
+    atomicExch(a.abort_flag, 1);
+    return false;
+}
+
+template <int PDE, int H>
+__global__ void __launch_bounds__(256) persist_central(const StageArgs a, int64_t level0, int64_t nsteps)
+{
+    using P = Phys<PDE>;
+    constexpr int NV = P::NV, ND = P::ND;
+    const int B = a.B, W2 = B + 2 * H, S = a.S;
+    const int64_t pe = blockIdx.x;
+    const int64_t nbr[2] = {pe == 0 ? a.P - 1 : pe - 1, pe == a.P - 1 ? 0 : pe + 1};
+    extern __shared__ double sm[];
+    double* U = sm;                // u^n            [NV][B]
+    double* ACC = U + NV * B;      // RK accumulator [NV][B]
+    double* X = ACC + NV * B;      // stage argument [NV][B]
+    double* G = X + NV * B;        // derived        [ND][W2]
+    double* HS = G + ND * W2;      // halo levels    [2H(q+1)][ND]
+    __shared__ int s_abort;
+    __shared__ int s_k[2];
+    const int nw = (a.mode == AT) ? a.q + 1 : 1;
+
+    for (int i = threadIdx.x; i < NV * B; i += blockDim.x) {
+        const int v = i / B, j = i - v * B;
+        const double x = a.u[v * a.N + pe * B + j];
+        U[i] = x;
+        X[i] = x;
+    }
+    if (threadIdx.x == 0) s_abort = 0;
+    int bad = 0;
+    __syncthreads();
+
+    for (int64_t n = level0; n < level0 + nsteps; ++n) {
+        for (int s = 0; s < S; ++s) {
+            // delays of both PE boundaries; wait for the neighbours' stage-s argument at level n-k
+            if (threadIdx.x < 2) {
+                const int side = threadIdx.x;
+                const int k = keff_at(a, n, s, pe, side);
+                s_k[side] = k;
+                a.dlog[((int64_t)s * a.P + pe) * 2 + side] = (uint8_t)k;
+                if (!wait_ge(a, a.done + nbr[side], (n - k) * S + s)) atomicExch(&s_abort, 1);
+                __threadfence();
+            }
+            __syncthreads();
+            if (s_abort) goto out;
+
+            // fill: own points from shared memory, buffer points from the ring (L2)
+            {
+                const int items = B + 2 * H * nw;
+                for (int it = threadIdx.x; it < items; it += blockDim.x) {
+                    double g[ND];
+                    double Q[NV];
+                    if (it < B) {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) Q[v] = X[v * B + it];
+                        P::derive(a, Q, g);
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) G[d * W2 + H + it] = g[d];
+                    } else {
+                        const int t = it - B;
+                        const int hp = t / nw, l = t - hp * nw;
+                        const int side = hp < H ? 0 : 1;
+                        const int h = side == 0 ? hp : hp - H;
+                        const int k = s_k[side];
+                        const double wl = (a.mode == AT) ? a.w[k][l] : 1.0;
+                        if (wl != 0.0) {
+                            const int64_t base = ring_index(a, n - k - l, s, nbr[side], 1 - side, h, 0);
+#pragma unroll
+                            for (int v = 0; v < NV; ++v) Q[v] = __ldcg(a.ring + base + v);
+                            P::derive(a, Q, g);
+#pragma unroll
+                            for (int d = 0; d < ND; ++d) HS[t * ND + d] = wl * g[d];
+                        } else {
+#pragma unroll
+                            for (int d = 0; d < ND; ++d) HS[t * ND + d] = 0.0;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            for (int c = threadIdx.x; c < 2 * H * ND; c += blockDim.x) {
+                const int hp = c / ND, d = c - hp * ND;
+                double acc = HS[(hp * nw) * ND + d];
+                for (int l = 1; l < nw; ++l) acc += HS[(hp * nw + l) * ND + d];
+                G[d * W2 + (hp < H ? hp : B + hp)] = acc;
+            }
+            __syncthreads();
+
+            // stencil, source and RK update of this stage, in shared memory
+            const bool last = (s == S - 1);
+            for (int it = threadIdx.x; it < NV * B; it += blockDim.x) {
+                const int v = it / B;
+                const int jl = it - v * B;
+                const int c = jl + H;
+                double K = 0.0;
+                const double x = X[it];
+                if constexpr (PDE == ADVDIFF) {
+#pragma unroll
+                    for (int o = -H; o <= H; ++o) K = fma(a.cm[o + H], G[c + o], K);
+                } else {
+                    const double* F = G + v * W2;
+#pragma unroll
+                    for (int o = -H; o <= H; ++o)
+                        if (o != 0) K = fma(a.c1[o + H], F[c + o], K);
+                    if (v > 0) {
+                        const double* D = G + (3 + v) * W2;
+#pragma unroll
+                        for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[c + o], K);
+                    }
+                    if (v == 3) K = fma(-a.prm[4] * x, exp(-a.prm[5] / G[7 * W2 + c]), K);
+                }
+                const double dt = a.dt;
+                const double un = U[it];
+                double y;
+                if (a.rk == RK4) {
+                    if (s == 0) {
+                        ACC[it] = K;
+                        y = fma(0.5 * dt, K, un);
+                    } else if (s < 3) {
+                        ACC[it] = fma(2.0, K, ACC[it]);
+                        y = fma(s == 1 ? 0.5 * dt : dt, K, un);
+                    } else {
+                        y = fma(dt * (1.0 / 6.0), ACC[it] + K, un);
+                    }
+                } else if (a.rk == RK3TVD) {
+                    const double xs = fma(dt, K, x);
+                    if (s == 0) y = xs;
+                    else if (s == 1) y = fma(0.75, un, 0.25 * xs);
+                    else y = fma(1.0 / 3.0, un, (2.0 / 3.0) * xs);
+                } else {
+                    if (s == 0) {
+                        ACC[it] = K;
+                        y = fma(dt, K, un);
+                    } else {
+                        y = fma(0.5 * dt, ACC[it] + K, un);
+                    }
+                }
+                X[it] = y;  // next stage argument (u^{n+1} after the last stage)
+                if (last) U[it] = y;
+                if (!isfinite(y)) bad = 1;
+            }
+            __syncthreads();
+
+            // the new stage argument (n, s+1) or (n+1, 0): wait until its ring slot is free
+            const int64_t I = n * S + s + 1;
+            const int64_t Ln = I / S;
+            const int sn = (int)(I - Ln * S);
+            if (threadIdx.x < 2) {
+                const int64_t need = (Ln - a.slack - 1) * S + sn + 1;
+                if (!wait_ge(a, a.done + nbr[threadIdx.x], need)) atomicExch(&s_abort, 1);
+            }
+            __syncthreads();
+            if (s_abort) goto out;
+            for (int t = threadIdx.x; t < 2 * H * NV; t += blockDim.x) {
+                const int v = t % NV, h = (t / NV) % H, side = t / (NV * H);
+                const int jpe = side == 0 ? h : B - H + h;
+                __stcg(a.ring + ring_index(a, Ln, sn, pe, side, h, v), X[v * B + jpe]);
+                __threadfence();
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && pe != a.withhold_pe) store_release(a.done + pe, I);
+        }
+    }
+out:
+    __syncthreads();
+    for (int i = threadIdx.x; i < NV * B; i += blockDim.x) {
+        const int v = i / B, j = i - v * B;
+        a.Y[v * a.N + pe * B + j] = U[i];
+    }
+    if (bad) atomicOr(a.status, 1);
+}
+
+__global__ void counters_set(int64_t* done, int64_t P, int64_t value, int* abort_flag)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
+        done[i] = value;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *abort_flag = 0;
+}
+
+template <int PDE, int H>
+void* persist_fn()
+{
+    return (void*)persist_central<PDE, H>;
+}
+
+} // namespace atk
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+void* persist_kernel(int pde, int order)
+{
+    if (pde == atk::ADVDIFF) {
+        if (order == 2) return atk::persist_fn<atk::ADVDIFF, 1>();
+        if (order == 4) return atk::persist_fn<atk::ADVDIFF, 2>();
+        return atk::persist_fn<atk::ADVDIFF, 3>();
+    }
+    if (pde == atk::RNS) {
+        if (order == 2) return atk::persist_fn<atk::RNS, 1>();
+        if (order == 4) return atk::persist_fn<atk::RNS, 2>();
+        return atk::persist_fn<atk::RNS, 3>();
+    }
+    return nullptr;
+}
+} // namespace
+
+size_t atk_persist_smem_bytes(int pde, int B, int H)
+{
+    const int nv = pde == atk::RNS ? 4 : 1, nd = pde == atk::RNS ? 8 : 1;
+    return sizeof(double) * ((size_t)3 * nv * B + (size_t)nd * (B + 2 * H) + (size_t)2 * H * (AT_QMAX + 1) * nd);
+}
+
+int atk_persist_block(int pde, int B)
+{
+    const int nv = pde == atk::RNS ? 4 : 1;
+    int want = nv * B;
+    if (want > 256) want = 256;
+    want = ((want + 31) / 32) * 32;
+    return want < 64 ? 64 : want;
+}
+
+// how many PEs one cooperative launch can hold (0: not available)
+int64_t atk_persist_capacity(int pde, int order, int B, int device)
+{
+    void* fn = persist_kernel(pde, order);
+    if (!fn) return 0;
+    const int H = order / 2;
+    const size_t smem = atk_persist_smem_bytes(pde, B, H);
+    if (smem > 200 * 1024) return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int per_sm = 0, sms = 0, coop = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, atk_persist_block(pde, B), smem) != cudaSuccess)
+        return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop) return 0;
+    return (int64_t)per_sm * sms;
+}
+
+cudaError_t atk_launch_persist(const atk::StageArgs& a, int pde, int order, int64_t level0, int64_t nsteps,
+                               cudaStream_t st)
+{
+    void* fn = persist_kernel(pde, order);
+    if (!fn) return cudaErrorInvalidValue;
+    atk::counters_set<<<(unsigned)((a.P + 255) / 256 < 1024 ? (a.P + 255) / 256 : 1024), 256, 0, st>>>(
+        a.done, a.P, level0 * a.S, a.abort_flag);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = atk_persist_smem_bytes(pde, a.B, order / 2);
+    atk::StageArgs args = a;
+    void* params[] = {(void*)&args, (void*)&level0, (void*)&nsteps};
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)a.P), dim3(atk_persist_block(pde, a.B)), params, smem, st);
+}

@@ -48,9 +48,10 @@ def self_drift(pb, init, steps, seed=0):
     return rel_err(b.state(), a.state())
 
 
-def parity(pb, init, steps, first_tol=TOL_STEP, run_tol=TOL_RUN, check_delays=True, conditioned=False):
+def parity(pb, init, steps, first_tol=TOL_STEP, run_tol=TOL_RUN, check_delays=True, conditioned=False,
+           path="auto"):
     from paper_2204_01133_gb300.api import Solver
-    s = Solver(pb, init)
+    s = Solver(pb, init, path=path)
     o = oracle.Oracle(pb, init)
     s.run(1)
     assert o.run(1) == 0
@@ -72,10 +73,11 @@ def parity(pb, init, steps, first_tol=TOL_STEP, run_tol=TOL_RUN, check_delays=Tr
     return s, o
 
 
-def test_advdiff_literal_config_full_run():
+@pytest.mark.parametrize("path", ["stage", "persistent"])
+def test_advdiff_literal_config_full_run(path):
     """N = 2048, 32 PEs of 64, AT4 + RK4, k uniform on {0..3}, seed 0, 10,000 steps."""
     pb, u0 = W.advdiff(n=2048, pe_size=64, order=4, mode="at", k_max=3, seed=0, cfl=0.075)
-    parity(pb, u0, 10000)
+    parity(pb, u0, 10000, path=path)
 
 
 @pytest.mark.parametrize("mode", ["sync", "as", "at"])
@@ -102,11 +104,12 @@ def test_advdiff_edge_shapes(pe_size, n):
     parity(pb, u0, 60)
 
 
+@pytest.mark.parametrize("path", ["stage", "persistent"])
 @pytest.mark.parametrize("case", ["flame", "ignition"])
-def test_rns_literal_size(case):
+def test_rns_literal_size(case, path):
     """Reacting N-S at N = 16,384 (256 PEs of 64), AT6 + RK4, k uniform on {0..4}."""
     pb, u0 = W.rns(case=case, n=16384, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003)
-    parity(pb, u0, 150)
+    parity(pb, u0, 150, path=path)
 
 
 @pytest.mark.parametrize("mode", ["sync", "as"])
@@ -182,3 +185,74 @@ def test_unstable_run_reports_status():
         s.run(3000)
     assert ei.value.code == api.AT_EUNSTABLE
     assert s.stats().status == api.AT_EUNSTABLE
+
+
+# --------------------------------------------------------------------------
+# persistent, neighbour-synchronised path
+# --------------------------------------------------------------------------
+def _run(pb, init, chunks, path):
+    from paper_2204_01133_gb300.api import Solver
+    s = Solver(pb, init, path=path)
+    for c in chunks:
+        s.run(c)
+    assert s.stats().path == {"stage": 1, "persistent": 2}[path]
+    return s.read_state(), s.read_delays()
+
+
+@pytest.mark.parametrize("maker", ["advdiff", "rns", "advdiff-as", "advdiff-rk3-step", "rns-order4-sync"])
+def test_persistent_equals_per_stage_bitwise(maker):
+    """Same arithmetic in the same order: the two paths agree bit for bit,
+    also when a run is split over several at_step calls."""
+    if maker == "advdiff":
+        pb, u0 = W.advdiff(n=2048, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075)
+    elif maker == "rns":
+        pb, u0 = W.rns(case="flame", n=16384, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003)
+    elif maker == "advdiff-as":
+        pb, u0 = W.advdiff(n=960, pe_size=48, order=6, mode="as", k_max=3, seed=2, cfl=0.01)
+    elif maker == "advdiff-rk3-step":
+        pb, u0 = W.advdiff(n=512, pe_size=16, order=2, mode="at", k_max=2, seed=3, cfl=0.04, rk="rk3tvd",
+                           per_stage=0)
+    else:
+        pb, u0 = W.rns(case="ignition", n=4096, pe_size=32, order=4, mode="sync", k_max=2, seed=1, dt=0.003)
+    a_state, a_del = _run(pb, u0, [200], "stage")
+    b_state, b_del = _run(pb, u0, [200], "persistent")
+    c_state, c_del = _run(pb, u0, [3, 1, 96, 100], "persistent")
+    assert np.array_equal(a_state, b_state) and np.array_equal(a_del, b_del)
+    assert np.array_equal(a_state, c_state) and np.array_equal(a_del, c_del)
+
+
+def test_persistent_after_per_stage_steps():
+    from paper_2204_01133_gb300.api import Solver
+    pb, u0 = W.rns(case="flame", n=16384, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003)
+    ref, _ = _run(pb, u0, [120], "stage")
+    s = Solver(pb, u0, path="stage")
+    s.run(50)
+    s.set_path("persistent")
+    s.run(40)
+    s.set_path("stage")
+    s.run(30)
+    assert np.array_equal(s.read_state(), ref)
+
+
+def test_persistent_wait_runs_out_without_fault():
+    """Fault injection: one PE never announces its progress.  Its neighbours'
+    bounded waits run out, the kernel ends, at_run reports AT_ETIMEOUT, and
+    the same context then runs correctly again."""
+    from paper_2204_01133_gb300 import api
+    pb, u0 = W.rns(case="flame", n=16384, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003)
+    s = api.Solver(pb, u0, path="persistent")
+    s.set_option(api.OPT_WAIT_LIMIT, 20000)
+    s.set_option(api.OPT_WITHHOLD_PE, 17)
+    with pytest.raises(api.AtError) as ei:
+        s.run(50)
+    assert ei.value.code == api.AT_ETIMEOUT
+    assert s.stats().status == api.AT_ETIMEOUT
+    # recover: restore the initial state, clear the fault, rerun
+    s.set_option(api.OPT_WITHHOLD_PE, -1)
+    s.set_option(api.OPT_WAIT_LIMIT, 4000000)
+    s.set_problem(u0)
+    s.set_delays()
+    s.set_path("persistent")
+    s.run(50)
+    ref, _ = _run(pb, u0, [50], "stage")
+    assert np.array_equal(s.read_state(), ref)

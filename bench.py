@@ -39,6 +39,8 @@ WORKLOADS = {
     "detonation-n16777216": dict(kind="detonation", n=1 << 24, pe_size=1024, mode="at", k_max=4, seed=0),
     "rns-flame-n16777216": dict(kind="rns", case="flame", n=1 << 24, pe_size=64, mode="at", k_max=4, seed=0,
                                 dt=0.003),
+    # 4,096 reacting instances, N log-uniform in [256, 8192] (9.4 M points), one batched launch
+    "batched-rns-4096": dict(kind="batched", count=4096, seed=0),
 }
 DEFAULT = "rns-flame-n16384"
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal, at 2070 MHz boost
@@ -152,6 +154,29 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    if WORKLOADS[args.workload]["kind"] == "batched":
+        from paper_2204_01133_gb300 import workloads as W
+        cfg = WORKLOADS[args.workload]
+        inst = W.batched_rns(count=cfg["count"], seed=cfg["seed"], nsteps=args.steps)
+        rng = np.random.default_rng(1)
+        sample = sorted(rng.choice(len(inst), size=8, replace=False).tolist())
+        t0 = time.perf_counter()
+        for i in sample:
+            pb, init, n = inst[i]
+            o = oracle.Oracle(pb, init)
+            o.run(n)
+        dt = time.perf_counter() - t0
+        value = len(sample) / dt
+        what = "%d random instances of the batch, %d RK4 steps each, single thread" % (len(sample), args.steps)
+        print(json.dumps({
+            "impl": "reference", "metric": "batched solves/s", "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "instances": cfg["count"]},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": what},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
     kind, (pb, init) = build_workload(args.workload)
     wl = describe(args.workload, pb)
     n = pb["n"]
@@ -212,6 +237,100 @@ def cpu_baseline(pb, init, budget_s=12.0):
     dt = time.perf_counter() - t0
     return {"value": sample_pb["n"] * steps / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
             "sample": "%s, %d RK steps, single thread" % (what, steps)}
+
+
+def run_batched(args):
+    """4,096 uneven reacting instances advanced together through the batch
+    ABI (one graph-replayed launch for the K timed steps), against the same
+    instances solved one after another through contexts (the plain
+    per-instance launch path), on a random sample of them."""
+    import torch
+    from paper_2204_01133_gb300 import api, build
+    from paper_2204_01133_gb300 import batch as BT
+    from paper_2204_01133_gb300 import workloads as W
+    build.build()
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    cfg = WORKLOADS[args.workload]
+    count = cfg["count"]
+    tune_steps = len(BT.CANDIDATES)
+    total = args.warmup + tune_steps + args.steps
+    inst = W.batched_rns(count=count, seed=cfg["seed"], nsteps=total)
+    points = sum(pb["n"] for pb, _, _ in inst)
+    b = BT.Batch(capacity=count, device=local)
+    for i, (pb, init, n) in enumerate(inst):
+        b.bind(i, pb, init, n)
+    b.run(args.warmup)
+    tune = BT.autotune(b, chunk=1, use_cache=False)
+    torch.cuda.synchronize()
+    peak_meas = fp64_probe(local)
+    l2 = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    l2.zero_()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    b.step(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    for i in range(0, count, 512):
+        assert b.query(i).left == 0
+    solves_s = count / (ms * 1e-3)
+    upd_s = points * args.steps / (ms * 1e-3)
+    # plain per-instance path on a random sample (same instances, same steps)
+    rng = np.random.default_rng(1)
+    sample = sorted(rng.choice(count, size=min(args.plain_sample, count), replace=False).tolist())
+    solvers = []
+    for i in sample:
+        pb, init, _ = inst[i]
+        solvers.append(api.Solver(pb, init, device=local))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in solvers:
+        s.step(args.steps)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain_solves_s = len(sample) / plain_s
+    sample_pts = sum(inst[i][0]["n"] for i in sample)
+    # e2e: host states in, K steps, host states out (pinned), through the batch ABI
+    host = [torch.from_numpy(np.ascontiguousarray(init)).pin_memory() for _, init, _ in inst]
+    b2 = BT.Batch(capacity=count, device=local)
+    b2.set_config(*b.config)
+    outs = [torch.empty_like(h).pin_memory() for h in host]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, (pb, _, _) in enumerate(inst):
+        b2.bind(i, pb, host[i], args.steps)
+    b2.step(args.steps)
+    for i in range(count):
+        outs[i].copy_(b2.state(i), non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    state_bytes = sum(8 * 4 * pb["n"] for pb, _, _ in inst)
+    fl = FLOPS_PER_POINT_STAGE["rns"] * points * 4 * args.steps
+    achieved = fl / (ms * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": "batched solves/s", "value": solves_s, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "instances": count, "points": points,
+                   "solve": "one instance advanced %d RK4 steps" % args.steps, "pde": "rns", "order": 6,
+                   "mode": "at", "k_max": "2..4 per instance", "pe_size": "32|64 per instance",
+                   "l2": "flushed before the timed region", "tuned": {"block": tune["block"],
+                                                                       "ctas_per_sm": tune["ctas_per_sm"]}},
+        "grid_pt_updates_per_s": upd_s,
+        "plain": {"solves_per_s": plain_solves_s, "sample_instances": len(sample), "sample_points": sample_pts,
+                  "path": "one context per instance, at_step(K) each, one stream", "speedup": solves_s / plain_solves_s},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None, "kernel": "batch_run<RNS,3>",
+                     "peak_measured": peak_meas},
+        "e2e": {"value": count / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": state_bytes / args.steps,
+                "d2h_bytes_per_step": state_bytes / args.steps},
+        "gpu_launches": 2, "clocks": clk,
+    }))
 
 
 def run_ours(args):
@@ -329,11 +448,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--plain-sample", type=int, default=256, help="instances timed on the plain path (batched)")
     ap.add_argument("--path", default="auto", choices=["auto", "stage", "persistent"],
                     help="execution path of the library (auto: persistent when the PEs fit on the GPU)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif WORKLOADS[args.workload]["kind"] == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

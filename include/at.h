@@ -174,6 +174,58 @@ int at_profile(at_ctx* ctx, int enable);
 
 int at_destroy(at_ctx* ctx);
 
+/* ---- batched solves ------------------------------------------------------
+ *
+ * Many independent solves (instances) of possibly different PDEs, sizes, PE
+ * sizes, delay models and step counts advance together.  Each instance owns
+ * its state and workspace (caller-owned device memory, sized by
+ * at_workspace_bytes for its own problem and delay model); the batch keeps a
+ * device table of slots.  One launch per kernel variant advances every bound
+ * slot: a persistent grid takes instances largest first from a device queue,
+ * and one CTA runs all stages and steps of an instance.  Each instance's
+ * result is bit-for-bit the one a context would compute for it alone
+ * (instance = its Philox counter word, as for a context).                   */
+typedef struct at_batch at_batch;
+
+typedef struct {
+    at_problem pb;
+    at_delays dl;
+    double* state_dev;      /* [nvar][n] FP64 device array; holds the initial state at bind  */
+    void* workspace_dev;    /* at_workspace_bytes(&pb, &dl) bytes of device memory, 256-B aligned */
+    size_t workspace_bytes;
+    int64_t nsteps;         /* steps this instance is to run in total                         */
+} at_instance;
+
+typedef struct {
+    int64_t level;      /* steps done                                                       */
+    int64_t left;       /* steps still to run                                               */
+    int32_t status;     /* 0 or AT_EUNSTABLE                                                */
+    int32_t bound;      /* 1 while the slot holds an instance                               */
+} at_slot_info;
+
+/* device bytes of the slot table for `capacity` slots */
+size_t at_batch_table_bytes(int64_t capacity);
+/* table_dev: caller-owned device memory of at_batch_table_bytes(capacity), 256-B aligned */
+int at_batch_create(at_batch** out, int device, void* cuda_stream, int64_t capacity, void* table_dev,
+                    size_t table_bytes);
+/* Bind an instance to a free slot: validates it, seeds its history ring from
+ * its state (level 0) and queues it.  Enqueued on the stream. */
+int at_batch_bind(at_batch* b, int64_t slot, const at_instance* inst);
+/* Free a slot (its instance's memory may be reused once the stream has passed). */
+int at_batch_release(at_batch* b, int64_t slot);
+/* Launch configuration: threads per CTA (64..256, multiple of 32), resident
+ * CTAs per SM (1..16, clamped to what fits), and whether at_batch_step replays
+ * a captured CUDA graph (1) or launches directly (0).  Default 256, 3, 1. */
+int at_batch_set_config(at_batch* b, int block, int ctas_per_sm, int use_graph);
+/* Every bound slot with steps left advances min(chunk, steps left).  Enqueued. */
+int at_batch_step(at_batch* b, int64_t chunk);
+/* at_batch_step, then synchronise and return AT_EUNSTABLE if any bound
+ * instance produced a non-finite value (at_batch_query tells which). */
+int at_batch_run(at_batch* b, int64_t chunk);
+/* state of one slot (synchronises the stream) */
+int at_batch_query(at_batch* b, int64_t slot, at_slot_info* info);
+int at_batch_destroy(at_batch* b);
+
 /* ---- allocation-free entry point (no counterpart in the paper) ----------
  *
  * For callers that must not allocate device memory while they run: a host

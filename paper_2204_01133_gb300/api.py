@@ -29,7 +29,9 @@ STAGES = {"rk2": 2, "rk3tvd": 3, "rk4": 4}
 
 # every symbol include/at.h declares
 SYMBOLS = ("at_create", "at_workspace_bytes", "at_set_problem", "at_set_delays", "at_step", "at_run",
-           "at_read", "at_profile", "at_set_option", "at_destroy", "at_last_error", "at_run_noalloc")
+           "at_read", "at_profile", "at_set_option", "at_destroy", "at_last_error", "at_run_noalloc",
+           "at_batch_table_bytes", "at_batch_create", "at_batch_bind", "at_batch_release", "at_batch_set_config",
+           "at_batch_step", "at_batch_run", "at_batch_query", "at_batch_destroy")
 PATH_AUTO, PATH_STAGE, PATH_PERSISTENT = 0, 1, 2
 OPT_PATH, OPT_WAIT_LIMIT, OPT_WITHHOLD_PE = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 8 << 20

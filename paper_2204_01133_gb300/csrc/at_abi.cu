@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -25,6 +26,11 @@ cudaError_t atk_set_smem_limits();
 int64_t atk_persist_capacity(int pde, int order, int B, int device);
 cudaError_t atk_launch_persist(const atk::StageArgs& a, int pde, int order, int64_t level0, int64_t nsteps,
                                cudaStream_t st);
+int atk_batch_variant(int pde, int order);
+cudaError_t atk_launch_batch(int variant, const atk::StageArgs* tab, int64_t* lvl, int64_t* left, const int* order,
+                             int n_order, int* queue, int64_t chunk, int grid, int block, size_t smem, cudaStream_t st);
+int atk_batch_max_ctas_per_sm(int variant, int block, size_t smem);
+cudaError_t atk_launch_batch_status(const atk::StageArgs* tab, const int* slots, int n, int* out, cudaStream_t st);
 
 // spare ring levels beyond k_max + q + 1: how far a PE of the persistent
 // path may run ahead of a neighbour before it must wait to reuse a slot
@@ -186,6 +192,77 @@ void extrap_weights(int q, int k, double* w)
     }
 }
 
+// The argument block of every kernel of one solve: layout of its workspace,
+// delay thresholds, extrapolation weights, pre-scaled stencil coefficients.
+atk::StageArgs build_args(const at_problem* pb, const at_delays* dl, const Layout& L, unsigned char* ws, double* state)
+{
+    atk::StageArgs a{};
+    a.acc = (double*)(ws + L.off_acc);
+    a.ring = (double*)(ws + L.off_ring);
+    a.dlog = (uint8_t*)(ws + L.off_dlog);
+    a.status = (int*)(ws + L.off_status);
+    a.abort_flag = (int*)(ws + L.off_status + sizeof(int));
+    a.done = (int64_t*)(ws + L.off_done);
+    a.wait_limit = (int64_t)4000000;
+    a.withhold_pe = (int64_t)-1;
+    a.slack = kRingSlack;
+    a.N = pb->n;
+    a.P = L.P;
+    a.B = pb->pe_size;
+    a.Tw = L.Tw;
+    a.wpp = L.wpp;
+    a.S = L.S;
+    a.R = L.R;
+    a.H = L.H;
+    a.q = L.q;
+    a.nvar = L.nvar;
+    a.mode = dl->mode;
+    a.kmax = dl->k_max;
+    a.per_stage = dl->per_stage ? 1 : 0;
+    a.rk = pb->rk;
+    a.instance = dl->instance;
+    a.key0 = (uint32_t)(dl->seed & 0xffffffffu);
+    a.key1 = (uint32_t)(dl->seed >> 32);
+    a.dt = pb->dt;
+    thresholds(dl, a.thr);
+    for (int k = 0; k <= dl->k_max; ++k) extrap_weights(L.q, k, a.w[k]);
+    for (int i = 0; i < 16; ++i) a.prm[i] = pb->prm[i];
+    const double dx = pb->dx;
+    if (!is_weno(pb->pde)) {
+        static const double d1_2[3] = {-1, 0, 1}, d2_2[3] = {1, -2, 1};
+        static const double d1_4[5] = {1, -8, 0, 8, -1}, d2_4[5] = {-1, 16, -30, 16, -1};
+        static const double d1_6[7] = {-1, 9, -45, 0, 45, -9, 1}, d2_6[7] = {2, -27, 270, -490, 270, -27, 2};
+        const double* d1 = pb->order == 2 ? d1_2 : (pb->order == 4 ? d1_4 : d1_6);
+        const double* d2 = pb->order == 2 ? d2_2 : (pb->order == 4 ? d2_4 : d2_6);
+        const double den1 = pb->order == 2 ? 2.0 : (pb->order == 4 ? 12.0 : 60.0);
+        const double den2 = pb->order == 2 ? 1.0 : (pb->order == 4 ? 12.0 : 180.0);
+        for (int o = 0; o <= 2 * L.H; ++o) {
+            a.c1[o] = -d1[o] / (den1 * dx);
+            a.c2[o] = d2[o] / (den2 * dx * dx);
+        }
+        if (pb->pde == AT_ADVDIFF) {
+            const double cc = pb->prm[0], aa = pb->prm[1];
+            for (int o = 0; o <= 2 * L.H; ++o)
+                a.cm[o] = -cc * d1[o] / (den1 * dx) + aa * d2[o] / (den2 * dx * dx);
+        } else {
+            const double gam = pb->prm[0], mu = pb->prm[1], Pr = pb->prm[2], Le = pb->prm[3];
+            const double cp = gam / (gam - 1.0);
+            const double lam = mu * cp / Pr;
+            a.k0 = 4.0 / 3.0 * mu;
+            a.k1 = 2.0 / 3.0 * mu;
+            a.k2 = lam;
+            a.k3 = lam / (cp * Le);
+        }
+    } else {
+        a.k0 = 1.0 / dx;
+    }
+    a.bufA = (double*)(ws + L.off_A);
+    a.bufB = (double*)(ws + L.off_B);
+    a.state = state;
+    a.u = state;
+    return a;
+}
+
 } // namespace
 
 struct at_ctx {
@@ -333,67 +410,10 @@ int at_set_delays(at_ctx* c, const at_delays* dl)
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     c->dl = *dl;
     c->L = L;
+    c->base = build_args(&c->pb, dl, L, c->ws, c->state);
+    c->base.wait_limit = c->wait_limit;
+    c->base.withhold_pe = c->withhold_pe;
     atk::StageArgs& a = c->base;
-    a = atk::StageArgs{};
-    a.acc = (double*)(c->ws + L.off_acc);
-    a.ring = (double*)(c->ws + L.off_ring);
-    a.dlog = (uint8_t*)(c->ws + L.off_dlog);
-    a.status = (int*)(c->ws + L.off_status);
-    a.abort_flag = (int*)(c->ws + L.off_status + sizeof(int));
-    a.done = (int64_t*)(c->ws + L.off_done);
-    a.wait_limit = c->wait_limit;
-    a.withhold_pe = c->withhold_pe;
-    a.slack = kRingSlack;
-    a.N = c->pb.n;
-    a.P = L.P;
-    a.B = c->pb.pe_size;
-    a.Tw = L.Tw;
-    a.wpp = L.wpp;
-    a.S = L.S;
-    a.R = L.R;
-    a.H = L.H;
-    a.q = L.q;
-    a.nvar = L.nvar;
-    a.mode = dl->mode;
-    a.kmax = dl->k_max;
-    a.per_stage = dl->per_stage ? 1 : 0;
-    a.rk = c->pb.rk;
-    a.instance = dl->instance;
-    a.key0 = (uint32_t)(dl->seed & 0xffffffffu);
-    a.key1 = (uint32_t)(dl->seed >> 32);
-    a.dt = c->pb.dt;
-    thresholds(dl, a.thr);
-    for (int k = 0; k <= dl->k_max; ++k) extrap_weights(L.q, k, a.w[k]);
-    for (int i = 0; i < 16; ++i) a.prm[i] = c->pb.prm[i];
-    const double dx = c->pb.dx;
-    if (!is_weno(c->pb.pde)) {
-        static const double d1_2[3] = {-1, 0, 1}, d2_2[3] = {1, -2, 1};
-        static const double d1_4[5] = {1, -8, 0, 8, -1}, d2_4[5] = {-1, 16, -30, 16, -1};
-        static const double d1_6[7] = {-1, 9, -45, 0, 45, -9, 1}, d2_6[7] = {2, -27, 270, -490, 270, -27, 2};
-        const double* d1 = c->pb.order == 2 ? d1_2 : (c->pb.order == 4 ? d1_4 : d1_6);
-        const double* d2 = c->pb.order == 2 ? d2_2 : (c->pb.order == 4 ? d2_4 : d2_6);
-        const double den1 = c->pb.order == 2 ? 2.0 : (c->pb.order == 4 ? 12.0 : 60.0);
-        const double den2 = c->pb.order == 2 ? 1.0 : (c->pb.order == 4 ? 12.0 : 180.0);
-        for (int o = 0; o <= 2 * L.H; ++o) {
-            a.c1[o] = -d1[o] / (den1 * dx);
-            a.c2[o] = d2[o] / (den2 * dx * dx);
-        }
-        if (c->pb.pde == AT_ADVDIFF) {
-            const double cc = c->pb.prm[0], aa = c->pb.prm[1];
-            for (int o = 0; o <= 2 * L.H; ++o)
-                a.cm[o] = -cc * d1[o] / (den1 * dx) + aa * d2[o] / (den2 * dx * dx);
-        } else {
-            const double gam = c->pb.prm[0], mu = c->pb.prm[1], Pr = c->pb.prm[2], Le = c->pb.prm[3];
-            const double cp = gam / (gam - 1.0);
-            const double lam = mu * cp / Pr;
-            a.k0 = 4.0 / 3.0 * mu;
-            a.k1 = 2.0 / 3.0 * mu;
-            a.k2 = lam;
-            a.k3 = lam / (cp * Le);
-        }
-    } else {
-        a.k0 = 1.0 / dx;
-    }
     // reset the run: zero ring, delay log and status, then seed level 0
     e = cudaMemsetAsync(a.ring, 0, sizeof(double) * L.ring_elems, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.dlog, 0, (size_t)L.S * L.P * 2, c->stream);
@@ -577,6 +597,333 @@ int at_destroy(at_ctx* c)
     cudaSetDevice(c->device);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     delete c;
+    return AT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched solves
+// ---------------------------------------------------------------------------
+namespace {
+const int kVariants = 8;
+
+struct BatchTable {  // carving of the caller's table memory
+    size_t off_args, off_lvl, off_left, off_order, off_slots, off_status, off_queue, total;
+};
+
+BatchTable batch_table(int64_t cap)
+{
+    BatchTable t{};
+    size_t off = 0;
+    t.off_args = off;
+    off = align256(off + sizeof(atk::StageArgs) * (size_t)cap);
+    t.off_lvl = off;
+    off = align256(off + sizeof(int64_t) * (size_t)cap);
+    t.off_left = off;
+    off = align256(off + sizeof(int64_t) * (size_t)cap);
+    t.off_order = off;  // queue order, grouped by kernel variant
+    off = align256(off + sizeof(int) * (size_t)cap);
+    t.off_slots = off;  // bound slots, for the status gather
+    off = align256(off + sizeof(int) * (size_t)cap);
+    t.off_status = off;
+    off = align256(off + sizeof(int) * (size_t)cap);
+    t.off_queue = off;  // one queue counter per variant
+    off = align256(off + sizeof(int) * kVariants);
+    t.total = off;
+    return t;
+}
+} // namespace
+
+struct at_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t cap = 0;
+    unsigned char* tab = nullptr;
+    BatchTable T{};
+    int sms = 0;
+    int block = 256, ctas_per_sm = 3, use_graph = 1;
+    // host mirrors
+    std::vector<atk::StageArgs> args;
+    std::vector<int64_t> level, left, cost;
+    std::vector<int> variant, bound;
+    std::vector<size_t> smem;
+    std::vector<int> order_h, slots_h, status_h;
+    std::vector<int64_t> lvl_h, left_h;  // staging for uploads
+    int group_begin[kVariants + 1] = {0};
+    size_t group_smem[kVariants] = {0};
+    bool dirty = true;
+    // graph of the last (chunk, order) configuration
+    cudaGraphExec_t gexec = nullptr;
+    int64_t gchunk = -1;
+    cudaStream_t cap_stream = nullptr;
+};
+
+namespace {
+cudaError_t batch_upload_order(at_batch* b)
+{
+    std::vector<std::vector<int>> groups(kVariants);
+    b->slots_h.clear();
+    for (int64_t i = 0; i < b->cap; ++i)
+        if (b->bound[i]) {
+            groups[b->variant[i]].push_back((int)i);
+            b->slots_h.push_back((int)i);
+        }
+    b->order_h.clear();
+    for (int g = 0; g < kVariants; ++g) {
+        // largest remaining work first (longest-processing-time order)
+        std::stable_sort(groups[g].begin(), groups[g].end(),
+                         [&](int x, int y) { return b->cost[x] * b->left[x] > b->cost[y] * b->left[y]; });
+        b->group_begin[g] = (int)b->order_h.size();
+        size_t sm = 0;
+        for (int i : groups[g]) {
+            b->order_h.push_back(i);
+            sm = std::max(sm, b->smem[i]);
+        }
+        b->group_smem[g] = sm;
+    }
+    b->group_begin[kVariants] = (int)b->order_h.size();
+    cudaError_t e = cudaSuccess;
+    if (!b->order_h.empty())
+        e = cudaMemcpyAsync(b->tab + b->T.off_order, b->order_h.data(), sizeof(int) * b->order_h.size(),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !b->slots_h.empty())
+        e = cudaMemcpyAsync(b->tab + b->T.off_slots, b->slots_h.data(), sizeof(int) * b->slots_h.size(),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host staging vectors change later
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    b->dirty = false;
+    return e;
+}
+
+cudaError_t batch_enqueue(at_batch* b, cudaStream_t st, int64_t chunk)
+{
+    cudaError_t e = cudaMemsetAsync(b->tab + b->T.off_queue, 0, sizeof(int) * kVariants, st);
+    for (int g = 0; g < kVariants && e == cudaSuccess; ++g) {
+        const int n = b->group_begin[g + 1] - b->group_begin[g];
+        if (n == 0) continue;
+        const size_t smem = b->group_smem[g];
+        int per_sm = atk_batch_max_ctas_per_sm(g, b->block, smem);
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        per_sm = std::min(per_sm, b->ctas_per_sm);
+        const int grid = std::min(n, per_sm * b->sms);
+        e = atk_launch_batch(g, (const atk::StageArgs*)(b->tab + b->T.off_args), (int64_t*)(b->tab + b->T.off_lvl),
+                             (int64_t*)(b->tab + b->T.off_left), (const int*)(b->tab + b->T.off_order) + b->group_begin[g],
+                             n, (int*)(b->tab + b->T.off_queue) + g, chunk, grid, b->block, smem, st);
+    }
+    return e;
+}
+} // namespace
+
+size_t at_batch_table_bytes(int64_t capacity)
+{
+    if (capacity <= 0 || capacity > (1 << 24)) return 0;
+    return batch_table(capacity).total;
+}
+
+int at_batch_create(at_batch** out, int device, void* cuda_stream, int64_t capacity, void* table_dev,
+                    size_t table_bytes)
+{
+    if (!out) return fail(AT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (capacity <= 0 || capacity > (1 << 24)) return fail(AT_EINVAL, "capacity must be 1..2^24");
+    if (!table_dev || ((uintptr_t)table_dev & 255)) return fail(AT_EINVAL, "table must be 256-byte aligned device memory");
+    if (table_bytes < batch_table(capacity).total)
+        return fail(AT_ENOMEM, "table of %zu bytes is below the %zu bytes needed", table_bytes,
+                    batch_table(capacity).total);
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    at_batch* b = new (std::nothrow) at_batch;
+    if (!b) return fail(AT_ENOMEM, "host allocation failed");
+    b->device = device;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->cap = capacity;
+    b->tab = (unsigned char*)table_dev;
+    b->T = batch_table(capacity);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, device);
+    b->args.resize(capacity);
+    b->level.assign(capacity, 0);
+    b->left.assign(capacity, 0);
+    b->cost.assign(capacity, 0);
+    b->variant.assign(capacity, 0);
+    b->bound.assign(capacity, 0);
+    b->smem.assign(capacity, 0);
+    b->lvl_h.assign(capacity, 0);
+    b->left_h.assign(capacity, 0);
+    e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = atk_set_smem_limits();
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "batch set-up");
+    }
+    *out = b;
+    return AT_OK;
+}
+
+int at_batch_bind(at_batch* b, int64_t slot, const at_instance* in)
+{
+    if (!b || !in) return fail(AT_EINVAL, "batch or instance is NULL");
+    if (slot < 0 || slot >= b->cap) return fail(AT_EINVAL, "slot %lld out of range", (long long)slot);
+    if (b->bound[slot]) return fail(AT_ESTATE, "slot %lld is bound", (long long)slot);
+    int st = check_problem(&in->pb);
+    if (st == AT_OK) st = check_delays(&in->dl);
+    if (st != AT_OK) return st;
+    if (in->nsteps < 0) return fail(AT_EINVAL, "nsteps must be >= 0");
+    if (!in->state_dev || !in->workspace_dev || ((uintptr_t)in->state_dev & 15) || ((uintptr_t)in->workspace_dev & 255))
+        return fail(AT_EINVAL, "state (16-B aligned) and workspace (256-B aligned) must be device memory");
+    const Layout L = layout(&in->pb, &in->dl);
+    if (in->workspace_bytes < L.total)
+        return fail(AT_ENOMEM, "workspace of %zu bytes is below the %zu bytes needed", in->workspace_bytes, L.total);
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    atk::StageArgs a = build_args(&in->pb, &in->dl, L, (unsigned char*)in->workspace_dev, in->state_dev);
+    e = cudaMemsetAsync(a.ring, 0, sizeof(double) * L.ring_elems, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.dlog, 0, (size_t)L.S * L.P * 2, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.status, 0, 2 * sizeof(int), b->stream);
+    if (e == cudaSuccess) e = atk_launch_ring_seed(a, b->stream);
+    b->args[slot] = a;
+    b->lvl_h[slot] = 0;
+    b->left_h[slot] = in->nsteps;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->tab + b->T.off_args + sizeof(atk::StageArgs) * slot, &b->args[slot],
+                            sizeof(atk::StageArgs), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->tab + b->T.off_lvl + sizeof(int64_t) * slot, &b->lvl_h[slot], sizeof(int64_t),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->tab + b->T.off_left + sizeof(int64_t) * slot, &b->left_h[slot], sizeof(int64_t),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch bind");
+    b->level[slot] = 0;
+    b->left[slot] = in->nsteps;
+    b->cost[slot] = (int64_t)L.nvar * in->pb.n * L.S * (is_weno(in->pb.pde) ? 8 : 1);
+    b->variant[slot] = atk_batch_variant(in->pb.pde, in->pb.order);
+    b->smem[slot] = atk_stage_smem_bytes(in->pb.pde, L.Tw, L.H);
+    b->bound[slot] = 1;
+    b->dirty = true;
+    return AT_OK;
+}
+
+int at_batch_release(at_batch* b, int64_t slot)
+{
+    if (!b) return fail(AT_EINVAL, "batch is NULL");
+    if (slot < 0 || slot >= b->cap || !b->bound[slot]) return fail(AT_EINVAL, "slot %lld is not bound", (long long)slot);
+    b->bound[slot] = 0;
+    b->dirty = true;
+    return AT_OK;
+}
+
+int at_batch_set_config(at_batch* b, int block, int ctas_per_sm, int use_graph)
+{
+    if (!b) return fail(AT_EINVAL, "batch is NULL");
+    if (block < 64 || block > 256 || block % 32) return fail(AT_EINVAL, "block must be 64..256, a multiple of 32");
+    if (ctas_per_sm < 1 || ctas_per_sm > 16) return fail(AT_EINVAL, "ctas_per_sm must be 1..16");
+    b->block = block;
+    b->ctas_per_sm = ctas_per_sm;
+    b->use_graph = use_graph ? 1 : 0;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    return AT_OK;
+}
+
+int at_batch_step(at_batch* b, int64_t chunk)
+{
+    if (!b) return fail(AT_EINVAL, "batch is NULL");
+    if (chunk < 0) return fail(AT_EINVAL, "chunk must be >= 0");
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if (b->dirty) {
+        e = batch_upload_order(b);
+        if (e != cudaSuccess) return cuda_fail(e, "batch queue upload");
+    }
+    if (chunk == 0 || b->order_h.empty()) return AT_OK;
+    if (b->use_graph) {
+        if (!b->gexec || b->gchunk != chunk) {
+            if (b->gexec) {
+                cudaGraphExecDestroy(b->gexec);
+                b->gexec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t le = batch_enqueue(b, b->cap_stream, chunk);
+                e = cudaStreamEndCapture(b->cap_stream, &g);
+                if (le != cudaSuccess) e = le;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+            b->gchunk = chunk;
+        }
+        e = cudaGraphLaunch(b->gexec, b->stream);
+    } else {
+        e = batch_enqueue(b, b->stream, chunk);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    for (int64_t i = 0; i < b->cap; ++i)
+        if (b->bound[i]) {
+            const int64_t n = std::min(chunk, b->left[i]);
+            b->level[i] += n;
+            b->left[i] -= n;
+        }
+    return AT_OK;
+}
+
+int at_batch_run(at_batch* b, int64_t chunk)
+{
+    int st = at_batch_step(b, chunk);
+    if (st != AT_OK) return st;
+    const int n = (int)b->slots_h.size();
+    b->status_h.assign(n, 0);
+    cudaError_t e = atk_launch_batch_status((const atk::StageArgs*)(b->tab + b->T.off_args),
+                                            (const int*)(b->tab + b->T.off_slots), n,
+                                            (int*)(b->tab + b->T.off_status), b->stream);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(b->status_h.data(), b->tab + b->T.off_status, sizeof(int) * n, cudaMemcpyDeviceToHost,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch run");
+    for (int i = 0; i < n; ++i)
+        if (b->status_h[i]) return fail(AT_EUNSTABLE, "slot %d produced a non-finite value", b->slots_h[i]);
+    return AT_OK;
+}
+
+int at_batch_query(at_batch* b, int64_t slot, at_slot_info* info)
+{
+    if (!b || !info) return fail(AT_EINVAL, "batch or info is NULL");
+    if (slot < 0 || slot >= b->cap) return fail(AT_EINVAL, "slot out of range");
+    at_slot_info r{};
+    r.bound = b->bound[slot];
+    if (r.bound) {
+        int64_t dev[2] = {0, 0};
+        int status = 0;
+        cudaError_t e = cudaMemcpyAsync(&dev[0], b->tab + b->T.off_lvl + sizeof(int64_t) * slot, sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&dev[1], b->tab + b->T.off_left + sizeof(int64_t) * slot, sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&status, b->args[slot].status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batch query");
+        r.level = dev[0];
+        r.left = dev[1];
+        r.status = status ? AT_EUNSTABLE : 0;
+    }
+    *info = r;
+    return AT_OK;
+}
+
+int at_batch_destroy(at_batch* b)
+{
+    if (!b) return AT_OK;
+    cudaSetDevice(b->device);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
     return AT_OK;
 }
 

@@ -47,6 +47,10 @@ struct StageArgs {
     int64_t wait_limit;  // polls before a wait gives up (bounded spin)
     int64_t withhold_pe; // fault injection: this PE never publishes (-1: none)
     int slack;           // ring levels beyond k_max + q + 1
+    // batched path: the solve's own buffers (the stage kernels get X/Y/u per launch)
+    double* bufA;
+    double* bufB;
+    double* state;
 };
 
 // ---------------------------------------------------------------------------

@@ -299,6 +299,9 @@ cudaError_t atk_launch_persist(const atk::StageArgs& a, int pde, int order, int6
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = atk_persist_smem_bytes(pde, a.B, order / 2);
+    // the attribute is per kernel, not per context: set it for this launch
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     atk::StageArgs args = a;
     void* params[] = {(void*)&args, (void*)&level0, (void*)&nsteps};
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)a.P), dim3(atk_persist_block(pde, a.B)), params, smem, st);

@@ -28,6 +28,18 @@
 
 namespace atk {
 
+// What changes from one stage evaluation to the next: the level, the stage,
+// the stage argument read by the stencils (X), the output (Y) and u^n.
+struct Cx {
+    int64_t level;
+    int stage;
+    const double* X;
+    double* Y;
+    const double* u;
+};
+
+__device__ __forceinline__ Cx launch_cx(const StageArgs& a) { return Cx{a.level, a.stage, a.X, a.Y, a.u}; }
+
 // ---------------------------------------------------------------------------
 // 1. fill the window
 //
@@ -39,8 +51,9 @@ namespace atk {
 // weighted level contributions: [2 H (q+1)][ND].
 // ---------------------------------------------------------------------------
 template <int PDE, bool WENO>
-__device__ __forceinline__ void fill_window(const StageArgs& a, double* __restrict__ G, double* __restrict__ SP,
-                                            double* __restrict__ HS, int64_t pe, int chunk, int64_t t0, int W2)
+__device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, double* __restrict__ G,
+                                            double* __restrict__ SP, double* __restrict__ HS, int64_t pe, int chunk,
+                                            int64_t t0, int W2)
 {
     using P = Phys<PDE>;
     constexpr int NV = P::NV, ND = P::ND;
@@ -57,7 +70,7 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, double* __restri
             const int i = L0 + it;
             const int64_t m = t0 - H + i;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) Q[v] = a.X[v * a.N + m];
+            for (int v = 0; v < NV; ++v) Q[v] = cx.X[v * a.N + m];
             P::derive(a, Q, g);
 #pragma unroll
             for (int d = 0; d < ND; ++d) G[d * W2 + i] = g[d];
@@ -68,11 +81,11 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, double* __restri
             const int side = hp < L0 ? 0 : 1;
             const int h = side == 0 ? hp : hp - L0;         // position in the neighbour's edge window
             const int64_t nbr = side == 0 ? (pe == 0 ? a.P - 1 : pe - 1) : (pe == a.P - 1 ? 0 : pe + 1);
-            const int k = keff(a, pe, side);
-            if (h == 0 && l == 0) a.dlog[((int64_t)a.stage * a.P + pe) * 2 + side] = (uint8_t)k;
+            const int k = keff_at(a, cx.level, cx.stage, pe, side);
+            if (h == 0 && l == 0) a.dlog[((int64_t)cx.stage * a.P + pe) * 2 + side] = (uint8_t)k;
             const double wl = (a.mode == AT) ? a.w[k][l] : 1.0;
             if (wl != 0.0) {  // a level with weight 0 is not part of the scheme (and may not exist yet)
-                const int64_t base = ring_index(a, a.level - k - l, a.stage, nbr, 1 - side, h, 0);
+                const int64_t base = ring_index(a, cx.level - k - l, cx.stage, nbr, 1 - side, h, 0);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) Q[v] = a.ring[base + v];
                 P::derive(a, Q, g);
@@ -102,42 +115,42 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, double* __restri
 // ---------------------------------------------------------------------------
 // 3. RK update of this stage, ring push, non-finite check
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void rk_update(const StageArgs& a, int v, int64_t j, int jpe, int64_t pe, double K,
-                                          double x)
+__device__ __forceinline__ void rk_update(const StageArgs& a, const Cx& cx, int v, int64_t j, int jpe, int64_t pe,
+                                          double K, double x)
 {
     const int64_t idx = v * a.N + j;
     const double dt = a.dt;
     double y;
     if (a.rk == RK4) {
-        const double un = a.u[idx];
-        if (a.stage == 0) {
+        const double un = cx.u[idx];
+        if (cx.stage == 0) {
             a.acc[idx] = K;
             y = fma(0.5 * dt, K, un);
-        } else if (a.stage < 3) {
+        } else if (cx.stage < 3) {
             a.acc[idx] = fma(2.0, K, a.acc[idx]);
-            y = fma(a.stage == 1 ? 0.5 * dt : dt, K, un);
+            y = fma(cx.stage == 1 ? 0.5 * dt : dt, K, un);
         } else {
             y = fma(dt * (1.0 / 6.0), a.acc[idx] + K, un);
         }
     } else if (a.rk == RK3TVD) {
         const double xs = fma(dt, K, x);
-        if (a.stage == 0) {
+        if (cx.stage == 0) {
             y = xs;
-        } else if (a.stage == 1) {
-            y = fma(0.75, a.u[idx], 0.25 * xs);
+        } else if (cx.stage == 1) {
+            y = fma(0.75, cx.u[idx], 0.25 * xs);
         } else {
-            y = fma(1.0 / 3.0, a.u[idx], (2.0 / 3.0) * xs);
+            y = fma(1.0 / 3.0, cx.u[idx], (2.0 / 3.0) * xs);
         }
     } else {  // RK2 (Heun)
-        const double un = a.u[idx];
-        if (a.stage == 0) {
+        const double un = cx.u[idx];
+        if (cx.stage == 0) {
             a.acc[idx] = K;
             y = fma(dt, K, un);
         } else {
             y = fma(0.5 * dt, a.acc[idx] + K, un);
         }
     }
-    a.Y[idx] = y;
+    cx.Y[idx] = y;
     if (!isfinite(y)) atomicOr(a.status, 1);
     int side = -1, h = 0;
     if (jpe < a.H) {
@@ -148,8 +161,8 @@ __device__ __forceinline__ void rk_update(const StageArgs& a, int v, int64_t j, 
         h = jpe - (a.B - a.H);
     }
     if (side >= 0) {
-        const bool last = (a.stage == a.S - 1);
-        a.ring[ring_index(a, last ? a.level + 1 : a.level, last ? 0 : a.stage + 1, pe, side, h, v)] = y;
+        const bool last = (cx.stage == a.S - 1);
+        a.ring[ring_index(a, last ? cx.level + 1 : cx.level, last ? 0 : cx.stage + 1, pe, side, h, v)] = y;
     }
 }
 
@@ -157,19 +170,17 @@ __device__ __forceinline__ void rk_update(const StageArgs& a, int v, int64_t j, 
 // central stencils: advection-diffusion and reacting Navier-Stokes
 // ---------------------------------------------------------------------------
 template <int PDE, int H>
-__global__ void __launch_bounds__(256) stage_central(const StageArgs a)
+__device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx, int64_t win, double* sm)
 {
     using P = Phys<PDE>;
     constexpr int NV = P::NV;
-    extern __shared__ double sm[];
     const int W2 = a.Tw + 2 * H;
     double* G = sm;
     double* HS = G + P::ND * W2;
-    const int64_t win = blockIdx.x;
     const int64_t pe = win / a.wpp;
     const int chunk = (int)(win - pe * a.wpp);
     const int64_t t0 = pe * a.B + (int64_t)chunk * a.Tw;
-    fill_window<PDE, false>(a, G, nullptr, HS, pe, chunk, t0, W2);
+    fill_window<PDE, false>(a, cx, G, nullptr, HS, pe, chunk, t0, W2);
     __syncthreads();
     const int items = NV * a.Tw;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -192,11 +203,18 @@ __global__ void __launch_bounds__(256) stage_central(const StageArgs a)
 #pragma unroll
                 for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[c + o], K);
             }
-            x = a.X[v * a.N + j];
+            x = cx.X[v * a.N + j];
             if (v == 3) K = fma(-a.prm[4] * x, exp(-a.prm[5] / G[7 * W2 + c]), K);
         }
-        rk_update(a, v, j, chunk * a.Tw + jl, pe, K, x);
+        rk_update(a, cx, v, j, chunk * a.Tw + jl, pe, K, x);
     }
+}
+
+template <int PDE, int H>
+__global__ void __launch_bounds__(256) stage_central(const StageArgs a)
+{
+    extern __shared__ double sm[];
+    central_window<PDE, H>(a, launch_cx(a), blockIdx.x, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -226,12 +244,11 @@ __device__ __forceinline__ double weno5(double f0, double f1, double f2, double 
 // WENO5 / AT-WENO5 fluxes: reactive Euler and scalar advection
 // ---------------------------------------------------------------------------
 template <int PDE>
-__global__ void __launch_bounds__(256) stage_weno(const StageArgs a)
+__device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, int64_t win, double* sm)
 {
     using P = Phys<PDE>;
     constexpr int NV = P::NV, ND = P::ND;
     constexpr int H = 3;
-    extern __shared__ double sm[];
     const int Tw = a.Tw;
     const int W2 = Tw + 2 * H;
     const int E = Tw + 1;  // edges of the window: edge e sits between points e-1 and e
@@ -240,11 +257,10 @@ __global__ void __launch_bounds__(256) stage_weno(const StageArgs a)
     double* LAM = SP + W2;
     double* REC = LAM + E;
     double* HS = REC + NV * 2 * E;
-    const int64_t win = blockIdx.x;
     const int64_t pe = win / a.wpp;
     const int chunk = (int)(win - pe * a.wpp);
     const int64_t t0 = pe * a.B + (int64_t)chunk * Tw;
-    fill_window<PDE, true>(a, G, SP, HS, pe, chunk, t0, W2);
+    fill_window<PDE, true>(a, cx, G, SP, HS, pe, chunk, t0, W2);
     __syncthreads();
     for (int e = threadIdx.x; e < E; e += blockDim.x)
         LAM[e] = 0.5 * fmax(SP[e - 1 + H], SP[e + H]);  // half the edge's local wave speed
@@ -288,8 +304,70 @@ __global__ void __launch_bounds__(256) stage_weno(const StageArgs a)
                 K = fma(-a.prm[1] * Q[3], exp(-a.prm[2] * Q[0] / p), K);
             }
         }
-        rk_update(a, v, j, chunk * Tw + jl, pe, K, x);
+        rk_update(a, cx, v, j, chunk * Tw + jl, pe, K, x);
     }
+}
+
+template <int PDE>
+__global__ void __launch_bounds__(256) stage_weno(const StageArgs a)
+{
+    extern __shared__ double sm[];
+    weno_window<PDE>(a, launch_cx(a), blockIdx.x, sm);
+}
+
+// ---------------------------------------------------------------------------
+// batched solves: a persistent grid pulls whole instances (largest first) from
+// a queue; one CTA runs every stage and step of its instance, so all of an
+// instance's PE-to-PE dependencies stay inside the CTA (a barrier between
+// stages, none between CTAs).  Per-slot level and remaining steps live on
+// the device, so a launch is the same from one chunk of steps to the next.
+// ---------------------------------------------------------------------------
+template <int PDE, int H, bool WENO>
+__global__ void __launch_bounds__(256) batch_run(const StageArgs* __restrict__ tab, int64_t* lvl, int64_t* left,
+                                                 const int* __restrict__ order, int n_order, int* queue,
+                                                 int64_t chunk)
+{
+    extern __shared__ double sm[];
+    __shared__ int s_q;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_q = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = s_q;
+        if (q >= n_order) return;
+        const int slot = order[q];
+        const StageArgs& a = tab[slot];
+        const int64_t L0 = lvl[slot];
+        const int64_t rem = left[slot];
+        const int64_t nst = rem < chunk ? rem : chunk;
+        const int64_t nwin = a.P * a.wpp;
+        for (int64_t n = L0; n < L0 + nst; ++n) {
+            for (int s = 0; s < a.S; ++s) {
+                // same buffers, stage by stage, as the per-stage launch sequence
+                const double* X = (s == 0) ? a.state : ((s & 1) ? a.bufA : a.bufB);
+                double* Y = (s == a.S - 1) ? a.state : ((s & 1) ? a.bufB : a.bufA);
+                const Cx cx{n, s, X, Y, a.state};
+                for (int64_t w = 0; w < nwin; ++w) {
+                    if constexpr (WENO)
+                        weno_window<PDE>(a, cx, w, sm);
+                    else
+                        central_window<PDE, H>(a, cx, w, sm);
+                    __syncthreads();
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
+            lvl[slot] = L0 + nst;
+            left[slot] = rem - nst;
+        }
+    }
+}
+
+// copy every slot's status word into one array (one read for the host)
+__global__ void batch_status(const StageArgs* __restrict__ tab, const int* __restrict__ slots, int n, int* out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = *tab[slots[i]].status;
 }
 
 // seed the ring with the edge windows of the state at level 0, stage 0
@@ -384,4 +462,56 @@ cudaError_t atk_set_smem_limits()
         if (e != cudaSuccess) return e;
     }
     return e;
+}
+
+// ---------------------------------------------------------------------------
+// batched path launchers.  Kernel variants: 0..2 advection-diffusion with
+// H = 1..3, 3..5 reacting N-S with H = 1..3, 6 reactive Euler, 7 scalar WENO.
+// ---------------------------------------------------------------------------
+int atk_batch_variant(int pde, int order)
+{
+    if (pde == atk::ADVDIFF) return order / 2 - 1;
+    if (pde == atk::RNS) return 3 + order / 2 - 1;
+    return pde == atk::EULER ? 6 : 7;
+}
+
+static void* batch_fn(int variant)
+{
+    switch (variant) {
+    case 0: return (void*)atk::batch_run<atk::ADVDIFF, 1, false>;
+    case 1: return (void*)atk::batch_run<atk::ADVDIFF, 2, false>;
+    case 2: return (void*)atk::batch_run<atk::ADVDIFF, 3, false>;
+    case 3: return (void*)atk::batch_run<atk::RNS, 1, false>;
+    case 4: return (void*)atk::batch_run<atk::RNS, 2, false>;
+    case 5: return (void*)atk::batch_run<atk::RNS, 3, false>;
+    case 6: return (void*)atk::batch_run<atk::EULER, 3, true>;
+    default: return (void*)atk::batch_run<atk::ADV_WENO, 3, true>;
+    }
+}
+
+cudaError_t atk_launch_batch(int variant, const atk::StageArgs* tab, int64_t* lvl, int64_t* left, const int* order,
+                             int n_order, int* queue, int64_t chunk, int grid, int block, size_t smem, cudaStream_t st)
+{
+    void* fn = batch_fn(variant);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* params[] = {(void*)&tab, (void*)&lvl, (void*)&left, (void*)&order, (void*)&n_order, (void*)&queue,
+                      (void*)&chunk};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(block), params, smem, st);
+}
+
+int atk_batch_max_ctas_per_sm(int variant, int block, size_t smem)
+{
+    int n = 0;
+    if (cudaFuncSetAttribute(batch_fn(variant), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_fn(variant), block, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t atk_launch_batch_status(const atk::StageArgs* tab, const int* slots, int n, int* out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    atk::batch_status<<<(n + 255) / 256, 256, 0, st>>>(tab, slots, n, out);
+    return cudaGetLastError();
 }

@@ -118,9 +118,10 @@ def rns_conserved(rho, u, T, Y, prm) -> np.ndarray:
 
 
 def rns(case="flame", n=16384, pe_size=64, order=6, mode="at", k_max=4, dist="uniform", prob=(),
-        seed=0, per_stage=1, dt=RNS_DT, T_init=3.0, Y_init=1.0, prm=None):
-    """Premixed flame from a periodic double-tanh burnt region, or homogeneous
-    autoignition at ``T_init`` with a 1 % Gaussian temperature bump."""
+        seed=0, per_stage=1, dt=RNS_DT, T_init=3.0, Y_init=1.0, prm=None, T_unburnt=1.0, instance=0):
+    """Premixed flame from a periodic double-tanh burnt region in unburnt gas
+    at ``T_unburnt``, or homogeneous autoignition at ``T_init`` with a 1 %
+    Gaussian temperature bump."""
     prm = list(prm) if prm is not None else rns_prm()
     dx = 1.0
     x = np.arange(n, dtype=np.float64) * dx
@@ -130,7 +131,7 @@ def rns(case="flame", n=16384, pe_size=64, order=6, mode="at", k_max=4, dist="un
     if case == "flame":
         w = 10.0 * dx
         s = 0.5 * (np.tanh((x - 0.375 * L) / w) - np.tanh((x - 0.625 * L) / w))
-        T = 1.0 + (qc / cp) * Y_init * s
+        T = T_unburnt + (qc / cp) * Y_init * s
         Y = Y_init * (1.0 - s)
     elif case == "ignition":
         sig = 0.05 * L
@@ -144,7 +145,7 @@ def rns(case="flame", n=16384, pe_size=64, order=6, mode="at", k_max=4, dist="un
     init = rns_conserved(rho, u, T, Y, prm)
     pb = base_problem(pde="rns", order=order, rk="rk4", n=n, pe_size=pe_size, dx=dx, dt=dt,
                       prm=prm, mode=mode, k_max=k_max, dist=dist, prob=list(prob), seed=seed,
-                      per_stage=per_stage)
+                      per_stage=per_stage, instance=instance)
     return pb, init
 
 
@@ -261,6 +262,29 @@ def entropy_wave(n=256, pe_size=32, mode="sync", k_max=1, dist="uniform", prob=(
     pb = base_problem(pde="euler", rk=rk, n=n, pe_size=pe_size, dx=dx, dt=dt, prm=prm, mode=mode,
                       k_max=k_max, dist=dist, prob=list(prob), seed=seed)
     return pb, init
+
+
+# --------------------------------------------------------------------------
+# Batched reacting instances: N log-uniform in [256, 8192], initial (unburnt)
+# temperature uniform in [900, 1400] K-equivalent (T / 300 K), equivalence
+# ratio uniform in [0.5, 1.5] (initial fuel fraction 0.5 * phi), PE size in
+# {32, 64}, largest delay in {2, 3, 4}, half flames and half ignitions.
+# --------------------------------------------------------------------------
+def batched_rns(count=4096, seed=0, nsteps=100, dt=0.002, n_min=256, n_max=8192):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        B = int(rng.choice([32, 64]))
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max))) / B)) * B
+        n = max(n, 4 * B)
+        T0 = float(rng.uniform(900.0, 1400.0)) / 300.0
+        phi = float(rng.uniform(0.5, 1.5))
+        k_max = int(rng.choice([2, 3, 4]))
+        case = "flame" if i % 2 == 0 else "ignition"
+        pb, init = rns(case=case, n=n, pe_size=B, mode="at", k_max=k_max, seed=seed * 1000003 + i, dt=dt,
+                       T_init=T0, T_unburnt=T0, Y_init=0.5 * phi, instance=i)
+        out.append((pb, init, nsteps))
+    return out
 
 
 CONFIGS = {

@@ -114,3 +114,17 @@ def test_calls_out_of_order_and_without_gpu(L):
         assert rc in (api.AT_ECUDA, api.AT_EINVAL)
         assert L.at_last_error()
     assert L.at_step(None, 1) == api.AT_EINVAL
+
+
+def test_batch_table_and_validation(L):
+    import ctypes
+    from paper_2204_01133_gb300 import api, batch
+    assert batch.table_bytes(0) == 0
+    t1, t2 = batch.table_bytes(1), batch.table_bytes(4096)
+    assert t1 > 0 and t2 > t1 and t2 % 256 == 0
+    h = ctypes.c_void_p()
+    batch._lib()
+    # a misaligned or too small table is refused before any CUDA call
+    assert L.at_batch_create(ctypes.byref(h), 0, None, 16, ctypes.c_void_p(256 + 8), 1 << 20) == api.AT_EINVAL
+    assert L.at_batch_create(ctypes.byref(h), 0, None, 16, ctypes.c_void_p(256), 16) == api.AT_ENOMEM
+    assert L.at_batch_create(ctypes.byref(h), 0, None, 0, ctypes.c_void_p(256), 1 << 20) == api.AT_EINVAL

@@ -1,0 +1,104 @@
+"""Batched solves on the GPU: every instance of a mixed batch must equal,
+bit for bit, the same instance solved alone through a context (same
+kernels' arithmetic, same delay stream), whatever the chunking, slot reuse,
+launch configuration or graph replay; and the standalone solves are pinned
+to the CPU oracle by test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+from paper_2204_01133_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2204_01133_gb300 import build
+    build.build()
+
+
+def mixed_instances():
+    out = []
+    for i, (pb, init, _) in enumerate(W.batched_rns(count=10, seed=3, nsteps=0, n_max=2048)):
+        out.append((pb, init, 23 + 7 * i))
+    pb, init = W.rns(case="flame", n=1536, pe_size=48, order=4, mode="as", k_max=3, seed=5, dt=0.003, instance=77)
+    out.append((pb, init, 40))
+    pb, init = W.advdiff(n=2048, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075)
+    out.append((dict(pb, instance=78), init, 60))
+    pb, init = W.advdiff(n=960, pe_size=48, order=2, mode="sync", k_max=1, seed=2, cfl=0.05, rk="rk2")
+    out.append((dict(pb, instance=79), init, 33))
+    pb, init = W.detonation(n=4096, pe_size=512, mode="at", k_max=4, seed=9)
+    out.append((dict(pb, instance=80), init, 25))
+    pb, init = W.adv_weno(n=512, pe_size=32, mode="at", k_max=3, seed=4, dt_coef=2.0)
+    out.append((dict(pb, instance=81), init, 30))
+    return out
+
+
+def alone(pb, init, nsteps):
+    from paper_2204_01133_gb300.api import Solver
+    s = Solver(pb, init, path="stage")
+    s.run(nsteps)
+    return s.read_state(), s.read_delays()
+
+
+@pytest.mark.parametrize("config", [(256, 3, True), (128, 6, False), (256, 1, True)])
+def test_batch_equals_alone_bitwise(config):
+    from paper_2204_01133_gb300.batch import Batch
+    inst = mixed_instances()
+    ref = [alone(pb, init, n)[0] for pb, init, n in inst]
+    b = Batch(capacity=len(inst) + 3)
+    b.set_config(*config)
+    for i, (pb, init, n) in enumerate(inst):
+        b.bind(i, pb, init, n)
+    while any(b.query(i).left > 0 for i in range(len(inst))):
+        b.run(9)
+    for i, (pb, init, n) in enumerate(inst):
+        info = b.query(i)
+        assert info.level == n and info.left == 0 and info.status == 0
+        got = b.state(i).cpu().numpy()
+        assert np.array_equal(got, ref[i]), (i, pb["pde"], np.abs(got - ref[i]).max())
+
+
+def test_batch_slot_reuse_and_late_admission():
+    """Continuous batching: a finished instance's slot is released and a new
+    instance bound while the others are mid-run; every result still equals
+    the instance solved alone."""
+    from paper_2204_01133_gb300.batch import Batch
+    inst = mixed_instances()[:6]
+    extra = W.batched_rns(count=12, seed=8, nsteps=0, n_max=1024)[10:]
+    b = Batch(capacity=6)
+    for i, (pb, init, n) in enumerate(inst):
+        b.bind(i, pb, init, n)
+    b.run(25)                        # instance 0 (23 steps) is done
+    assert b.query(0).left == 0
+    done0 = b.release(0)
+    got0 = done0["state"].cpu().numpy()
+    assert np.array_equal(got0, alone(*inst[0])[0])
+    pb, init, _ = extra[0]
+    b.bind(0, pb, init, 31)          # late admission into the freed slot
+    while any(b.query(i).left > 0 for i in range(6)):
+        b.run(10)
+    assert np.array_equal(b.state(0).cpu().numpy(), alone(pb, init, 31)[0])
+    for i in range(1, 6):
+        assert np.array_equal(b.state(i).cpu().numpy(), alone(*inst[i])[0])
+
+
+def test_autotuner_keeps_results_and_picks_a_candidate(tmp_path, monkeypatch):
+    from paper_2204_01133_gb300 import batch as BT
+    monkeypatch.setenv("AT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    inst = W.batched_rns(count=24, seed=11, nsteps=0, n_max=4096)
+    b = BT.Batch(capacity=24)
+    for i, (pb, init, _) in enumerate(inst):
+        b.bind(i, pb, init, 40)
+    res = BT.autotune(b, chunk=2, candidates=[(256, 2), (128, 4), (256, 4)])
+    assert (res["block"], res["ctas_per_sm"]) in [(256, 2), (128, 4), (256, 4)]
+    while any(b.query(i).left > 0 for i in range(24)):
+        b.run(7)
+    for i in (0, 5, 23):
+        pb, init, _ = inst[i]
+        assert np.array_equal(b.state(i).cpu().numpy(), alone(pb, init, 40)[0])
+    again = BT.autotune(b, chunk=2, candidates=[(256, 2), (128, 4), (256, 4)])
+    assert again["cached"] and again["block"] == res["block"]

@@ -256,3 +256,16 @@ def test_persistent_wait_runs_out_without_fault():
     s.run(50)
     ref, _ = _run(pb, u0, [50], "stage")
     assert np.array_equal(s.read_state(), ref)
+
+
+def test_contexts_of_different_pe_sizes_interleaved():
+    """Several contexts set up first and stepped afterwards, with different
+    PE sizes (and so different shared-memory needs) on the persistent path."""
+    from paper_2204_01133_gb300.api import Solver
+    probs = [W.rns(case="flame", n=2048, pe_size=B, mode="at", k_max=4, seed=B, dt=0.003) for B in (64, 32, 128)]
+    solvers = [Solver(pb, u0) for pb, u0 in probs]
+    for s in solvers:
+        s.run(20)
+    for (pb, u0), s in zip(probs, solvers):
+        assert s.stats().path == 2
+        assert np.array_equal(s.read_state(), _run(pb, u0, [20], "stage")[0])

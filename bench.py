@@ -41,6 +41,9 @@ WORKLOADS = {
                                 dt=0.003),
     # 4,096 reacting instances, N log-uniform in [256, 8192] (9.4 M points), one batched launch
     "batched-rns-4096": dict(kind="batched", count=4096, seed=0),
+    # Poisson arrivals at 2,000 requests/s of the three problem types, N log-uniform in
+    # [512, 262,144], 100..5,000 steps: a burst of --serve-requests requests
+    "serving-mixed": dict(kind="serving", rate=2000.0, seed=0),
 }
 DEFAULT = "rns-flame-n16384"
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal, at 2070 MHz boost
@@ -174,6 +177,31 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "instances": cfg["count"]},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": what},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+    if WORKLOADS[args.workload]["kind"] == "serving":
+        from paper_2204_01133_gb300 import workloads as W
+        cfg = WORKLOADS[args.workload]
+        stream = W.serving_stream(rate=cfg["rate"], duration=1e9, seed=cfg["seed"], max_requests=args.serve_requests)
+        # bounded sample: the first requests, each run for at most 50 of its steps
+        t0, pts, nreq = time.perf_counter(), 0, 0
+        for d in stream[:3]:
+            pb, init = W.serving_request(d["kind"], d["n"], d["seed"], d["id"])
+            st = min(50, d["steps"])
+            o = oracle.Oracle(pb, init)
+            o.run(st)
+            pts += pb["n"] * st
+            nreq += st / d["steps"]
+        dt = time.perf_counter() - t0
+        value = nreq / dt
+        what = "first 3 requests of the stream, up to 50 of their steps each, single thread"
+        print(json.dumps({
+            "impl": "reference", "metric": "served solves/s", "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": what,
+                             "grid_pt_updates_per_s": pts / dt},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
         return
@@ -319,17 +347,65 @@ def run_batched(args):
         "config": {"workload": args.workload, "instances": count, "points": points,
                    "solve": "one instance advanced %d RK4 steps" % args.steps, "pde": "rns", "order": 6,
                    "mode": "at", "k_max": "2..4 per instance", "pe_size": "32|64 per instance",
-                   "l2": "flushed before the timed region", "tuned": {"block": tune["block"],
-                                                                       "ctas_per_sm": tune["ctas_per_sm"]}},
+                   "l2": "flushed before the timed region",
+                   "tuned": {"mode": ["instance", "flat"][tune["mode"]], "block": tune["block"],
+                             "ctas_per_sm": tune["ctas_per_sm"]}},
         "grid_pt_updates_per_s": upd_s,
         "plain": {"solves_per_s": plain_solves_s, "sample_instances": len(sample), "sample_points": sample_pts,
                   "path": "one context per instance, at_step(K) each, one stream", "speedup": solves_s / plain_solves_s},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None, "kernel": "batch_run<RNS,3>",
+                     "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
+                     "kernel": ["batch_run<RNS,3>", "batch_stage<RNS,3>"][tune["mode"]],
                      "peak_measured": peak_meas},
         "e2e": {"value": count / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": state_bytes / args.steps,
                 "d2h_bytes_per_step": state_bytes / args.steps},
-        "gpu_launches": 2, "clocks": clk,
+        "gpu_launches": 2 if tune["mode"] == 0 else 5 * args.steps + 1, "clocks": clk,
+    }))
+
+
+def run_serving(args):
+    """A burst of the serving stream (arrivals at 2,000 requests/s) served
+    with continuous batching, then the same requests one at a time through a
+    context each; solves/s over the makespan and p50/p99 latency for both."""
+    import torch
+    from paper_2204_01133_gb300 import build
+    from paper_2204_01133_gb300 import workloads as W
+    from paper_2204_01133_gb300.serve import Server, serve_plain, summarize
+    build.build()
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    cfg = WORKLOADS[args.workload]
+    stream = W.serving_stream(rate=cfg["rate"], duration=1e9, seed=cfg["seed"], max_requests=args.serve_requests)
+    # warm-up: a few small requests through both paths (module loads, first launches)
+    warm = W.serving_stream(rate=1e4, duration=1e9, seed=99, n_min=512, n_max=2048, steps_min=10, steps_max=20,
+                            max_requests=4)
+    Server(mem_budget=args.serve_budget_gb << 30).run(warm)
+    serve_plain(warm)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    srv = Server(mem_budget=args.serve_budget_gb << 30, capacity=1024, chunk=args.serve_chunk)
+    done, elapsed = srv.run(stream)
+    clk = clocks.stop()
+    served = summarize(done, elapsed)
+    pdone, pel = serve_plain(stream)
+    plain = summarize(pdone, pel)
+    work = sum(r.n * r.steps for r in done)
+    print(json.dumps({
+        "metric": "served solves/s", "value": served["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "steps": None, "warmup": len(warm), "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "requests": len(stream), "arrival_rate_per_s": cfg["rate"],
+                   "mix": "advdiff | rns | detonation, N log-uniform [512, 262144], steps 100..5000",
+                   "budget_gb": args.serve_budget_gb, "chunk_steps": args.serve_chunk,
+                   "batch_mode": "flat", "ticks": srv.ticks,
+                   "offered_point_steps": work},
+        "served": served, "plain": plain, "speedup_solves_per_s": served["solves_per_s"] / plain["solves_per_s"],
+        "latency_p50_s": served["latency_p50_s"], "latency_p99_s": served["latency_p99_s"],
+        "e2e": {"value": served["solves_per_s"], "unit": "solves/s",
+                "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": "initial states are uploaded at admission; results stay on the device"},
+        "clocks": clk,
     }))
 
 
@@ -449,6 +525,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--plain-sample", type=int, default=256, help="instances timed on the plain path (batched)")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests in the served burst (serving)")
+    ap.add_argument("--serve-budget-gb", type=int, default=16, help="device-memory budget of the server (GB)")
+    ap.add_argument("--serve-chunk", type=int, default=50, help="steps per serving tick")
     ap.add_argument("--path", default="auto", choices=["auto", "stage", "persistent"],
                     help="execution path of the library (auto: persistent when the PEs fit on the GPU)")
     args = ap.parse_args()
@@ -456,6 +535,8 @@ def main():
         run_reference(args)
     elif WORKLOADS[args.workload]["kind"] == "batched":
         run_batched(args)
+    elif WORKLOADS[args.workload]["kind"] == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -203,20 +203,32 @@ typedef struct {
     int32_t bound;      /* 1 while the slot holds an instance                               */
 } at_slot_info;
 
-/* device bytes of the slot table for `capacity` slots */
-size_t at_batch_table_bytes(int64_t capacity);
-/* table_dev: caller-owned device memory of at_batch_table_bytes(capacity), 256-B aligned */
-int at_batch_create(at_batch** out, int device, void* cuda_stream, int64_t capacity, void* table_dev,
-                    size_t table_bytes);
+/* Batch modes (at_batch_set_config): AT_BATCH_INSTANCE, a persistent grid
+ * where one CTA runs all stages and steps of one instance (best for many
+ * small instances); AT_BATCH_FLAT, one launch per stage over the windows of
+ * all instances, so a large instance spreads over every SM (replayed from a
+ * captured graph of chunk x stages launches).  Same results either way. */
+enum { AT_BATCH_INSTANCE = 0, AT_BATCH_FLAT = 1 };
+
+/* device bytes of the slot table for `capacity` slots and, for the flat
+ * mode, a window map of `max_windows` windows (the sum over bound instances
+ * of n / window length) */
+size_t at_batch_table_bytes(int64_t capacity, int64_t max_windows);
+/* table_dev: caller-owned device memory of at_batch_table_bytes(capacity,
+ * max_windows), 256-B aligned */
+int at_batch_create(at_batch** out, int device, void* cuda_stream, int64_t capacity, int64_t max_windows,
+                    void* table_dev, size_t table_bytes);
 /* Bind an instance to a free slot: validates it, seeds its history ring from
- * its state (level 0) and queues it.  Enqueued on the stream. */
+ * its state (level 0) and queues it.  Enqueued on the stream.  AT_ENOMEM when
+ * the window map would overflow. */
 int at_batch_bind(at_batch* b, int64_t slot, const at_instance* inst);
 /* Free a slot (its instance's memory may be reused once the stream has passed). */
 int at_batch_release(at_batch* b, int64_t slot);
-/* Launch configuration: threads per CTA (64..256, multiple of 32), resident
- * CTAs per SM (1..16, clamped to what fits), and whether at_batch_step replays
- * a captured CUDA graph (1) or launches directly (0).  Default 256, 3, 1. */
-int at_batch_set_config(at_batch* b, int block, int ctas_per_sm, int use_graph);
+/* Launch configuration: mode (AT_BATCH_*), threads per CTA (64..256,
+ * multiple of 32), resident CTAs per SM in the instance mode (1..16, clamped
+ * to what fits), and whether at_batch_step replays a captured CUDA graph (1)
+ * or launches directly (0).  Default AT_BATCH_INSTANCE, 256, 3, 1. */
+int at_batch_set_config(at_batch* b, int mode, int block, int ctas_per_sm, int use_graph);
 /* Every bound slot with steps left advances min(chunk, steps left).  Enqueued. */
 int at_batch_step(at_batch* b, int64_t chunk);
 /* at_batch_step, then synchronise and return AT_EUNSTABLE if any bound

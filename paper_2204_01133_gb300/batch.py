@@ -26,12 +26,12 @@ def _lib():
     L = api.lib()
     if not _batch_ready:
         P, vp = ctypes.POINTER, ctypes.c_void_p
-        L.at_batch_table_bytes.argtypes = [ctypes.c_int64]
+        L.at_batch_table_bytes.argtypes = [ctypes.c_int64, ctypes.c_int64]
         L.at_batch_table_bytes.restype = ctypes.c_size_t
-        L.at_batch_create.argtypes = [P(vp), ctypes.c_int, vp, ctypes.c_int64, vp, ctypes.c_size_t]
+        L.at_batch_create.argtypes = [P(vp), ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int64, vp, ctypes.c_size_t]
         L.at_batch_bind.argtypes = [vp, ctypes.c_int64, P(Instance)]
         L.at_batch_release.argtypes = [vp, ctypes.c_int64]
-        L.at_batch_set_config.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.at_batch_set_config.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.at_batch_step.argtypes = [vp, ctypes.c_int64]
         L.at_batch_run.argtypes = [vp, ctypes.c_int64]
         L.at_batch_query.argtypes = [vp, ctypes.c_int64, P(SlotInfo)]
@@ -53,27 +53,33 @@ class SlotInfo(ctypes.Structure):
                 ("bound", ctypes.c_int32)]
 
 
-def table_bytes(capacity: int) -> int:
-    return int(_lib().at_batch_table_bytes(int(capacity)))
+INSTANCE, FLAT = 0, 1
+
+
+def table_bytes(capacity: int, max_windows: int = None) -> int:
+    mw = 128 * int(capacity) if max_windows is None else int(max_windows)
+    return int(_lib().at_batch_table_bytes(int(capacity), mw))
 
 
 class Batch:
     """A device slot table of ``capacity`` independent solves."""
 
-    def __init__(self, capacity: int, device: int = 0, stream=None):
+    def __init__(self, capacity: int, device: int = 0, stream=None, max_windows: int = None):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
         self.capacity = int(capacity)
+        self.max_windows = 128 * self.capacity if max_windows is None else int(max_windows)
         L = _lib()
         self._stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.table = torch.empty(table_bytes(capacity), dtype=torch.uint8, device=self.device)
+        self.table = torch.empty(table_bytes(capacity, self.max_windows), dtype=torch.uint8, device=self.device)
         h = ctypes.c_void_p()
         api.check(L.at_batch_create(ctypes.byref(h), device, ctypes.c_void_p(self._stream.cuda_stream),
-                                    self.capacity, ctypes.c_void_p(self.table.data_ptr()), self.table.numel()))
+                                    self.capacity, self.max_windows, ctypes.c_void_p(self.table.data_ptr()),
+                                    self.table.numel()))
         self._h = h
         self.slots = {}  # slot -> dict(pb, state, ws, nsteps)
-        self.config = (256, 3, 1)
+        self.config = (INSTANCE, 256, 3, 1)
 
     def bind(self, slot: int, pb: dict, init, nsteps: int, state=None, workspace=None):
         torch = self.torch
@@ -101,9 +107,10 @@ class Batch:
         api.check(_lib().at_batch_release(self._h, int(slot)))
         return self.slots.pop(int(slot))
 
-    def set_config(self, block: int = 256, ctas_per_sm: int = 3, use_graph: bool = True):
-        api.check(_lib().at_batch_set_config(self._h, int(block), int(ctas_per_sm), 1 if use_graph else 0))
-        self.config = (int(block), int(ctas_per_sm), 1 if use_graph else 0)
+    def set_config(self, mode: int = INSTANCE, block: int = 256, ctas_per_sm: int = 3, use_graph: bool = True):
+        api.check(_lib().at_batch_set_config(self._h, int(mode), int(block), int(ctas_per_sm),
+                                             1 if use_graph else 0))
+        self.config = (int(mode), int(block), int(ctas_per_sm), 1 if use_graph else 0)
 
     def step(self, chunk: int):
         api.check(_lib().at_batch_step(self._h, int(chunk)))
@@ -135,7 +142,8 @@ class Batch:
 # --------------------------------------------------------------------------
 # autotuner
 # --------------------------------------------------------------------------
-CANDIDATES = [(256, 1), (256, 2), (256, 3), (256, 4), (128, 4), (128, 6), (128, 8)]
+CANDIDATES = [(INSTANCE, 256, 2), (INSTANCE, 256, 3), (INSTANCE, 128, 4), (INSTANCE, 128, 6), (INSTANCE, 128, 8),
+              (FLAT, 256, 1), (FLAT, 128, 1)]
 
 
 def _cache_path():
@@ -170,23 +178,23 @@ def autotune(batch: Batch, chunk: int, candidates=CANDIDATES, use_cache: bool = 
             cache = {}
     key = "%s|%s|%d" % (gpu, sig, chunk)
     if use_cache and key in cache:
-        block, per_sm = cache[key]["block"], cache[key]["ctas_per_sm"]
-        batch.set_config(block, per_sm, True)
-        return dict(cache[key], cached=True)
+        c = cache[key]
+        batch.set_config(c["mode"], c["block"], c["ctas_per_sm"], True)
+        return dict(c, cached=True)
     timings = []
-    for block, per_sm in candidates:
-        batch.set_config(block, per_sm, False)
+    for mode, block, per_sm in candidates:
+        batch.set_config(mode, block, per_sm, False)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
         batch.step(chunk)
         e1.record()
         torch.cuda.synchronize()
-        timings.append((e0.elapsed_time(e1), block, per_sm))
-    ms, block, per_sm = min(timings)
-    batch.set_config(block, per_sm, True)
-    res = {"block": block, "ctas_per_sm": per_sm, "ms": ms, "trials": [[t, b, c] for t, b, c in timings],
-           "cached": False}
+        timings.append((e0.elapsed_time(e1), mode, block, per_sm))
+    ms, mode, block, per_sm = min(timings)
+    batch.set_config(mode, block, per_sm, True)
+    res = {"mode": mode, "block": block, "ctas_per_sm": per_sm, "ms": ms,
+           "trials": [[t, m, b, c] for t, m, b, c in timings], "cached": False}
     if use_cache:
         cache[key] = res
         try:

@@ -30,6 +30,10 @@ int atk_batch_variant(int pde, int order);
 cudaError_t atk_launch_batch(int variant, const atk::StageArgs* tab, int64_t* lvl, int64_t* left, const int* order,
                              int n_order, int* queue, int64_t chunk, int grid, int block, size_t smem, cudaStream_t st);
 int atk_batch_max_ctas_per_sm(int variant, int block, size_t smem);
+cudaError_t atk_launch_batch_stage(int variant, const atk::StageArgs* tab, const int64_t* lvl, const int64_t* left,
+                                   const int* win_slot, const int* win_idx, int nwin, int stage, int block,
+                                   size_t smem, cudaStream_t st);
+cudaError_t atk_launch_batch_advance(int64_t* lvl, int64_t* left, const int* slots, int n, cudaStream_t st);
 cudaError_t atk_launch_batch_status(const atk::StageArgs* tab, const int* slots, int n, int* out, cudaStream_t st);
 
 // spare ring levels beyond k_max + q + 1: how far a PE of the persistent
@@ -607,10 +611,11 @@ namespace {
 const int kVariants = 8;
 
 struct BatchTable {  // carving of the caller's table memory
-    size_t off_args, off_lvl, off_left, off_order, off_slots, off_status, off_queue, total;
+    size_t off_args, off_lvl, off_left, off_order, off_slots, off_status, off_queue, off_wslot, off_widx, total;
+    int64_t max_windows;
 };
 
-BatchTable batch_table(int64_t cap)
+BatchTable batch_table(int64_t cap, int64_t max_windows)
 {
     BatchTable t{};
     size_t off = 0;
@@ -628,6 +633,11 @@ BatchTable batch_table(int64_t cap)
     off = align256(off + sizeof(int) * (size_t)cap);
     t.off_queue = off;  // one queue counter per variant
     off = align256(off + sizeof(int) * kVariants);
+    t.off_wslot = off;  // flat mode: slot and window index of every window, grouped by variant
+    off = align256(off + sizeof(int) * (size_t)max_windows);
+    t.off_widx = off;
+    off = align256(off + sizeof(int) * (size_t)max_windows);
+    t.max_windows = max_windows;
     t.total = off;
     return t;
 }
@@ -640,7 +650,7 @@ struct at_batch {
     unsigned char* tab = nullptr;
     BatchTable T{};
     int sms = 0;
-    int block = 256, ctas_per_sm = 3, use_graph = 1;
+    int mode = 0, block = 256, ctas_per_sm = 3, use_graph = 1;
     // host mirrors
     std::vector<atk::StageArgs> args;
     std::vector<int64_t> level, left, cost;
@@ -650,11 +660,18 @@ struct at_batch {
     std::vector<int64_t> lvl_h, left_h;  // staging for uploads
     int group_begin[kVariants + 1] = {0};
     size_t group_smem[kVariants] = {0};
+    std::vector<int> wslot_h, widx_h;
+    std::vector<int64_t> windows;  // windows per slot
+    int64_t bound_windows = 0;
+    int64_t wbegin[kVariants + 1] = {0};
+    int group_stages[kVariants] = {0};
     bool dirty = true;
     // graph of the last (chunk, order) configuration
     cudaGraphExec_t gexec = nullptr;
     int64_t gchunk = -1;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t branch[kVariants] = {nullptr};
+    cudaEvent_t fork = nullptr, join[kVariants] = {nullptr};
 };
 
 namespace {
@@ -681,7 +698,31 @@ cudaError_t batch_upload_order(at_batch* b)
         b->group_smem[g] = sm;
     }
     b->group_begin[kVariants] = (int)b->order_h.size();
+    // flat-mode window map, in the same order
+    b->wslot_h.clear();
+    b->widx_h.clear();
+    for (int g = 0; g < kVariants; ++g) {
+        b->wbegin[g] = (int64_t)b->wslot_h.size();
+        int smax = 0;
+        for (int q = b->group_begin[g]; q < b->group_begin[g + 1]; ++q) {
+            const int i = b->order_h[q];
+            for (int64_t w = 0; w < b->windows[i]; ++w) {
+                b->wslot_h.push_back(i);
+                b->widx_h.push_back((int)w);
+            }
+            smax = std::max(smax, b->args[i].S);
+        }
+        b->group_stages[g] = smax;
+    }
+    b->wbegin[kVariants] = (int64_t)b->wslot_h.size();
     cudaError_t e = cudaSuccess;
+    if (!b->wslot_h.empty()) {
+        e = cudaMemcpyAsync(b->tab + b->T.off_wslot, b->wslot_h.data(), sizeof(int) * b->wslot_h.size(),
+                            cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->tab + b->T.off_widx, b->widx_h.data(), sizeof(int) * b->widx_h.size(),
+                                cudaMemcpyHostToDevice, b->stream);
+    }
     if (!b->order_h.empty())
         e = cudaMemcpyAsync(b->tab + b->T.off_order, b->order_h.data(), sizeof(int) * b->order_h.size(),
                             cudaMemcpyHostToDevice, b->stream);
@@ -697,41 +738,64 @@ cudaError_t batch_upload_order(at_batch* b)
     return e;
 }
 
+// queue reset, then one launch per non-empty kernel variant; variants run on
+// branch streams forked from and joined back into `st`, so they overlap.
+// Flat mode: per variant, `chunk` x (stages + level advance) launches.
 cudaError_t batch_enqueue(at_batch* b, cudaStream_t st, int64_t chunk)
 {
     cudaError_t e = cudaMemsetAsync(b->tab + b->T.off_queue, 0, sizeof(int) * kVariants, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, st);
+    const atk::StageArgs* tab = (const atk::StageArgs*)(b->tab + b->T.off_args);
+    int64_t* lvl = (int64_t*)(b->tab + b->T.off_lvl);
+    int64_t* left = (int64_t*)(b->tab + b->T.off_left);
     for (int g = 0; g < kVariants && e == cudaSuccess; ++g) {
         const int n = b->group_begin[g + 1] - b->group_begin[g];
         if (n == 0) continue;
         const size_t smem = b->group_smem[g];
-        int per_sm = atk_batch_max_ctas_per_sm(g, b->block, smem);
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        per_sm = std::min(per_sm, b->ctas_per_sm);
-        const int grid = std::min(n, per_sm * b->sms);
-        e = atk_launch_batch(g, (const atk::StageArgs*)(b->tab + b->T.off_args), (int64_t*)(b->tab + b->T.off_lvl),
-                             (int64_t*)(b->tab + b->T.off_left), (const int*)(b->tab + b->T.off_order) + b->group_begin[g],
-                             n, (int*)(b->tab + b->T.off_queue) + g, chunk, grid, b->block, smem, st);
+        const int* order = (const int*)(b->tab + b->T.off_order) + b->group_begin[g];
+        e = cudaStreamWaitEvent(b->branch[g], b->fork, 0);
+        if (e != cudaSuccess) break;
+        if (b->mode == 0) {
+            int per_sm = atk_batch_max_ctas_per_sm(g, b->block, smem);
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            per_sm = std::min(per_sm, b->ctas_per_sm);
+            const int grid = std::min(n, per_sm * b->sms);
+            e = atk_launch_batch(g, tab, lvl, left, order, n, (int*)(b->tab + b->T.off_queue) + g, chunk, grid,
+                                 b->block, smem, b->branch[g]);
+        } else {
+            const int nwin = (int)(b->wbegin[g + 1] - b->wbegin[g]);
+            const int* ws = (const int*)(b->tab + b->T.off_wslot) + b->wbegin[g];
+            const int* wi = (const int*)(b->tab + b->T.off_widx) + b->wbegin[g];
+            for (int64_t step = 0; step < chunk && e == cudaSuccess; ++step) {
+                for (int stage = 0; stage < b->group_stages[g] && e == cudaSuccess; ++stage)
+                    e = atk_launch_batch_stage(g, tab, lvl, left, ws, wi, nwin, stage, b->block, smem, b->branch[g]);
+                if (e == cudaSuccess) e = atk_launch_batch_advance(lvl, left, order, n, b->branch[g]);
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b->join[g], b->branch[g]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join[g], 0);
     }
     return e;
 }
 } // namespace
 
-size_t at_batch_table_bytes(int64_t capacity)
+size_t at_batch_table_bytes(int64_t capacity, int64_t max_windows)
 {
-    if (capacity <= 0 || capacity > (1 << 24)) return 0;
-    return batch_table(capacity).total;
+    if (capacity <= 0 || capacity > (1 << 24) || max_windows < 0 || max_windows > ((int64_t)1 << 30)) return 0;
+    return batch_table(capacity, max_windows).total;
 }
 
-int at_batch_create(at_batch** out, int device, void* cuda_stream, int64_t capacity, void* table_dev,
-                    size_t table_bytes)
+int at_batch_create(at_batch** out, int device, void* cuda_stream, int64_t capacity, int64_t max_windows,
+                    void* table_dev, size_t table_bytes)
 {
     if (!out) return fail(AT_EINVAL, "out is NULL");
     *out = nullptr;
     if (capacity <= 0 || capacity > (1 << 24)) return fail(AT_EINVAL, "capacity must be 1..2^24");
+    if (max_windows < 0 || max_windows > ((int64_t)1 << 30)) return fail(AT_EINVAL, "max_windows out of range");
     if (!table_dev || ((uintptr_t)table_dev & 255)) return fail(AT_EINVAL, "table must be 256-byte aligned device memory");
-    if (table_bytes < batch_table(capacity).total)
+    if (table_bytes < batch_table(capacity, max_windows).total)
         return fail(AT_ENOMEM, "table of %zu bytes is below the %zu bytes needed", table_bytes,
-                    batch_table(capacity).total);
+                    batch_table(capacity, max_windows).total);
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     at_batch* b = new (std::nothrow) at_batch;
@@ -740,7 +804,7 @@ int at_batch_create(at_batch** out, int device, void* cuda_stream, int64_t capac
     b->stream = (cudaStream_t)cuda_stream;
     b->cap = capacity;
     b->tab = (unsigned char*)table_dev;
-    b->T = batch_table(capacity);
+    b->T = batch_table(capacity, max_windows);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, device);
     b->args.resize(capacity);
     b->level.assign(capacity, 0);
@@ -749,9 +813,15 @@ int at_batch_create(at_batch** out, int device, void* cuda_stream, int64_t capac
     b->variant.assign(capacity, 0);
     b->bound.assign(capacity, 0);
     b->smem.assign(capacity, 0);
+    b->windows.assign(capacity, 0);
     b->lvl_h.assign(capacity, 0);
     b->left_h.assign(capacity, 0);
     e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int g = 0; g < kVariants && e == cudaSuccess; ++g) {
+        e = cudaStreamCreateWithFlags(&b->branch[g], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[g], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = atk_set_smem_limits();
     if (e != cudaSuccess) {
         delete b;
@@ -775,6 +845,10 @@ int at_batch_bind(at_batch* b, int64_t slot, const at_instance* in)
     const Layout L = layout(&in->pb, &in->dl);
     if (in->workspace_bytes < L.total)
         return fail(AT_ENOMEM, "workspace of %zu bytes is below the %zu bytes needed", in->workspace_bytes, L.total);
+    const int64_t nwin = L.P * L.wpp;
+    if (b->bound_windows + nwin > b->T.max_windows)
+        return fail(AT_ENOMEM, "the batch's window map holds %lld windows; bound %lld + this %lld",
+                    (long long)b->T.max_windows, (long long)b->bound_windows, (long long)nwin);
     cudaError_t e = cudaSetDevice(b->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     atk::StageArgs a = build_args(&in->pb, &in->dl, L, (unsigned char*)in->workspace_dev, in->state_dev);
@@ -800,6 +874,8 @@ int at_batch_bind(at_batch* b, int64_t slot, const at_instance* in)
     b->cost[slot] = (int64_t)L.nvar * in->pb.n * L.S * (is_weno(in->pb.pde) ? 8 : 1);
     b->variant[slot] = atk_batch_variant(in->pb.pde, in->pb.order);
     b->smem[slot] = atk_stage_smem_bytes(in->pb.pde, L.Tw, L.H);
+    b->windows[slot] = nwin;
+    b->bound_windows += nwin;
     b->bound[slot] = 1;
     b->dirty = true;
     return AT_OK;
@@ -810,15 +886,19 @@ int at_batch_release(at_batch* b, int64_t slot)
     if (!b) return fail(AT_EINVAL, "batch is NULL");
     if (slot < 0 || slot >= b->cap || !b->bound[slot]) return fail(AT_EINVAL, "slot %lld is not bound", (long long)slot);
     b->bound[slot] = 0;
+    b->bound_windows -= b->windows[slot];
+    b->windows[slot] = 0;
     b->dirty = true;
     return AT_OK;
 }
 
-int at_batch_set_config(at_batch* b, int block, int ctas_per_sm, int use_graph)
+int at_batch_set_config(at_batch* b, int mode, int block, int ctas_per_sm, int use_graph)
 {
     if (!b) return fail(AT_EINVAL, "batch is NULL");
+    if (mode != AT_BATCH_INSTANCE && mode != AT_BATCH_FLAT) return fail(AT_EINVAL, "unknown batch mode %d", mode);
     if (block < 64 || block > 256 || block % 32) return fail(AT_EINVAL, "block must be 64..256, a multiple of 32");
     if (ctas_per_sm < 1 || ctas_per_sm > 16) return fail(AT_EINVAL, "ctas_per_sm must be 1..16");
+    b->mode = mode;
     b->block = block;
     b->ctas_per_sm = ctas_per_sm;
     b->use_graph = use_graph ? 1 : 0;
@@ -923,6 +1003,11 @@ int at_batch_destroy(at_batch* b)
     cudaSetDevice(b->device);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (int g = 0; g < kVariants; ++g) {
+        if (b->branch[g]) cudaStreamDestroy(b->branch[g]);
+        if (b->join[g]) cudaEventDestroy(b->join[g]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
     return AT_OK;
 }

@@ -363,6 +363,41 @@ __global__ void __launch_bounds__(256) batch_run(const StageArgs* __restrict__ t
     }
 }
 
+// Flat mode: one launch per stage over the windows of every bound instance
+// of a kernel variant (window w belongs to slot win_slot[w] and is its window
+// win_idx[w]), so large instances spread over all SMs; an instance with no
+// steps left, or whose RK scheme has fewer stages, skips the launch.
+template <int PDE, int H, bool WENO>
+__global__ void __launch_bounds__(256) batch_stage(const StageArgs* __restrict__ tab, const int64_t* __restrict__ lvl,
+                                                   const int64_t* __restrict__ left, const int* __restrict__ win_slot,
+                                                   const int* __restrict__ win_idx, int stage)
+{
+    extern __shared__ double sm[];
+    const int slot = win_slot[blockIdx.x];
+    if (left[slot] <= 0) return;
+    const StageArgs& a = tab[slot];
+    if (stage >= a.S) return;
+    const double* X = (stage == 0) ? a.state : ((stage & 1) ? a.bufA : a.bufB);
+    double* Y = (stage == a.S - 1) ? a.state : ((stage & 1) ? a.bufB : a.bufA);
+    const Cx cx{lvl[slot], stage, X, Y, a.state};
+    if constexpr (WENO)
+        weno_window<PDE>(a, cx, win_idx[blockIdx.x], sm);
+    else
+        central_window<PDE, H>(a, cx, win_idx[blockIdx.x], sm);
+}
+
+// after every stage of a step: advance the level of each slot with steps left
+__global__ void batch_advance(int64_t* lvl, int64_t* left, const int* __restrict__ slots, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int s = slots[i];
+        if (left[s] > 0) {
+            lvl[s] += 1;
+            left[s] -= 1;
+        }
+    }
+}
+
 // copy every slot's status word into one array (one read for the host)
 __global__ void batch_status(const StageArgs* __restrict__ tab, const int* __restrict__ slots, int n, int* out)
 {
@@ -498,6 +533,38 @@ cudaError_t atk_launch_batch(int variant, const atk::StageArgs* tab, int64_t* lv
     void* params[] = {(void*)&tab, (void*)&lvl, (void*)&left, (void*)&order, (void*)&n_order, (void*)&queue,
                       (void*)&chunk};
     return cudaLaunchKernel(fn, dim3(grid), dim3(block), params, smem, st);
+}
+
+static void* batch_stage_fn(int variant)
+{
+    switch (variant) {
+    case 0: return (void*)atk::batch_stage<atk::ADVDIFF, 1, false>;
+    case 1: return (void*)atk::batch_stage<atk::ADVDIFF, 2, false>;
+    case 2: return (void*)atk::batch_stage<atk::ADVDIFF, 3, false>;
+    case 3: return (void*)atk::batch_stage<atk::RNS, 1, false>;
+    case 4: return (void*)atk::batch_stage<atk::RNS, 2, false>;
+    case 5: return (void*)atk::batch_stage<atk::RNS, 3, false>;
+    case 6: return (void*)atk::batch_stage<atk::EULER, 3, true>;
+    default: return (void*)atk::batch_stage<atk::ADV_WENO, 3, true>;
+    }
+}
+
+cudaError_t atk_launch_batch_stage(int variant, const atk::StageArgs* tab, const int64_t* lvl, const int64_t* left,
+                                   const int* win_slot, const int* win_idx, int nwin, int stage, int block,
+                                   size_t smem, cudaStream_t st)
+{
+    void* fn = batch_stage_fn(variant);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* params[] = {(void*)&tab, (void*)&lvl, (void*)&left, (void*)&win_slot, (void*)&win_idx, (void*)&stage};
+    return cudaLaunchKernel(fn, dim3(nwin), dim3(block), params, smem, st);
+}
+
+cudaError_t atk_launch_batch_advance(int64_t* lvl, int64_t* left, const int* slots, int n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    atk::batch_advance<<<(n + 255) / 256, 256, 0, st>>>(lvl, left, slots, n);
+    return cudaGetLastError();
 }
 
 int atk_batch_max_ctas_per_sm(int variant, int block, size_t smem)

@@ -287,6 +287,47 @@ def batched_rns(count=4096, seed=0, nsteps=100, dt=0.002, n_min=256, n_max=8192)
     return out
 
 
+# --------------------------------------------------------------------------
+# Served requests: a Poisson stream mixing the advection-diffusion, reacting
+# N-S and detonation problem types, N log-uniform in [512, 262,144], step
+# counts uniform in [100, 5,000], a seed per request.
+# --------------------------------------------------------------------------
+def serving_request(kind: str, n: int, seed: int, instance: int):
+    if kind == "advdiff":
+        B = 64
+        n = max(2 * B, (n // B) * B)
+        pb, init = advdiff(n=n, pe_size=B, mode="at", k_max=3, seed=seed, cfl=0.075)
+    elif kind == "rns":
+        B = 64
+        n = max(4 * B, (n // B) * B)
+        pb, init = rns(case="flame" if seed % 2 == 0 else "ignition", n=n, pe_size=B, mode="at", k_max=4,
+                       seed=seed, dt=0.003)
+    else:
+        B = 512
+        n = max(2 * B, (n // B) * B)
+        pb, init = detonation(n=n, pe_size=B, mode="at", k_max=4, seed=seed)
+    return dict(pb, instance=instance), init
+
+
+def serving_stream(rate=2000.0, duration=10.0, seed=0, n_min=512, n_max=262144, steps_min=100, steps_max=5000,
+                   max_requests=None):
+    """Arrival times (seconds from 0) and request descriptions; the initial
+    states are made when a request is admitted (``serving_request``)."""
+    rng = np.random.default_rng(seed)
+    out, t, i = [], 0.0, 0
+    kinds = ("advdiff", "rns", "detonation")
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t > duration or (max_requests is not None and i >= max_requests):
+            break
+        kind = kinds[int(rng.integers(3))]
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        steps = int(rng.integers(steps_min, steps_max + 1))
+        out.append({"id": i, "arrival": t, "kind": kind, "n": n, "steps": steps, "seed": int(seed * 1000003 + i)})
+        i += 1
+    return out
+
+
 CONFIGS = {
     "advdiff-n2048": lambda **kw: advdiff(**kw),
     "rns-flame-n16384": lambda **kw: rns(case="flame", **kw),

@@ -122,9 +122,10 @@ def test_batch_table_and_validation(L):
     assert batch.table_bytes(0) == 0
     t1, t2 = batch.table_bytes(1), batch.table_bytes(4096)
     assert t1 > 0 and t2 > t1 and t2 % 256 == 0
+    assert batch.table_bytes(16, 1 << 20) > batch.table_bytes(16, 16) + 8 * ((1 << 20) - 16) - 512
     h = ctypes.c_void_p()
     batch._lib()
     # a misaligned or too small table is refused before any CUDA call
-    assert L.at_batch_create(ctypes.byref(h), 0, None, 16, ctypes.c_void_p(256 + 8), 1 << 20) == api.AT_EINVAL
-    assert L.at_batch_create(ctypes.byref(h), 0, None, 16, ctypes.c_void_p(256), 16) == api.AT_ENOMEM
-    assert L.at_batch_create(ctypes.byref(h), 0, None, 0, ctypes.c_void_p(256), 1 << 20) == api.AT_EINVAL
+    assert L.at_batch_create(ctypes.byref(h), 0, None, 16, 64, ctypes.c_void_p(256 + 8), 1 << 20) == api.AT_EINVAL
+    assert L.at_batch_create(ctypes.byref(h), 0, None, 16, 64, ctypes.c_void_p(256), 16) == api.AT_ENOMEM
+    assert L.at_batch_create(ctypes.byref(h), 0, None, 0, 64, ctypes.c_void_p(256), 1 << 20) == api.AT_EINVAL

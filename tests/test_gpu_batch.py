@@ -44,7 +44,8 @@ def alone(pb, init, nsteps):
     return s.read_state(), s.read_delays()
 
 
-@pytest.mark.parametrize("config", [(256, 3, True), (128, 6, False), (256, 1, True)])
+@pytest.mark.parametrize("config", [(0, 256, 3, True), (0, 128, 6, False), (0, 256, 1, True), (1, 256, 1, True),
+                                    (1, 128, 1, False)])
 def test_batch_equals_alone_bitwise(config):
     from paper_2204_01133_gb300.batch import Batch
     inst = mixed_instances()
@@ -62,7 +63,8 @@ def test_batch_equals_alone_bitwise(config):
         assert np.array_equal(got, ref[i]), (i, pb["pde"], np.abs(got - ref[i]).max())
 
 
-def test_batch_slot_reuse_and_late_admission():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_slot_reuse_and_late_admission(mode):
     """Continuous batching: a finished instance's slot is released and a new
     instance bound while the others are mid-run; every result still equals
     the instance solved alone."""
@@ -70,6 +72,7 @@ def test_batch_slot_reuse_and_late_admission():
     inst = mixed_instances()[:6]
     extra = W.batched_rns(count=12, seed=8, nsteps=0, n_max=1024)[10:]
     b = Batch(capacity=6)
+    b.set_config(mode, 256, 3, True)
     for i, (pb, init, n) in enumerate(inst):
         b.bind(i, pb, init, n)
     b.run(25)                        # instance 0 (23 steps) is done
@@ -93,12 +96,26 @@ def test_autotuner_keeps_results_and_picks_a_candidate(tmp_path, monkeypatch):
     b = BT.Batch(capacity=24)
     for i, (pb, init, _) in enumerate(inst):
         b.bind(i, pb, init, 40)
-    res = BT.autotune(b, chunk=2, candidates=[(256, 2), (128, 4), (256, 4)])
-    assert (res["block"], res["ctas_per_sm"]) in [(256, 2), (128, 4), (256, 4)]
+    cands = [(BT.INSTANCE, 256, 2), (BT.INSTANCE, 128, 4), (BT.FLAT, 256, 1)]
+    res = BT.autotune(b, chunk=2, candidates=cands)
+    assert (res["mode"], res["block"], res["ctas_per_sm"]) in cands
     while any(b.query(i).left > 0 for i in range(24)):
         b.run(7)
     for i in (0, 5, 23):
         pb, init, _ = inst[i]
         assert np.array_equal(b.state(i).cpu().numpy(), alone(pb, init, 40)[0])
-    again = BT.autotune(b, chunk=2, candidates=[(256, 2), (128, 4), (256, 4)])
-    assert again["cached"] and again["block"] == res["block"]
+    again = BT.autotune(b, chunk=2, candidates=cands)
+    assert again["cached"] and again["block"] == res["block"] and again["mode"] == res["mode"]
+
+
+def test_flat_mode_window_map_limit():
+    from paper_2204_01133_gb300 import api
+    from paper_2204_01133_gb300.batch import Batch
+    b = Batch(capacity=4, max_windows=40)
+    pb, init = W.rns(case="flame", n=2048, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003)  # 32 windows
+    b.bind(0, pb, init, 5)
+    with pytest.raises(api.AtError) as ei:
+        b.bind(1, pb, init, 5)
+    assert ei.value.code == api.AT_ENOMEM
+    b.release(0)
+    b.bind(1, pb, init, 5)  # fits again once the first is released

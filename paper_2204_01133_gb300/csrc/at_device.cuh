@@ -142,6 +142,15 @@ struct Phys<RNS> {
         g[6] = a.k3 * Y;
         g[7] = T;
     }
+    // the temperature exactly as derive() forms it (same operations, same rounding)
+    __device__ static double temperature(const StageArgs& a, const double* Q)
+    {
+        const double gm1 = a.prm[0] - 1.0, qc = a.prm[6];
+        const double rinv = 1.0 / Q[0];
+        const double u = Q[1] * rinv;
+        const double p = gm1 * (Q[2] - fma(0.5 * Q[1], u, qc * Q[3]));
+        return p * rinv;
+    }
 };
 
 // Reactive Euler, WENO form: g = [C/2 (4), Q (4)], C = (rho u, rho u^2 + p,

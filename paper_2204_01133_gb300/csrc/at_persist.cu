@@ -54,8 +54,76 @@ __device__ bool wait_ge(const StageArgs& a, int64_t* ctr, int64_t target)
     return false;
 }
 
+// stencil, source and RK update of own point (v, jl) for stage s, in shared
+// memory: the same arithmetic, in the same order, as the per-stage kernels
+// (the Arrhenius factor exp(-Ea/T) arrives precomputed in E)
 template <int PDE, int H>
-__global__ void __launch_bounds__(256) persist_central(const StageArgs a, int64_t level0, int64_t nsteps)
+__device__ __forceinline__ double point_update(const StageArgs& a, int s, int v, int jl, const double* G,
+                                               const double* E, double* X, double* U, double* ACC, int W2, int B,
+                                               bool last)
+{
+    const int it = v * B + jl;
+    const int c = jl + H;
+    double K = 0.0;
+    const double x = X[it];
+    if constexpr (PDE == ADVDIFF) {
+#pragma unroll
+        for (int o = -H; o <= H; ++o) K = fma(a.cm[o + H], G[c + o], K);
+    } else {
+        const double* F = G + v * W2;
+#pragma unroll
+        for (int o = -H; o <= H; ++o)
+            if (o != 0) K = fma(a.c1[o + H], F[c + o], K);
+        if (v > 0) {
+            const double* D = G + (3 + v) * W2;
+#pragma unroll
+            for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[c + o], K);
+        }
+        if (v == 3) K = fma(-a.prm[4] * x, E[jl], K);
+    }
+    const double dt = a.dt;
+    const double un = U[it];
+    double y;
+    if (a.rk == RK4) {
+        if (s == 0) {
+            ACC[it] = K;
+            y = fma(0.5 * dt, K, un);
+        } else if (s < 3) {
+            ACC[it] = fma(2.0, K, ACC[it]);
+            y = fma(s == 1 ? 0.5 * dt : dt, K, un);
+        } else {
+            y = fma(dt * (1.0 / 6.0), ACC[it] + K, un);
+        }
+    } else if (a.rk == RK3TVD) {
+        const double xs = fma(dt, K, x);
+        if (s == 0) y = xs;
+        else if (s == 1) y = fma(0.75, un, 0.25 * xs);
+        else y = fma(1.0 / 3.0, un, (2.0 / 3.0) * xs);
+    } else {
+        if (s == 0) {
+            ACC[it] = K;
+            y = fma(dt, K, un);
+        } else {
+            y = fma(0.5 * dt, ACC[it] + K, un);
+        }
+    }
+    X[it] = y;  // next stage argument (u^{n+1} after the last stage)
+    if (last) U[it] = y;
+    return y;
+}
+
+// GB300's FP64 unit spends the same time on a warp instruction whatever the
+// number of active lanes, so the work is laid out in whole, uniform warps
+// with fixed roles; two barriers per stage:
+//   (A) warps of the "derive" role: own-point derived quantities;
+//       warps of the "source" role: exp(-Ea/T) of own points;
+//       the halo warp: delays, the bounded neighbour waits, then the buffer
+//       levels from the ring, weighted and summed per buffer point;
+//   (C) the worker warps: stencil, source and RK update of every (point,
+//       variable), one variable per warp; the edge points go straight into
+//       the ring.  Then the progress counter is published.
+template <int PDE, int H>
+__global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_t level0, int64_t nsteps)
 {
     using P = Phys<PDE>;
     constexpr int NV = P::NV, ND = P::ND;
@@ -63,14 +131,37 @@ __global__ void __launch_bounds__(256) persist_central(const StageArgs a, int64_
     const int64_t pe = blockIdx.x;
     const int64_t nbr[2] = {pe == 0 ? a.P - 1 : pe - 1, pe == a.P - 1 ? 0 : pe + 1};
     extern __shared__ double sm[];
-    double* U = sm;                // u^n            [NV][B]
-    double* ACC = U + NV * B;      // RK accumulator [NV][B]
-    double* X = ACC + NV * B;      // stage argument [NV][B]
-    double* G = X + NV * B;        // derived        [ND][W2]
-    double* HS = G + ND * W2;      // halo levels    [2H(q+1)][ND]
+    double* U = sm;                // u^n                 [NV][B]
+    double* ACC = U + NV * B;      // RK accumulator      [NV][B]
+    double* X = ACC + NV * B;      // stage argument      [NV][B]
+    double* G = X + NV * B;        // derived             [ND][W2]
+    double* HS = G + ND * W2;      // halo levels         [2H(q+1)][ND]
+    double* E = HS + 2 * H * (AT_QMAX + 1) * ND;  // exp(-Ea/T) of own points [B]
     __shared__ int s_abort;
     __shared__ int s_k[2];
     const int nw = (a.mode == AT) ? a.q + 1 : 1;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int hwarp = (int)(blockDim.x >> 5) - 1;  // the halo warp
+    const int nwork = hwarp * 32;                    // threads of the worker warps
+    // warps per role in phase A: enough for one point per lane, at most half the workers
+    int bw = (B + 31) / 32;
+    if (PDE == RNS && bw > hwarp / 2) bw = hwarp / 2;
+    if (bw > hwarp) bw = hwarp;
+    if (bw < 1) bw = 1;
+    // Roles of the worker warps in phase A.  Warp w runs on SM sub-partition
+    // w % 4 and the halo warp on hwarp % 4.  With 2 + 2 role warps and the halo
+    // warp on sub-partition 0 (a 64-point reacting PE), the two source warps
+    // (the heaviest) take sub-partitions 1 and 2 and both derive warps take 3;
+    // otherwise the derive warps come first and the source warps next.
+    int derive_rank = -1, source_rank = -1;
+    if (PDE == RNS && bw == 2 && hwarp == 8) {
+        if (warp == 1 || warp == 2) source_rank = warp - 1;
+        if (warp == 3 || warp == 7) derive_rank = warp == 3 ? 0 : 1;
+    } else if (warp < hwarp) {
+        if (warp < bw) derive_rank = warp;
+        else if (PDE == RNS && warp < 2 * bw) source_rank = warp - bw;
+    }
 
     for (int i = threadIdx.x; i < NV * B; i += blockDim.x) {
         const int v = i / B, j = i - v * B;
@@ -84,130 +175,99 @@ __global__ void __launch_bounds__(256) persist_central(const StageArgs a, int64_
 
     for (int64_t n = level0; n < level0 + nsteps; ++n) {
         for (int s = 0; s < S; ++s) {
-            // delays of both PE boundaries; wait for the neighbours' stage-s argument at level n-k
-            if (threadIdx.x < 2) {
-                const int side = threadIdx.x;
-                const int k = keff_at(a, n, s, pe, side);
-                s_k[side] = k;
-                a.dlog[((int64_t)s * a.P + pe) * 2 + side] = (uint8_t)k;
-                if (!wait_ge(a, a.done + nbr[side], (n - k) * S + s)) atomicExch(&s_abort, 1);
-                __threadfence();
-            }
-            __syncthreads();
-            if (s_abort) goto out;
-
-            // fill: own points from shared memory, buffer points from the ring (L2)
-            {
-                const int items = B + 2 * H * nw;
-                for (int it = threadIdx.x; it < items; it += blockDim.x) {
-                    double g[ND];
-                    double Q[NV];
-                    if (it < B) {
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) Q[v] = X[v * B + it];
-                        P::derive(a, Q, g);
-#pragma unroll
-                        for (int d = 0; d < ND; ++d) G[d * W2 + H + it] = g[d];
-                    } else {
-                        const int t = it - B;
+            const bool last = (s == S - 1);
+            const int64_t I = n * S + s + 1;  // the stage argument this stage produces
+            const int64_t Ln = I / S;
+            const int sn = (int)(I - Ln * S);
+            // (A)
+            if (warp == hwarp) {
+                if (lane < 2) {
+                    const int side = lane;
+                    const int k = keff_at(a, n, s, pe, side);
+                    s_k[side] = k;
+                    a.dlog[((int64_t)s * a.P + pe) * 2 + side] = (uint8_t)k;
+                    // the neighbour's stage-s argument at level n-k, and the ring slot of (Ln, sn) free
+                    if (!wait_ge(a, a.done + nbr[side], (n - k) * S + s) ||
+                        !wait_ge(a, a.done + nbr[side], (Ln - a.slack - 1) * S + sn + 1))
+                        atomicExch(&s_abort, 1);
+                    __threadfence();
+                }
+                __syncwarp();
+                if (!*(volatile int*)&s_abort) {
+                    const int t = lane;
+                    if (t < 2 * H * nw) {
                         const int hp = t / nw, l = t - hp * nw;
                         const int side = hp < H ? 0 : 1;
                         const int h = side == 0 ? hp : hp - H;
                         const int k = s_k[side];
                         const double wl = (a.mode == AT) ? a.w[k][l] : 1.0;
+                        double g[ND];
+                        double Q[NV];
                         if (wl != 0.0) {
                             const int64_t base = ring_index(a, n - k - l, s, nbr[side], 1 - side, h, 0);
 #pragma unroll
                             for (int v = 0; v < NV; ++v) Q[v] = __ldcg(a.ring + base + v);
                             P::derive(a, Q, g);
 #pragma unroll
-                            for (int d = 0; d < ND; ++d) HS[t * ND + d] = wl * g[d];
+                            for (int d = 0; d < ND; ++d) HS[t * ND + d] = g[d];
                         } else {
 #pragma unroll
                             for (int d = 0; d < ND; ++d) HS[t * ND + d] = 0.0;
                         }
                     }
-                }
-            }
-            __syncthreads();
-            for (int c = threadIdx.x; c < 2 * H * ND; c += blockDim.x) {
-                const int hp = c / ND, d = c - hp * ND;
-                double acc = HS[(hp * nw) * ND + d];
-                for (int l = 1; l < nw; ++l) acc += HS[(hp * nw + l) * ND + d];
-                G[d * W2 + (hp < H ? hp : B + hp)] = acc;
-            }
-            __syncthreads();
-
-            // stencil, source and RK update of this stage, in shared memory
-            const bool last = (s == S - 1);
-            for (int it = threadIdx.x; it < NV * B; it += blockDim.x) {
-                const int v = it / B;
-                const int jl = it - v * B;
-                const int c = jl + H;
-                double K = 0.0;
-                const double x = X[it];
-                if constexpr (PDE == ADVDIFF) {
-#pragma unroll
-                    for (int o = -H; o <= H; ++o) K = fma(a.cm[o + H], G[c + o], K);
-                } else {
-                    const double* F = G + v * W2;
-#pragma unroll
-                    for (int o = -H; o <= H; ++o)
-                        if (o != 0) K = fma(a.c1[o + H], F[c + o], K);
-                    if (v > 0) {
-                        const double* D = G + (3 + v) * W2;
-#pragma unroll
-                        for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[c + o], K);
-                    }
-                    if (v == 3) K = fma(-a.prm[4] * x, exp(-a.prm[5] / G[7 * W2 + c]), K);
-                }
-                const double dt = a.dt;
-                const double un = U[it];
-                double y;
-                if (a.rk == RK4) {
-                    if (s == 0) {
-                        ACC[it] = K;
-                        y = fma(0.5 * dt, K, un);
-                    } else if (s < 3) {
-                        ACC[it] = fma(2.0, K, ACC[it]);
-                        y = fma(s == 1 ? 0.5 * dt : dt, K, un);
-                    } else {
-                        y = fma(dt * (1.0 / 6.0), ACC[it] + K, un);
-                    }
-                } else if (a.rk == RK3TVD) {
-                    const double xs = fma(dt, K, x);
-                    if (s == 0) y = xs;
-                    else if (s == 1) y = fma(0.75, un, 0.25 * xs);
-                    else y = fma(1.0 / 3.0, un, (2.0 / 3.0) * xs);
-                } else {
-                    if (s == 0) {
-                        ACC[it] = K;
-                        y = fma(dt, K, un);
-                    } else {
-                        y = fma(0.5 * dt, ACC[it] + K, un);
+                    __syncwarp();
+                    // weighted sum over levels, in level order: lanes (buffer point, quantity)
+                    for (int c = lane; c < 2 * H * ND; c += 32) {
+                        const int hp = c / ND, d = c - hp * ND;
+                        const int k = s_k[hp < H ? 0 : 1];
+                        double acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * HS[(hp * nw) * ND + d];
+                        for (int l = 1; l < nw; ++l) acc = fma(a.w[k][l], HS[(hp * nw + l) * ND + d], acc);
+                        G[d * W2 + (hp < H ? hp : B + hp)] = acc;
                     }
                 }
-                X[it] = y;  // next stage argument (u^{n+1} after the last stage)
-                if (last) U[it] = y;
-                if (!isfinite(y)) bad = 1;
-            }
-            __syncthreads();
-
-            // the new stage argument (n, s+1) or (n+1, 0): wait until its ring slot is free
-            const int64_t I = n * S + s + 1;
-            const int64_t Ln = I / S;
-            const int sn = (int)(I - Ln * S);
-            if (threadIdx.x < 2) {
-                const int64_t need = (Ln - a.slack - 1) * S + sn + 1;
-                if (!wait_ge(a, a.done + nbr[threadIdx.x], need)) atomicExch(&s_abort, 1);
+            } else if (derive_rank >= 0) {
+                for (int it = derive_rank * 32 + lane; it < B; it += bw * 32) {
+                    double g[ND];
+                    double Q[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) Q[v] = X[v * B + it];
+                    P::derive(a, Q, g);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) G[d * W2 + H + it] = g[d];
+                }
+            } else if constexpr (PDE == RNS) {
+                if (source_rank >= 0) {
+                    for (int it = source_rank * 32 + lane; it < B; it += bw * 32) {
+                        double Q[NV];
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) Q[v] = X[v * B + it];
+                        E[it] = exp(-a.prm[5] / P::temperature(a, Q));
+                    }
+                }
             }
             __syncthreads();
             if (s_abort) goto out;
-            for (int t = threadIdx.x; t < 2 * H * NV; t += blockDim.x) {
-                const int v = t % NV, h = (t / NV) % H, side = t / (NV * H);
-                const int jpe = side == 0 ? h : B - H + h;
-                __stcg(a.ring + ring_index(a, Ln, sn, pe, side, h, v), X[v * B + jpe]);
-                __threadfence();
+
+            // (C)
+            if (warp < hwarp) {
+                for (int it = threadIdx.x; it < NV * B; it += nwork) {
+                    const int v = it / B;
+                    const int jl = it - v * B;
+                    const double y = point_update<PDE, H>(a, s, v, jl, G, E, X, U, ACC, W2, B, last);
+                    if (!isfinite(y)) bad = 1;
+                    int side = -1, h = 0;
+                    if (jl < H) {
+                        side = 0;
+                        h = jl;
+                    } else if (jl >= B - H) {
+                        side = 1;
+                        h = jl - (B - H);
+                    }
+                    if (side >= 0) {
+                        __stcg(a.ring + ring_index(a, Ln, sn, pe, side, h, v), y);
+                        __threadfence();
+                    }
+                }
             }
             __syncthreads();
             if (threadIdx.x == 0 && pe != a.withhold_pe) store_release(a.done + pe, I);
@@ -260,16 +320,21 @@ void* persist_kernel(int pde, int order)
 size_t atk_persist_smem_bytes(int pde, int B, int H)
 {
     const int nv = pde == atk::RNS ? 4 : 1, nd = pde == atk::RNS ? 8 : 1;
-    return sizeof(double) * ((size_t)3 * nv * B + (size_t)nd * (B + 2 * H) + (size_t)2 * H * (AT_QMAX + 1) * nd);
+    return sizeof(double) *
+           ((size_t)3 * nv * B + (size_t)nd * (B + 2 * H) + (size_t)2 * H * (AT_QMAX + 1) * nd + (size_t)B);
 }
 
+// worker warps for the PE's points (at least two roles' worth for phase A)
+// plus one halo warp
 int atk_persist_block(int pde, int B)
 {
     const int nv = pde == atk::RNS ? 4 : 1;
-    int want = nv * B;
+    const int bw = (B + 31) / 32;
+    int want = ((nv * B + 31) / 32) * 32;
     if (want > 256) want = 256;
-    want = ((want + 31) / 32) * 32;
-    return want < 64 ? 64 : want;
+    if (want < 64 * bw) want = 64 * bw;
+    if (want > 256) want = 256;
+    return want + 32;
 }
 
 // how many PEs one cooperative launch can hold (0: not available)

@@ -45,10 +45,10 @@ __device__ __forceinline__ Cx launch_cx(const StageArgs& a) { return Cx{a.level,
 //
 // Work items: one per point of the window inside the PE (read the field,
 // derive), plus one per (buffer point, time level) pair of the window's PE
-// boundaries (read the ring at level n-k-l, derive, scale by the
-// extrapolation weight).  All items run concurrently, one per thread; the
-// level contributions are then summed per buffer point.  HS stages the
-// weighted level contributions: [2 H (q+1)][ND].
+// boundaries (read the ring at level n-k-l, derive).  All items run
+// concurrently, one per thread; the level contributions are then combined
+// per buffer point with the extrapolation weights.  HS stages the level
+// contributions: [2 H (q+1)][ND].
 // ---------------------------------------------------------------------------
 template <int PDE, bool WENO>
 __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, double* __restrict__ G,
@@ -93,7 +93,7 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
                     if (l == 0) SP[side == 0 ? h : W2 - R0 + h] = P::speed(a, Q);  // level n-k, not extrapolated
                 }
 #pragma unroll
-                for (int d = 0; d < ND; ++d) HS[t * ND + d] = wl * g[d];
+                for (int d = 0; d < ND; ++d) HS[t * ND + d] = g[d];
             } else {
 #pragma unroll
                 for (int d = 0; d < ND; ++d) HS[t * ND + d] = 0.0;
@@ -102,11 +102,13 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
     }
     if (L0 + R0 == 0) return;
     __syncthreads();
-    // sum the level contributions of every buffer point (in level order)
+    // weighted sum of the level contributions of every buffer point, in level order
     for (int c = threadIdx.x; c < (L0 + R0) * ND; c += blockDim.x) {
         const int hp = c / ND, d = c - hp * ND;
-        double acc = HS[(hp * nw) * ND + d];
-        for (int l = 1; l < nw; ++l) acc += HS[(hp * nw + l) * ND + d];
+        const int side = hp < L0 ? 0 : 1;
+        const int k = keff_at(a, cx.level, cx.stage, pe, side);
+        double acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * HS[(hp * nw) * ND + d];
+        for (int l = 1; l < nw; ++l) acc = fma(a.w[k][l], HS[(hp * nw + l) * ND + d], acc);
         const int i = hp < L0 ? hp : W2 - R0 + (hp - L0);
         G[d * W2 + i] = acc;
     }

@@ -92,6 +92,9 @@ def lib():
         L.orc_weno5_js.restype = ctypes.c_double
         L.orc_edge_flux.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, P(ctypes.c_int32),
                                     ctypes.c_int64, ctypes.c_int64, P(ctypes.c_double)]
+        L.orc_set_level.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        L.orc_set_state.argtypes = [ctypes.c_void_p, P(ctypes.c_double)]
+        L.orc_force_delays.argtypes = [ctypes.c_void_p, P(ctypes.c_int32)]
         _lib = L
     return _lib
 
@@ -186,6 +189,21 @@ class Oracle:
         lib().orc_edge_flux(self._h, int(level), int(stage), kf.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                             int(pe), int(i), _dptr(F))
         return F
+
+    def set_level(self, level: int) -> None:
+        lib().orc_set_level(self._h, int(level))
+
+    def set_state(self, u: np.ndarray) -> None:
+        f = np.ascontiguousarray(u, dtype=np.float64).reshape(self.nvar, self.n)
+        lib().orc_set_state(self._h, _dptr(f))
+
+    def force_delays(self, k) -> None:
+        if k is None:
+            lib().orc_force_delays(self._h, None)
+            return
+        kf = np.ascontiguousarray(k, dtype=np.int32).reshape(self.P, 2)
+        self._kfix = kf
+        lib().orc_force_delays(self._h, kf.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
 
     def draw(self, level: int, stage: int, pe: int, side: int) -> int:
         return int(lib().orc_draw(self._h, int(level), int(stage), int(pe), int(side)))

@@ -59,6 +59,7 @@ struct orc_ctx {
     int64_t level;
     int32_t* keff; /* delays in use  [S][P][2]        */
     uint8_t* dlog; /* last step's    [S][P][2]        */
+    int32_t* kfix; /* forced raw delays [P][2], or NULL to draw them */
 };
 
 /* ------------------------------------------------------------------ */
@@ -492,7 +493,7 @@ static int step(orc_ctx* c)
             for (int r = 0; r < s; ++r) acc += c->a[s][r] * c->K[(size_t)r * nf + i];
             U[i] = c->u[i] + c->pb.dt * acc;
         }
-        orc_rhs(c, n, s, NULL, c->K + (size_t)s * nf);
+        orc_rhs(c, n, s, c->kfix, c->K + (size_t)s * nf);
     }
     int bad = 0;
     for (size_t i = 0; i < nf; ++i) {
@@ -567,6 +568,7 @@ orc_ctx* orc_create(const orc_problem* pb, const double* init)
 void orc_destroy(orc_ctx* c)
 {
     if (!c) return;
+    free(c->kfix);
     free(c->u);
     free(c->hist);
     free(c->K);
@@ -603,4 +605,24 @@ void orc_edge_flux(orc_ctx* c, int64_t level, int stage, const int32_t* kforce, 
 {
     set_keff(c, level, stage, kforce);
     edge_flux(c, level, stage, pe, i, F);
+}
+
+/* pieces for the pins: place the run at a level with a given u^n, and use
+ * fixed delays (clamped like drawn ones) instead of drawing them */
+void orc_set_level(orc_ctx* c, int64_t level) { c->level = level; }
+
+void orc_set_state(orc_ctx* c, const double* u)
+{
+    memcpy(c->u, u, (size_t)c->nvar * c->N * sizeof(double));
+}
+
+void orc_force_delays(orc_ctx* c, const int32_t* k)
+{
+    if (!k) {
+        free(c->kfix);
+        c->kfix = NULL;
+        return;
+    }
+    if (!c->kfix) c->kfix = (int32_t*)malloc((size_t)c->P * 2 * sizeof(int32_t));
+    memcpy(c->kfix, k, (size_t)c->P * 2 * sizeof(int32_t));
 }

@@ -73,6 +73,10 @@ void orc_thresholds(int k_max, int dist, const double* prob, uint64_t* thr);
 int orc_draw(const orc_ctx* c, int64_t level, int stage, int64_t pe, int side);
 void orc_lagrange_weights(int q, int k, double* w);
 double orc_weno5_js(const double v[5], double eps);
+void orc_set_level(orc_ctx* c, int64_t level);
+void orc_set_state(orc_ctx* c, const double* u /* [nvar][n] */);
+/* fixed raw delays [P][2] for every following step (NULL: draw again) */
+void orc_force_delays(orc_ctx* c, const int32_t* k);
 /* WENO flux F[nvar] at the edge between points i and i+1 as PE `pe` sees it */
 void orc_edge_flux(orc_ctx* c, int64_t level, int stage, const int32_t* kforce, int64_t pe, int64_t i,
                    double* F);

@@ -265,6 +265,45 @@ def test_at_local_truncation_order(order, deriv):
 
 
 # --------------------------------------------------------------------------
+# Eq. rkat1: one RK2 step with AT4 at a PE boundary; the delay adds a local
+# error term proportional to k (k^2 + 3k + 2) dt^3 / dx^2
+# --------------------------------------------------------------------------
+def test_rk2_at4_excess_error_scales_like_eq_rkat1():
+    alpha = 1.0
+    n, B = 64, 16
+    dx = 2 * math.pi / n
+    dt = 0.1 * dx * dx / alpha
+    pb, u0 = W.advdiff(n=n, pe_size=B, order=4, c=0.0, a=alpha, dt=dt, rk="rk2", k_max=4)
+    x = np.arange(n) * dx
+
+    def exact(t):
+        return np.exp(-alpha * t) * np.sin(x + 0.4)
+
+    def d2_sync(f):  # standard 4th-order second derivative (Eq. ks), periodic
+        return (-np.roll(f, 2) + 16 * np.roll(f, 1) - 30 * f + 16 * np.roll(f, -1) - np.roll(f, -2)) / (12 * dx * dx)
+
+    L0 = 10
+    errs = {}
+    for k in range(0, 5):
+        o = oracle.Oracle(pb, u0)
+        for lvl in range(0, L0 + 1):
+            t = lvl * dt
+            o.set_history(lvl, 0, exact(t)[None, :])
+            # stage 2 at old levels from synchronous stages of exact data (Sec. 2.3)
+            o.set_history(lvl, 1, (exact(t) + dt * alpha * d2_sync(exact(t)))[None, :])
+        o.set_level(L0)
+        o.set_state(exact(L0 * dt)[None, :])
+        o.force_delays(np.full((n // B, 2), k))
+        assert o.run(1) == 0
+        j = B  # first point of PE 1
+        errs[k] = o.state()[0][j] - exact((L0 + 1) * dt)[j]
+    excess = {k: errs[k] - errs[0] for k in range(1, 5)}
+    for k in range(2, 5):
+        want = k * (k * k + 3 * k + 2) / 6.0   # relative to k = 1
+        assert abs(excess[k] / excess[1] - want) < 0.05 * want, (k, excess)
+
+
+# --------------------------------------------------------------------------
 # Zero delay == synchronous (Sec. 2.2 after Eq. at1; Eq. rkat2 at k = 0)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("maker", ["advdiff", "rns", "euler", "adv_weno"])

@@ -61,9 +61,9 @@ FLOPS_PER_POINT_STAGE = {
 # DRAM bytes per launch of the stage kernel from the same ncu captures
 # (dram__bytes_read.sum + dram__bytes_write.sum), or None where not captured
 TRAFFIC_PER_LAUNCH = {
-    "rns-flame-n16384": None,  # persistent path: not captured yet
-    "rns-flame-n16777216": 1.663e9 + 1.086e9,
-    "detonation-n16777216": 5.458e8 + 4.972e8,
+    "rns-flame-n16384": 1.208e6,  # persistent launch: the state is read once, writes stay in L2
+    "rns-flame-n16777216": 1.662e9 + 1.086e9,
+    "detonation-n16777216": 5.46e8 + 4.935e8,
 }
 
 
@@ -280,7 +280,7 @@ def run_batched(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     cfg = WORKLOADS[args.workload]
-    count = cfg["count"]
+    count = args.batch_count or cfg["count"]
     tune_steps = len(BT.CANDIDATES)
     total = args.warmup + tune_steps + args.steps
     inst = W.batched_rns(count=count, seed=cfg["seed"], nsteps=total)
@@ -525,6 +525,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--plain-sample", type=int, default=256, help="instances timed on the plain path (batched)")
+    ap.add_argument("--batch-count", type=int, default=0, help="instances of the batched workload (0: 4,096)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests in the served burst (serving)")
     ap.add_argument("--serve-budget-gb", type=int, default=16, help="device-memory budget of the server (GB)")
     ap.add_argument("--serve-chunk", type=int, default=50, help="steps per serving tick")

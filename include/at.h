@@ -59,8 +59,10 @@ typedef enum {
  *               Lax-Friedrichs splitting (Sec. 3, Eqs. Csplit, wender);
  *               prm = {gamma, A, Ea, Q, eps}
  *   AT_ADV_WENO u_t + c u_x = 0 with WENO5 (the order test of Sec. 3);
- *               prm = {c, eps}                                              */
-enum { AT_ADVDIFF = 0, AT_RNS = 1, AT_EULER = 2, AT_ADV_WENO = 3 };
+ *               prm = {c, eps}
+ *   AT_BURGERS  u_t + (u^2/2)_x = 0 with WENO5 (the nonlinear order test of
+ *               Sec. 3); prm = {0, eps}                                     */
+enum { AT_ADVDIFF = 0, AT_RNS = 1, AT_EULER = 2, AT_ADV_WENO = 3, AT_BURGERS = 4 };
 /* RK schemes (Sec. 2.3): Heun RK2 (Eq. rk2), Shu-Osher TVD RK3, classic RK4 */
 enum { AT_RK2 = 0, AT_RK3TVD = 1, AT_RK4 = 2 };
 /* Boundary treatment (Sec. 2.1, 2.2, 3): synchronous; standard scheme on
@@ -89,7 +91,7 @@ enum {
 };
 
 typedef struct {
-    int32_t pde;      /* AT_ADVDIFF | AT_RNS | AT_EULER | AT_ADV_WENO                 */
+    int32_t pde;      /* AT_ADVDIFF | AT_RNS | AT_EULER | AT_ADV_WENO | AT_BURGERS    */
     int32_t order;    /* 2 | 4 | 6 for central PDEs; ignored for WENO5                */
     int32_t rk;       /* AT_RK2 | AT_RK3TVD | AT_RK4                                  */
     int32_t pe_size;  /* points per PE, >= 2 x halo width (order/2, or 3 for WENO5)   */

@@ -30,6 +30,8 @@
  *    U^{n,(s)} = u^n + dt sum_{i<s} a_si K_i is kept for every level, and the
  *    buffer points of stage s read U^{n-k-l,(s)}: the message of Sec. 2.3
  *    carries all stages of a step, so stage s of an old level is available.
+ *  - Inviscid Burgers u_t + (u^2/2)_x = 0 with WENO5 / AT-WENO5 (the
+ *    nonlinear order test of Sec. 3).
  *  - Governing equations (Sec. 4, Eqs. ge, convEq) reduced to two species
  *    (fuel -> product, equal molecular weights and heat capacities) with
  *    constant transport and a one-step irreversible Arrhenius rate (Sec. 5.2
@@ -235,7 +237,7 @@ static void state_at(const orc_ctx* c, const double* f, int64_t m, double* Q)
     for (int v = 0; v < c->nvar; ++v) Q[v] = f[(size_t)v * c->N + m];
 }
 
-/* ADVDIFF: [u].  ADV_WENO: [c u, u].
+/* ADVDIFF: [u].  ADV_WENO: [c u, u].  BURGERS: [u^2 / 2, u].
  * RNS (Eq. convEq with two species, R = 1, p = rho T):
  *   [rho u, rho u^2 + p, u (rho E + p), rho u Y, u, u^2, T, Y]
  * EULER: [rho u, rho u^2 + p, u (rho E + p), rho u Y, rho, rho u, rho E, rho Y] */
@@ -248,6 +250,10 @@ static void derive(const orc_ctx* c, const double* Q, double* g)
         break;
     case ORC_ADV_WENO:
         g[0] = pr[0] * Q[0];
+        g[1] = Q[0];
+        break;
+    case ORC_BURGERS:
+        g[0] = 0.5 * Q[0] * Q[0];
         g[1] = Q[0];
         break;
     case ORC_RNS: {
@@ -286,6 +292,7 @@ static double wave_speed(const orc_ctx* c, const double* Q)
 {
     const double* pr = c->pb.prm;
     if (c->pb.pde == ORC_ADV_WENO) return fabs(pr[0]);
+    if (c->pb.pde == ORC_BURGERS) return fabs(Q[0]);
     double gam = pr[0], qc = pr[3];
     double rho = Q[0], u = Q[1] / rho;
     double p = (gam - 1.0) * (Q[2] - 0.5 * Q[1] * u - qc * Q[3]);
@@ -522,12 +529,12 @@ orc_ctx* orc_create(const orc_problem* pb, const double* init)
     if (!pb || !init) return NULL;
     if (pb->pe_size <= 0 || pb->n <= 0 || pb->n % pb->pe_size) return NULL;
     if (pb->k_max < 0 || pb->k_max > 15) return NULL;
-    if (pb->pde < 0 || pb->pde > 3) return NULL;
+    if (pb->pde < 0 || pb->pde > 4) return NULL;
     orc_ctx* c = (orc_ctx*)calloc(1, sizeof *c);
     if (!c) return NULL;
     c->pb = *pb;
     c->nvar = nvar_of(pb->pde);
-    int weno = (pb->pde == ORC_EULER || pb->pde == ORC_ADV_WENO);
+    int weno = (pb->pde == ORC_EULER || pb->pde == ORC_ADV_WENO || pb->pde == ORC_BURGERS);
     if (weno) {
         c->H = 3;
         c->q = 1;
@@ -539,7 +546,7 @@ orc_ctx* orc_create(const orc_problem* pb, const double* init)
         c->H = pb->order / 2;
         c->q = pb->order / 2;
     }
-    c->nder = (pb->pde == ORC_ADVDIFF) ? 1 : (pb->pde == ORC_ADV_WENO ? 2 : 8);
+    c->nder = (pb->pde == ORC_ADVDIFF) ? 1 : ((pb->pde == ORC_ADV_WENO || pb->pde == ORC_BURGERS) ? 2 : 8);
     if (pb->pe_size < 2 * c->H) {
         free(c);
         return NULL;

@@ -70,7 +70,7 @@ struct Layout {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int nvar_of(int pde) { return (pde == AT_RNS || pde == AT_EULER) ? 4 : 1; }
-bool is_weno(int pde) { return pde == AT_EULER || pde == AT_ADV_WENO; }
+bool is_weno(int pde) { return pde == AT_EULER || pde == AT_ADV_WENO || pde == AT_BURGERS; }
 int stages_of(int rk) { return rk == AT_RK2 ? 2 : (rk == AT_RK3TVD ? 3 : 4); }
 
 // window length: the largest divisor of the PE size in [2H, 256]; a PE size
@@ -88,7 +88,7 @@ int window_of(int B, int H)
 int check_problem(const at_problem* pb)
 {
     if (!pb) return fail(AT_EINVAL, "problem is NULL");
-    if (pb->pde < 0 || pb->pde > 3) return fail(AT_EINVAL, "unknown pde %d", pb->pde);
+    if (pb->pde < 0 || pb->pde > 4) return fail(AT_EINVAL, "unknown pde %d", pb->pde);
     if (pb->rk < 0 || pb->rk > 2) return fail(AT_EINVAL, "unknown rk %d", pb->rk);
     if (!is_weno(pb->pde) && pb->order != 2 && pb->order != 4 && pb->order != 6)
         return fail(AT_EINVAL, "central order must be 2, 4 or 6 (got %d)", pb->order);
@@ -608,7 +608,7 @@ int at_destroy(at_ctx* c)
 // batched solves
 // ---------------------------------------------------------------------------
 namespace {
-const int kVariants = 8;
+const int kVariants = 9;
 
 struct BatchTable {  // carving of the caller's table memory
     size_t off_args, off_lvl, off_left, off_order, off_slots, off_status, off_queue, off_wslot, off_widx, total;

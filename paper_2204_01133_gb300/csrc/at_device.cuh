@@ -13,7 +13,7 @@
 
 namespace atk {
 
-enum { ADVDIFF = 0, RNS = 1, EULER = 2, ADV_WENO = 3 };
+enum { ADVDIFF = 0, RNS = 1, EULER = 2, ADV_WENO = 3, BURGERS = 4 };
 enum { RK2 = 0, RK3TVD = 1, RK4 = 2 };
 enum { SYNC = 0, AS = 1, AT = 2 };
 
@@ -194,6 +194,18 @@ struct Phys<ADV_WENO> {
         g[1] = Q[0];
     }
     __device__ static double speed(const StageArgs& a, const double*) { return fabs(a.prm[0]); }
+};
+
+// Inviscid Burgers, WENO form: g = [u^2 / 4, u] (C/2 with C = u^2/2); speed |u|.
+template <>
+struct Phys<BURGERS> {
+    static constexpr int NV = 1, ND = 2;
+    __device__ static void derive(const StageArgs&, const double* Q, double* g)
+    {
+        g[0] = 0.5 * (0.5 * Q[0] * Q[0]);
+        g[1] = Q[0];
+    }
+    __device__ static double speed(const StageArgs&, const double* Q) { return fabs(Q[0]); }
 };
 
 } // namespace atk

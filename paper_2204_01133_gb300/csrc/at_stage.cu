@@ -222,24 +222,36 @@ __global__ void __launch_bounds__(256) stage_central(const StageArgs a)
 // ---------------------------------------------------------------------------
 // WENO5-JS reconstruction at the right edge of f[2] from f[0..4]
 // (candidates of Eq. atRecon at k = 0, ideal weights {1/10, 3/5, 3/10},
-// indicators of Eq. betaS, weights of Eq. omg with power 2).  The three
-// normalised weights share one division: alpha_i ~ gamma_i prod_{j!=i} d_j^2.
+// indicators of Eq. betaS, weights of Eq. omg with power 2), arranged for
+// few FP64 instructions without changing the mathematics:
+//  * the indicators are formed as 12 beta_i = 13 s_i^2 + 3 r_i^2 (with
+//    s_i the second difference and r_0, r_2 built from s_0, s_2) and eps as
+//    12 eps: the weights omega_i = alpha_i / sum alpha are unchanged by a
+//    common factor of the indicators and eps;
+//  * the three weights share one division: alpha_i ~ gamma_i prod_{j!=i}
+//    d_j^2, with gamma_i and the candidates' 1/6 folded into constants.
+// eps12 = 12 eps.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double weno5(double f0, double f1, double f2, double f3, double f4, double eps)
+__device__ __forceinline__ double weno5(double f0, double f1, double f2, double f3, double f4, double eps12)
 {
-    const double p0 = fma(2.0, f0, fma(-7.0, f1, 11.0 * f2));
-    const double p1 = fma(-1.0, f1, fma(5.0, f2, 2.0 * f3));
-    const double p2 = fma(2.0, f2, fma(5.0, f3, -f4));
-    const double s0 = fma(-2.0, f1, f0) + f2, r0 = fma(-4.0, f1, f0) + 3.0 * f2;
-    const double s1 = fma(-2.0, f2, f1) + f3, r1 = f1 - f3;
-    const double s2 = fma(-2.0, f3, f2) + f4, r2 = fma(-4.0, f3, 3.0 * f2) + f4;
-    const double d0 = eps + fma(13.0 / 12.0 * s0, s0, 0.25 * r0 * r0);
-    const double d1 = eps + fma(13.0 / 12.0 * s1, s1, 0.25 * r1 * r1);
-    const double d2 = eps + fma(13.0 / 12.0 * s2, s2, 0.25 * r2 * r2);
+    // gamma_i x 6 x candidate: 6 p0 = 2f0 - 7f1 + 11f2, 6 p1 = -f1 + 5f2 + 2f3, 6 p2 = 2f2 + 5f3 - f4
+    const double g0 = fma(0.2, f0, fma(-0.7, f1, 1.1 * f2));   // 0.1 (2 f0 - 7 f1 + 11 f2)
+    const double g1 = fma(-0.6, f1, fma(3.0, f2, 1.2 * f3));   // 0.6 (-f1 + 5 f2 + 2 f3)
+    const double g2 = fma(0.6, f2, fma(1.5, f3, -0.3 * f4));   // 0.3 (2 f2 + 5 f3 - f4)
+    const double s0 = fma(-2.0, f1, f0) + f2;
+    const double s1 = fma(-2.0, f2, f1) + f3;
+    const double s2 = fma(-2.0, f3, f2) + f4;
+    const double r0 = fma(2.0, f2 - f1, s0);  // f0 - 4 f1 + 3 f2
+    const double r1 = f1 - f3;
+    const double r2 = fma(2.0, f2 - f3, s2);  // 3 f2 - 4 f3 + f4
+    const double d0 = fma(13.0 * s0, s0, fma(3.0 * r0, r0, eps12));  // 12 (eps + beta_0)
+    const double d1 = fma(13.0 * s1, s1, fma(3.0 * r1, r1, eps12));
+    const double d2 = fma(13.0 * s2, s2, fma(3.0 * r2, r2, eps12));
     const double e0 = d0 * d0, e1 = d1 * d1, e2 = d2 * d2;
-    const double a0 = 0.1 * (e1 * e2), a1 = 0.6 * (e0 * e2), a2 = 0.3 * (e0 * e1);
-    const double num = fma(a0, p0, fma(a1, p1, a2 * p2));
-    return num / (6.0 * (a0 + a1 + a2));
+    const double a0 = e1 * e2, a1 = e0 * e2, a2 = e0 * e1;   // alpha_i / gamma_i, common factor dropped
+    const double num = fma(a0, g0, fma(a1, g1, a2 * g2));
+    const double den = fma(0.6, a0, fma(3.6, a1, 1.8 * a2)); // 6 sum gamma_i a_i
+    return num / den;
 }
 
 // ---------------------------------------------------------------------------
@@ -267,7 +279,7 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
     for (int e = threadIdx.x; e < E; e += blockDim.x)
         LAM[e] = 0.5 * fmax(SP[e - 1 + H], SP[e + H]);  // half the edge's local wave speed
     __syncthreads();
-    const double eps = (PDE == EULER) ? a.prm[4] : a.prm[1];
+    const double eps12 = 12.0 * ((PDE == EULER) ? a.prm[4] : a.prm[1]);
     const int items = NV * 2 * E;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int r = it / E;
@@ -279,11 +291,11 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
         double rec;
         if ((r & 1) == 0) {  // f+ = C/2 + (lam/2) Q on points e-3..e+1
             rec = weno5(fma(hl, Qv[e], C[e]), fma(hl, Qv[e + 1], C[e + 1]), fma(hl, Qv[e + 2], C[e + 2]),
-                        fma(hl, Qv[e + 3], C[e + 3]), fma(hl, Qv[e + 4], C[e + 4]), eps);
+                        fma(hl, Qv[e + 3], C[e + 3]), fma(hl, Qv[e + 4], C[e + 4]), eps12);
         } else {  // f- = C/2 - (lam/2) Q on points e+2..e-2 (mirrored)
             rec = weno5(fma(-hl, Qv[e + 5], C[e + 5]), fma(-hl, Qv[e + 4], C[e + 4]),
                         fma(-hl, Qv[e + 3], C[e + 3]), fma(-hl, Qv[e + 2], C[e + 2]),
-                        fma(-hl, Qv[e + 1], C[e + 1]), eps);
+                        fma(-hl, Qv[e + 1], C[e + 1]), eps12);
         }
         REC[r * E + e] = rec;
     }
@@ -441,7 +453,7 @@ size_t atk_stage_smem_bytes(int pde, int Tw, int H)
 int atk_stage_block(int pde, int Tw)
 {
     int nv = (pde == atk::RNS || pde == atk::EULER) ? 4 : 1;
-    int want = (pde == atk::EULER || pde == atk::ADV_WENO) ? 256 : nv * Tw;
+    int want = (pde == atk::EULER || pde == atk::ADV_WENO || pde == atk::BURGERS) ? 256 : nv * Tw;
     if (want > 256) want = 256;
     want = ((want + 31) / 32) * 32;
     return want < 32 ? 32 : want;
@@ -464,6 +476,7 @@ cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaSt
         else atk::stage_central<atk::RNS, 3><<<grid, block, smem, st>>>(a);
         break;
     case atk::EULER: atk::stage_weno<atk::EULER><<<grid, block, smem, st>>>(a); break;
+    case atk::BURGERS: atk::stage_weno<atk::BURGERS><<<grid, block, smem, st>>>(a); break;
     default: atk::stage_weno<atk::ADV_WENO><<<grid, block, smem, st>>>(a); break;
     }
     return cudaGetLastError();
@@ -487,6 +500,8 @@ cudaError_t atk_set_smem_limits()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(atk::stage_weno<atk::ADV_WENO>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(atk::stage_weno<atk::BURGERS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(atk::stage_central<atk::RNS, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(atk::stage_central<atk::RNS, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -503,12 +518,14 @@ cudaError_t atk_set_smem_limits()
 
 // ---------------------------------------------------------------------------
 // batched path launchers.  Kernel variants: 0..2 advection-diffusion with
-// H = 1..3, 3..5 reacting N-S with H = 1..3, 6 reactive Euler, 7 scalar WENO.
+// H = 1..3, 3..5 reacting N-S with H = 1..3, 6 reactive Euler, 7 scalar WENO
+// advection, 8 Burgers.
 // ---------------------------------------------------------------------------
 int atk_batch_variant(int pde, int order)
 {
     if (pde == atk::ADVDIFF) return order / 2 - 1;
     if (pde == atk::RNS) return 3 + order / 2 - 1;
+    if (pde == atk::BURGERS) return 8;
     return pde == atk::EULER ? 6 : 7;
 }
 
@@ -522,6 +539,7 @@ static void* batch_fn(int variant)
     case 4: return (void*)atk::batch_run<atk::RNS, 2, false>;
     case 5: return (void*)atk::batch_run<atk::RNS, 3, false>;
     case 6: return (void*)atk::batch_run<atk::EULER, 3, true>;
+    case 8: return (void*)atk::batch_run<atk::BURGERS, 3, true>;
     default: return (void*)atk::batch_run<atk::ADV_WENO, 3, true>;
     }
 }
@@ -547,6 +565,7 @@ static void* batch_stage_fn(int variant)
     case 4: return (void*)atk::batch_stage<atk::RNS, 2, false>;
     case 5: return (void*)atk::batch_stage<atk::RNS, 3, false>;
     case 6: return (void*)atk::batch_stage<atk::EULER, 3, true>;
+    case 8: return (void*)atk::batch_stage<atk::BURGERS, 3, true>;
     default: return (void*)atk::batch_stage<atk::ADV_WENO, 3, true>;
     }
 }

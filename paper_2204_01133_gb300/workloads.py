@@ -11,6 +11,7 @@ Physics constants of the workloads (``prm``):
 
 * ``advdiff``   [c, a]                              u_t + c u_x = a u_xx
 * ``adv_weno``  [c, eps]                            u_t + c u_x = 0 (WENO5)
+* ``burgers``   [0, eps]                            u_t + (u^2/2)_x = 0 (WENO5)
 * ``rns``       [gamma, mu, Pr, Le, A, Ea, q_c]     reacting Navier-Stokes
 * ``euler``     [gamma, A, Ea, Q, eps]              reactive Euler (WENO5)
 
@@ -24,7 +25,7 @@ from functools import lru_cache
 
 import numpy as np
 
-NVAR = {"advdiff": 1, "adv_weno": 1, "rns": 4, "euler": 4}
+NVAR = {"advdiff": 1, "adv_weno": 1, "burgers": 1, "rns": 4, "euler": 4}
 
 
 def base_problem(**kw) -> dict:
@@ -88,6 +89,34 @@ def adv_weno_exact(pb: dict, t: float) -> np.ndarray:
     x = -1.0 + np.arange(pb["n"], dtype=np.float64) * pb["dx"]
     xs = x - c * t
     return (np.sin(np.pi * xs + 0.25) ** 4)[None, :]
+
+
+# --------------------------------------------------------------------------
+# Inviscid Burgers with WENO5 (the nonlinear order test of Sec. 3:
+# x in [-1, 1], u0 = 0.5 + sin(pi x), RK3, dt ~ dx^2).
+# --------------------------------------------------------------------------
+def burgers(n=256, pe_size=16, eps=1e-6, mode="at", k_max=1, dist="uniform", prob=(), seed=0, per_stage=1,
+            dt=None, dt_coef=None, rk="rk3tvd"):
+    dx = 2.0 / n
+    if dt is None:
+        dt = dt_coef * dx * dx if dt_coef is not None else 0.4 * dx / 1.5
+    pb = base_problem(pde="burgers", rk=rk, n=n, pe_size=pe_size, dx=dx, dt=dt, prm=[0.0, eps], mode=mode,
+                      k_max=k_max, dist=dist, prob=list(prob), seed=seed, per_stage=per_stage)
+    x = -1.0 + np.arange(n, dtype=np.float64) * dx
+    init = (0.5 + np.sin(np.pi * x))[None, :].copy()
+    return pb, init
+
+
+def burgers_exact(pb: dict, t: float) -> np.ndarray:
+    """Before the shock (t < 1/pi): u = u0(xi) with x = xi + u0(xi) t, xi by
+    Newton's method on the characteristics."""
+    x = -1.0 + np.arange(pb["n"], dtype=np.float64) * pb["dx"]
+    xi = x - 0.5 * t
+    for _ in range(60):
+        f = xi + (0.5 + np.sin(np.pi * xi)) * t - x
+        df = 1.0 + np.pi * np.cos(np.pi * xi) * t
+        xi = xi - f / df
+    return (0.5 + np.sin(np.pi * xi))[None, :]
 
 
 # --------------------------------------------------------------------------

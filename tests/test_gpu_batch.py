@@ -34,6 +34,8 @@ def mixed_instances():
     out.append((dict(pb, instance=80), init, 25))
     pb, init = W.adv_weno(n=512, pe_size=32, mode="at", k_max=3, seed=4, dt_coef=2.0)
     out.append((dict(pb, instance=81), init, 30))
+    pb, init = W.burgers(n=768, pe_size=48, mode="at", k_max=2, seed=7, dt_coef=1.0)
+    out.append((dict(pb, instance=82), init, 35))
     return out
 
 

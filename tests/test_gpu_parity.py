@@ -137,6 +137,12 @@ def test_scalar_weno(mode):
     parity(pb, u0, 100)
 
 
+@pytest.mark.parametrize("mode", ["sync", "as", "at"])
+def test_burgers_weno(mode):
+    pb, u0 = W.burgers(n=1024, pe_size=64, mode=mode, k_max=3, seed=6, dt_coef=1.0)
+    parity(pb, u0, 150)
+
+
 def test_detonation_full_size_sampled_pes():
     """The N = 2^24, 16,384-PE detonation in the launch configuration the
     benchmark times.  The oracle recomputes sampled PEs on a 5-PE window of

@@ -306,7 +306,7 @@ def test_rk2_at4_excess_error_scales_like_eq_rkat1():
 # --------------------------------------------------------------------------
 # Zero delay == synchronous (Sec. 2.2 after Eq. at1; Eq. rkat2 at k = 0)
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("maker", ["advdiff", "rns", "euler", "adv_weno"])
+@pytest.mark.parametrize("maker", ["advdiff", "rns", "euler", "adv_weno", "burgers"])
 def test_zero_delay_is_bitwise_sync(maker):
     if maker == "advdiff":
         mk = lambda **kw: W.advdiff(n=256, pe_size=16, cfl=0.075, **kw)
@@ -314,8 +314,10 @@ def test_zero_delay_is_bitwise_sync(maker):
         mk = lambda **kw: W.rns(case="flame", n=512, pe_size=32, dt=0.003, **kw)
     elif maker == "euler":
         mk = lambda **kw: W.detonation(n=2048, pe_size=256, **kw)
-    else:
+    elif maker == "adv_weno":
         mk = lambda **kw: W.adv_weno(n=128, pe_size=16, **kw)
+    else:
+        mk = lambda **kw: W.burgers(n=128, pe_size=16, **kw)
     pb_s, u0 = mk(mode="sync")
     pb_a, _ = mk(mode="at", k_max=0)
     pb_d, _ = mk(mode="at", k_max=2, dist="uniform")
@@ -580,6 +582,21 @@ def test_weno_linear_advection_orders_sync_at_as():
     assert r_a[-1] > 3.5, (e_a, r_a)
     assert r_as[-1] < 2.6, (e_as, r_as)
     assert e_as[-1] > 10 * e_a[-1]
+
+
+def test_burgers_order_before_the_shock():
+    """Sec. 3 nonlinear order test (Table wenoNLin trend): inviscid Burgers,
+    u0 = 0.5 + sin(pi x) on [-1, 1], t = 0.15 (before the shock), against the
+    exact solution along characteristics: sync and AT-WENO near 5th order,
+    AS-WENO about 2nd."""
+    def mk(n, mode, **kw):
+        pb, u0 = W.burgers(n=n, pe_size=16, mode=mode, k_max=1, dt_coef=0.5)
+        return pb, u0, lambda pb, t: W.burgers_exact(pb, t)[0]
+    e_s, r_s = _order_runs(mk, (64, 128, 256), "sync", 0.15)
+    e_a, r_a = _order_runs(mk, (64, 128, 256), "at", 0.15)
+    e_as, r_as = _order_runs(mk, (64, 128, 256), "as", 0.15)
+    assert r_s[-1] > 4.5 and r_a[-1] > 4.0, (e_s, r_s, e_a, r_a)
+    assert r_as[-1] < 2.5 and e_as[-1] > 10 * e_a[-1], (e_as, r_as)
 
 
 def test_euler_entropy_wave_closed_form():

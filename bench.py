@@ -145,10 +145,8 @@ def fp64_probe(device: int):
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2204_01133_gb300 import shard
+    return shard.env()
 
 
 def run_reference(args):
@@ -276,14 +274,19 @@ def run_batched(args):
     from paper_2204_01133_gb300 import api, build
     from paper_2204_01133_gb300 import batch as BT
     from paper_2204_01133_gb300 import workloads as W
+    from paper_2204_01133_gb300 import shard
     build.build()
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     cfg = WORKLOADS[args.workload]
     count = args.batch_count or cfg["count"]
     tune_steps = len(BT.CANDIDATES)
     total = args.warmup + tune_steps + args.steps
-    inst = W.batched_rns(count=count, seed=cfg["seed"], nsteps=total)
+    # weak scaling: every rank runs a batch of its own (seed per rank)
+    inst = W.batched_rns(count=count, seed=cfg["seed"] + 7919 * rank, nsteps=total)
     points = sum(pb["n"] for pb, _, _ in inst)
     b = BT.Batch(capacity=count, device=local)
     for i, (pb, init, n) in enumerate(inst):
@@ -297,17 +300,21 @@ def run_batched(args):
     clocks = Clocks(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     e0.record()
     b.step(args.steps)
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    if world > 1:
+        torch.distributed.barrier()
+    ms = shard.max_over_ranks(e0.elapsed_time(e1))
     clk = clocks.stop()
     for i in range(0, count, 512):
         assert b.query(i).left == 0
-    solves_s = count / (ms * 1e-3)
-    upd_s = points * args.steps / (ms * 1e-3)
+    solves_s = world * count / (ms * 1e-3)
+    upd_s = world * points * args.steps / (ms * 1e-3)
     # plain per-instance path on a random sample (same instances, same steps)
     rng = np.random.default_rng(1)
     sample = sorted(rng.choice(count, size=min(args.plain_sample, count), replace=False).tolist())
@@ -340,8 +347,12 @@ def run_batched(args):
     state_bytes = sum(8 * 4 * pb["n"] for pb, _, _ in inst)
     fl = FLOPS_PER_POINT_STAGE["rns"] * points * 4 * args.steps
     achieved = fl / (ms * 1e-3) / 1e12
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     print(json.dumps({
-        "metric": "batched solves/s", "value": solves_s, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "metric": "batched solves/s", "value": solves_s, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "instances": count, "points": points,
@@ -361,6 +372,8 @@ def run_batched(args):
                 "d2h_bytes_per_step": state_bytes / args.steps},
         "gpu_launches": 2 if tune["mode"] == 0 else 5 * args.steps + 1, "clocks": clk,
     }))
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_serving(args):
@@ -460,10 +473,8 @@ def run_ours(args):
     path = {1: "stage", 2: "persistent"}.get(st.path, "?")
     launch_ms = st.stage_ms / max(st.launches_timed, 1)
     units_per_launch = n * (S * args.steps if path == "persistent" else 1)  # point-stages per launch
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2204_01133_gb300 import shard
+    ms = shard.max_over_ranks(ms)
     value = world * n * args.steps / (ms * 1e-3)
 
     # end to end through the C ABI with host buffers: upload, steps, download
@@ -480,11 +491,7 @@ def run_ours(args):
     s.run(e2e_steps)
     api.check(api.lib().at_read(s._h, api.READ_STATE, ctypes.c_void_p(host_out.data_ptr()), state_bytes, 0))
     e2e_s = time.perf_counter() - t0
-    e2e_val = n * e2e_steps / e2e_s
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = world * n * e2e_steps / float(t.item())
+    e2e_val = world * n * e2e_steps / shard.max_over_ranks(e2e_s)
 
     if rank == 0:
         fl = FLOPS_PER_POINT_STAGE[kind] * units_per_launch  # per launch

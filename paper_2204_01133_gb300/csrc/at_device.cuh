@@ -6,6 +6,8 @@
 #pragma once
 #include <cstdint>
 
+#include "exp_table.h"
+
 #define AT_KMAX_LIMIT 15
 #define AT_QMAX 3
 #define AT_HMAX 3
@@ -30,6 +32,7 @@ struct StageArgs {
     int64_t N, P;
     int64_t level;     // n: the step being computed
     int B, Tw, wpp;    // PE size, window length, windows per PE
+    int wpc, win_smem; // per-stage central kernels: windows per CTA, shared doubles per window
     int stage, S, R, H, q, nvar;
     int mode, kmax, per_stage, rk;
     uint32_t instance, key0, key1;
@@ -94,6 +97,39 @@ __device__ __forceinline__ int keff_at(const StageArgs& a, int64_t level, int st
 __device__ __forceinline__ int keff(const StageArgs& a, int64_t pe, int side)
 {
     return keff_at(a, a.level, a.stage, pe, side);
+}
+
+// exp(x) by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989)
+// with 64 table entries: x = (64 M + j) ln2/64 + r, |r| <= ln2/128, and
+// exp(x) = 2^M 2^(j/64) (1 + expm1(r)), expm1(r) by its Taylor polynomial of
+// degree 5 (the first omitted term is below 4e-17).  The product with 2^M is
+// an integer add to the exponent field, exact while the result is normal,
+// which the fast path |x| < 512 guarantees (tested on the high word with
+// integer instructions); every other x (and Inf, NaN) goes to exp().  About
+// ten FP64 instructions; within 2 ulp of the correctly rounded value.
+__device__ __forceinline__ double at_exp(double x)
+{
+    if ((__double2hiint(x) & 0x7fffffff) >= 0x40800000) return exp(x);
+    const double shift = 0x1.8p52;                 // round to integer, result in the low word
+    const double t = fma(x, AT_EXP_INV_L, shift);
+    const int n = __double2loint(t);               // 64 M + j
+    const double nf = t - shift;
+    double r = fma(-nf, AT_EXP_L_HI, x);
+    r = fma(-nf, AT_EXP_L_LO, r);
+    double c = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    c = fma(c, r, 1.0 / 6.0);
+    c = fma(c, r, 0.5);
+    const double em1 = fma(c, r * r, r);           // expm1(r)
+    const double tj = __ldg(&at_exp_tab[n & 63]);  // 2^(j/64)
+    const double e = fma(tj, em1, tj);
+    return __hiloint2double(__double2hiint(e) + ((n >> 6) << 20), __double2loint(e));
+}
+
+// Inf or NaN: exponent field all ones, tested on the high word with integer
+// instructions (the FP64 pipe is the scarce one on this chip)
+__device__ __forceinline__ bool nonfinite(double v)
+{
+    return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
 }
 
 __device__ __forceinline__ int64_t ring_index(const StageArgs& a, int64_t level, int stage, int64_t pe, int side,

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                     const int v = it / B;
                     const int jl = it - v * B;
                     const double y = point_update<PDE, H>(a, s, v, jl, G, E, X, U, ACC, W2, B, last);
-                    if (!isfinite(y)) bad = 1;
+                    if (nonfinite(y)) bad = 1;
                     int side = -1, h = 0;
                     if (jl < H) {
                         side = 0;

@@ -46,14 +46,14 @@ __device__ __forceinline__ Cx launch_cx(const StageArgs& a) { return Cx{a.level,
 // Work items: one per point of the window inside the PE (read the field,
 // derive), plus one per (buffer point, time level) pair of the window's PE
 // boundaries (read the ring at level n-k-l, derive).  All items run
-// concurrently, one per thread; the level contributions are then combined
-// per buffer point with the extrapolation weights.  HS stages the level
-// contributions: [2 H (q+1)][ND].
+// concurrently, one per thread of the window's thread group (lt of gs); the
+// level contributions are then combined per buffer point with the
+// extrapolation weights.  HS stages the level contributions: [2 H (q+1)][ND].
 // ---------------------------------------------------------------------------
 template <int PDE, bool WENO>
 __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, double* __restrict__ G,
                                             double* __restrict__ SP, double* __restrict__ HS, int64_t pe, int chunk,
-                                            int64_t t0, int W2)
+                                            int64_t t0, int W2, int lt, int gs)
 {
     using P = Phys<PDE>;
     constexpr int NV = P::NV, ND = P::ND;
@@ -63,7 +63,7 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
     const int nw = (a.mode == AT) ? a.q + 1 : 1;     // time levels per ring-halo point
     const int own = W2 - L0 - R0;
     const int items = own + (L0 + R0) * nw;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    for (int it = lt; it < items; it += gs) {
         double g[ND];
         double Q[NV];
         if (it < own) {
@@ -100,10 +100,9 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
             }
         }
     }
-    if (L0 + R0 == 0) return;
-    __syncthreads();
+    __syncthreads();  // unconditional: every thread group of the CTA passes the same barriers
     // weighted sum of the level contributions of every buffer point, in level order
-    for (int c = threadIdx.x; c < (L0 + R0) * ND; c += blockDim.x) {
+    for (int c = lt; c < (L0 + R0) * ND; c += gs) {
         const int hp = c / ND, d = c - hp * ND;
         const int side = hp < L0 ? 0 : 1;
         const int k = keff_at(a, cx.level, cx.stage, pe, side);
@@ -117,43 +116,56 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
 // ---------------------------------------------------------------------------
 // 3. RK update of this stage, ring push, non-finite check
 // ---------------------------------------------------------------------------
+// pointwise operands of one update besides K and the stage argument: u^n and
+// the accumulator, loaded only where the scheme reads them
+struct RkIn {
+    double un, ac;
+};
+
+__device__ __forceinline__ RkIn rk_load(const StageArgs& a, const Cx& cx, int64_t idx)
+{
+    RkIn r{0.0, 0.0};
+    if (!(a.rk == RK3TVD && cx.stage == 0)) r.un = cx.u[idx];
+    if (a.rk != RK3TVD && cx.stage > 0) r.ac = a.acc[idx];
+    return r;
+}
+
 __device__ __forceinline__ void rk_update(const StageArgs& a, const Cx& cx, int v, int64_t j, int jpe, int64_t pe,
-                                          double K, double x)
+                                          double K, double x, RkIn in)
 {
     const int64_t idx = v * a.N + j;
     const double dt = a.dt;
+    const double un = in.un;
     double y;
     if (a.rk == RK4) {
-        const double un = cx.u[idx];
         if (cx.stage == 0) {
             a.acc[idx] = K;
             y = fma(0.5 * dt, K, un);
         } else if (cx.stage < 3) {
-            a.acc[idx] = fma(2.0, K, a.acc[idx]);
+            a.acc[idx] = fma(2.0, K, in.ac);
             y = fma(cx.stage == 1 ? 0.5 * dt : dt, K, un);
         } else {
-            y = fma(dt * (1.0 / 6.0), a.acc[idx] + K, un);
+            y = fma(dt * (1.0 / 6.0), in.ac + K, un);
         }
     } else if (a.rk == RK3TVD) {
         const double xs = fma(dt, K, x);
         if (cx.stage == 0) {
             y = xs;
         } else if (cx.stage == 1) {
-            y = fma(0.75, cx.u[idx], 0.25 * xs);
+            y = fma(0.75, un, 0.25 * xs);
         } else {
-            y = fma(1.0 / 3.0, cx.u[idx], (2.0 / 3.0) * xs);
+            y = fma(1.0 / 3.0, un, (2.0 / 3.0) * xs);
         }
     } else {  // RK2 (Heun)
-        const double un = cx.u[idx];
         if (cx.stage == 0) {
             a.acc[idx] = K;
             y = fma(dt, K, un);
         } else {
-            y = fma(0.5 * dt, a.acc[idx] + K, un);
+            y = fma(0.5 * dt, in.ac + K, un);
         }
     }
     cx.Y[idx] = y;
-    if (!isfinite(y)) atomicOr(a.status, 1);
+    if (nonfinite(y)) atomicOr(a.status, 1);
     int side = -1, h = 0;
     if (jpe < a.H) {
         side = 0;
@@ -172,7 +184,8 @@ __device__ __forceinline__ void rk_update(const StageArgs& a, const Cx& cx, int 
 // central stencils: advection-diffusion and reacting Navier-Stokes
 // ---------------------------------------------------------------------------
 template <int PDE, int H>
-__device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx, int64_t win, double* sm)
+__device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx, int64_t win, double* sm, int lt,
+                                               int gs)
 {
     using P = Phys<PDE>;
     constexpr int NV = P::NV;
@@ -182,15 +195,33 @@ __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx,
     const int64_t pe = win / a.wpp;
     const int chunk = (int)(win - pe * a.wpp);
     const int64_t t0 = pe * a.B + (int64_t)chunk * a.Tw;
-    fill_window<PDE, false>(a, cx, G, nullptr, HS, pe, chunk, t0, W2);
-    __syncthreads();
     const int items = NV * a.Tw;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    // advection-diffusion (few FP64 operations per byte): the pointwise
+    // operands of the thread's first update item are loaded before the fill,
+    // so that their latency overlaps it
+    constexpr bool kPrefetch = (PDE == ADVDIFF);
+    double x0 = 0.0;
+    RkIn in0{0.0, 0.0};
+    if (kPrefetch && lt < items) {
+        const int v = lt / a.Tw;
+        const int64_t idx = v * a.N + t0 + (lt - v * a.Tw);
+        if constexpr (PDE != ADVDIFF) x0 = cx.X[idx];
+        in0 = rk_load(a, cx, idx);
+    }
+    fill_window<PDE, false>(a, cx, G, nullptr, HS, pe, chunk, t0, W2, lt, gs);
+    __syncthreads();
+    for (int it = lt; it < items; it += gs) {
         const int v = it / a.Tw;
         const int jl = it - v * a.Tw;
         const int64_t j = t0 + jl;
         const int c = jl + H;
-        double K = 0.0, x = 0.0;
+        double x = x0;
+        RkIn in = in0;
+        if (!kPrefetch || it != lt) {
+            if constexpr (PDE != ADVDIFF) x = cx.X[v * a.N + j];
+            in = rk_load(a, cx, v * a.N + j);
+        }
+        double K = 0.0;
         if constexpr (PDE == ADVDIFF) {
 #pragma unroll
             for (int o = -H; o <= H; ++o) K = fma(a.cm[o + H], G[c + o], K);
@@ -205,18 +236,23 @@ __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx,
 #pragma unroll
                 for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[c + o], K);
             }
-            x = cx.X[v * a.N + j];
             if (v == 3) K = fma(-a.prm[4] * x, exp(-a.prm[5] / G[7 * W2 + c]), K);
         }
-        rk_update(a, cx, v, j, chunk * a.Tw + jl, pe, K, x);
+        rk_update(a, cx, v, j, chunk * a.Tw + jl, pe, K, x, in);
     }
 }
 
+// One CTA evaluates a.wpc consecutive windows, one thread group each (a.wpc
+// > 1 only when every window spans a whole PE, so all groups pass the same
+// barriers, and a.wpc divides the window count).
 template <int PDE, int H>
-__global__ void __launch_bounds__(256) stage_central(const StageArgs a)
+__global__ void __launch_bounds__(256, PDE == ADVDIFF ? 6 : 5) stage_central(const StageArgs a)
 {
     extern __shared__ double sm[];
-    central_window<PDE, H>(a, launch_cx(a), blockIdx.x, sm);
+    const int gs = blockDim.x / a.wpc;
+    const int g = threadIdx.x / gs;
+    central_window<PDE, H>(a, launch_cx(a), (int64_t)blockIdx.x * a.wpc + g, sm + (size_t)g * a.win_smem,
+                           threadIdx.x - g * gs, gs);
 }
 
 // ---------------------------------------------------------------------------
@@ -274,7 +310,7 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
     const int64_t pe = win / a.wpp;
     const int chunk = (int)(win - pe * a.wpp);
     const int64_t t0 = pe * a.B + (int64_t)chunk * Tw;
-    fill_window<PDE, true>(a, cx, G, SP, HS, pe, chunk, t0, W2);
+    fill_window<PDE, true>(a, cx, G, SP, HS, pe, chunk, t0, W2, threadIdx.x, blockDim.x);
     __syncthreads();
     for (int e = threadIdx.x; e < E; e += blockDim.x)
         LAM[e] = 0.5 * fmax(SP[e - 1 + H], SP[e + H]);  // half the edge's local wave speed
@@ -318,7 +354,7 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
                 K = fma(-a.prm[1] * Q[3], exp(-a.prm[2] * Q[0] / p), K);
             }
         }
-        rk_update(a, cx, v, j, chunk * Tw + jl, pe, K, x);
+        rk_update(a, cx, v, j, chunk * Tw + jl, pe, K, x, rk_load(a, cx, v * a.N + j));
     }
 }
 
@@ -365,7 +401,7 @@ __global__ void __launch_bounds__(256) batch_run(const StageArgs* __restrict__ t
                     if constexpr (WENO)
                         weno_window<PDE>(a, cx, w, sm);
                     else
-                        central_window<PDE, H>(a, cx, w, sm);
+                        central_window<PDE, H>(a, cx, w, sm, threadIdx.x, blockDim.x);
                     __syncthreads();
                 }
             }
@@ -382,7 +418,7 @@ __global__ void __launch_bounds__(256) batch_run(const StageArgs* __restrict__ t
 // win_idx[w]), so large instances spread over all SMs; an instance with no
 // steps left, or whose RK scheme has fewer stages, skips the launch.
 template <int PDE, int H, bool WENO>
-__global__ void __launch_bounds__(256) batch_stage(const StageArgs* __restrict__ tab, const int64_t* __restrict__ lvl,
+__global__ void __launch_bounds__(256, 4) batch_stage(const StageArgs* __restrict__ tab, const int64_t* __restrict__ lvl,
                                                    const int64_t* __restrict__ left, const int* __restrict__ win_slot,
                                                    const int* __restrict__ win_idx, int stage)
 {
@@ -397,7 +433,7 @@ __global__ void __launch_bounds__(256) batch_stage(const StageArgs* __restrict__
     if constexpr (WENO)
         weno_window<PDE>(a, cx, win_idx[blockIdx.x], sm);
     else
-        central_window<PDE, H>(a, cx, win_idx[blockIdx.x], sm);
+        central_window<PDE, H>(a, cx, win_idx[blockIdx.x], sm, threadIdx.x, blockDim.x);
 }
 
 // after every stage of a step: advance the level of each slot with steps left
@@ -462,22 +498,37 @@ int atk_stage_block(int pde, int Tw)
 cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaStream_t st)
 {
     const int64_t windows = a.P * a.wpp;
-    const dim3 grid((unsigned)windows), block(atk_stage_block(pde, a.Tw));
-    const size_t smem = atk_stage_smem_bytes(pde, a.Tw, a.H);
+    const int b1 = atk_stage_block(pde, a.Tw);
+    const size_t smem1 = atk_stage_smem_bytes(pde, a.Tw, a.H);
+    // central stencils on small windows: several windows per CTA (whole PEs
+    // only, dividing the window count), so a CTA carries up to 256 threads
+    int m = 1;
+    if ((pde == atk::ADVDIFF || pde == atk::RNS) && a.wpp == 1) {
+        for (int c = 4; c >= 2; c /= 2)
+            if (c * b1 <= 256 && windows % c == 0) {
+                m = c;
+                break;
+            }
+    }
+    atk::StageArgs b = a;
+    b.wpc = m;
+    b.win_smem = (int)(smem1 / sizeof(double));
+    const dim3 grid((unsigned)(windows / m)), block(b1 * m);
+    const size_t smem = smem1 * m;
     switch (pde) {
     case atk::ADVDIFF:
-        if (order == 2) atk::stage_central<atk::ADVDIFF, 1><<<grid, block, smem, st>>>(a);
-        else if (order == 4) atk::stage_central<atk::ADVDIFF, 2><<<grid, block, smem, st>>>(a);
-        else atk::stage_central<atk::ADVDIFF, 3><<<grid, block, smem, st>>>(a);
+        if (order == 2) atk::stage_central<atk::ADVDIFF, 1><<<grid, block, smem, st>>>(b);
+        else if (order == 4) atk::stage_central<atk::ADVDIFF, 2><<<grid, block, smem, st>>>(b);
+        else atk::stage_central<atk::ADVDIFF, 3><<<grid, block, smem, st>>>(b);
         break;
     case atk::RNS:
-        if (order == 2) atk::stage_central<atk::RNS, 1><<<grid, block, smem, st>>>(a);
-        else if (order == 4) atk::stage_central<atk::RNS, 2><<<grid, block, smem, st>>>(a);
-        else atk::stage_central<atk::RNS, 3><<<grid, block, smem, st>>>(a);
+        if (order == 2) atk::stage_central<atk::RNS, 1><<<grid, block, smem, st>>>(b);
+        else if (order == 4) atk::stage_central<atk::RNS, 2><<<grid, block, smem, st>>>(b);
+        else atk::stage_central<atk::RNS, 3><<<grid, block, smem, st>>>(b);
         break;
-    case atk::EULER: atk::stage_weno<atk::EULER><<<grid, block, smem, st>>>(a); break;
-    case atk::BURGERS: atk::stage_weno<atk::BURGERS><<<grid, block, smem, st>>>(a); break;
-    default: atk::stage_weno<atk::ADV_WENO><<<grid, block, smem, st>>>(a); break;
+    case atk::EULER: atk::stage_weno<atk::EULER><<<grid, block, smem, st>>>(b); break;
+    case atk::BURGERS: atk::stage_weno<atk::BURGERS><<<grid, block, smem, st>>>(b); break;
+    default: atk::stage_weno<atk::ADV_WENO><<<grid, block, smem, st>>>(b); break;
     }
     return cudaGetLastError();
 }

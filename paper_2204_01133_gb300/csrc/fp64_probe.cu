@@ -4,9 +4,12 @@
 // measures the FP64 FMA rate the GPU sustains: every thread runs 8
 // independent fma chains, so the pipe, not latency, limits the rate.  Used
 // by the benchmark to put the roofline denominator next to the nominal one.
+// It also exports the stage kernels' table-driven exponential for testing.
 #include <cuda_runtime.h>
 
 #include <cstdint>
+
+#include "at_device.cuh"
 
 namespace {
 
@@ -105,4 +108,24 @@ extern "C" int at_probe_fp64_fma_lanes(int device, void* stream, int iters, int 
 extern "C" int at_probe_fp64_fma(int device, void* stream, int iters, int reps, double* tflops, double* ms_best)
 {
     return at_probe_fp64_fma_lanes(device, stream, iters, reps, 32, tflops, ms_best);
+}
+
+namespace {
+__global__ void exp_eval(const double* __restrict__ x, double* __restrict__ y, int64_t n, int which)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = which == 0 ? atk::at_exp(x[i]) : exp(x[i]);
+}
+} // namespace
+
+// y[i] = at_exp(x[i]) (which = 0) or CUDA's exp(x[i]) (which = 1) for device
+// arrays of n doubles, on the default stream; synchronous.
+extern "C" int at_probe_exp(const double* x, double* y, int64_t n, int which)
+{
+    if (n <= 0) return 0;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    exp_eval<<<blocks, 256>>>(x, y, n, which);
+    if (cudaGetLastError() != cudaSuccess) return -3;
+    return cudaDeviceSynchronize() != cudaSuccess ? -3 : 0;
 }

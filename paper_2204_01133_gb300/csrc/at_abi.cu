@@ -228,6 +228,8 @@ atk::StageArgs build_args(const at_problem* pb, const at_delays* dl, const Layou
     a.key0 = (uint32_t)(dl->seed & 0xffffffffu);
     a.key1 = (uint32_t)(dl->seed >> 32);
     a.dt = pb->dt;
+    a.hdt = 0.5 * pb->dt;
+    a.dt6 = pb->dt * (1.0 / 6.0);
     thresholds(dl, a.thr);
     for (int k = 0; k <= dl->k_max; ++k) extrap_weights(L.q, k, a.w[k]);
     for (int i = 0; i < 16; ++i) a.prm[i] = pb->prm[i];

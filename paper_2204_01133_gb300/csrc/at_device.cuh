@@ -36,7 +36,7 @@ struct StageArgs {
     int stage, S, R, H, q, nvar;
     int mode, kmax, per_stage, rk;
     uint32_t instance, key0, key1;
-    double dt;
+    double dt, hdt, dt6;                      // dt, dt/2, dt/6 (formed once on the host)
     uint64_t thr[AT_KMAX_LIMIT];              // Philox word-0 thresholds
     double w[AT_KMAX_LIMIT + 1][AT_QMAX + 1]; // extrapolation weights by delay
     double c1[2 * AT_HMAX + 1];               // -d1_m / dx  (central)
@@ -125,6 +125,23 @@ __device__ __forceinline__ double at_exp(double x)
     return __hiloint2double(__double2hiint(e) + ((n >> 6) << 20), __double2loint(e));
 }
 
+// 1/x by two Newton-Raphson steps r <- r + r (1 - x r) from the hardware's
+// approximate reciprocal (rcp.approx.ftz.f64): each step squares the
+// relative error, leaving the result within about an ulp of 1/x for the
+// normal, finite, nonzero x the kernels divide by (densities, pressures,
+// temperatures, WENO weight sums).  Zero, Inf or subnormal x give Inf or
+// NaN, which the non-finite check reports.  Five FP64-pipe instructions, about
+// half of an IEEE division.
+__device__ __forceinline__ double at_rcp(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
 // Inf or NaN: exponent field all ones, tested on the high word with integer
 // instructions (the FP64 pipe is the scarce one on this chip)
 __device__ __forceinline__ bool nonfinite(double v)
@@ -164,7 +181,7 @@ struct Phys<RNS> {
     __device__ static void derive(const StageArgs& a, const double* Q, double* g)
     {
         const double gm1 = a.prm[0] - 1.0, qc = a.prm[6];
-        const double rinv = 1.0 / Q[0];
+        const double rinv = at_rcp(Q[0]);
         const double u = Q[1] * rinv;
         const double p = gm1 * (Q[2] - fma(0.5 * Q[1], u, qc * Q[3]));
         const double T = p * rinv;
@@ -182,7 +199,7 @@ struct Phys<RNS> {
     __device__ static double temperature(const StageArgs& a, const double* Q)
     {
         const double gm1 = a.prm[0] - 1.0, qc = a.prm[6];
-        const double rinv = 1.0 / Q[0];
+        const double rinv = at_rcp(Q[0]);
         const double u = Q[1] * rinv;
         const double p = gm1 * (Q[2] - fma(0.5 * Q[1], u, qc * Q[3]));
         return p * rinv;
@@ -200,7 +217,7 @@ struct Phys<EULER> {
     }
     __device__ static void derive(const StageArgs& a, const double* Q, double* g)
     {
-        const double u = Q[1] / Q[0];
+        const double u = Q[1] * at_rcp(Q[0]);
         const double p = pressure(a, Q, u);
         g[0] = 0.5 * Q[1];
         g[1] = 0.5 * fma(Q[1], u, p);
@@ -213,7 +230,7 @@ struct Phys<EULER> {
     }
     __device__ static double speed(const StageArgs& a, const double* Q)
     {
-        const double rinv = 1.0 / Q[0];
+        const double rinv = at_rcp(Q[0]);
         const double u = Q[1] * rinv;
         const double p = pressure(a, Q, u);
         return fabs(u) + sqrt(a.prm[0] * p * rinv);

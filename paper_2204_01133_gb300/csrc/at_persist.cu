@@ -87,12 +87,12 @@ __device__ __forceinline__ double point_update(const StageArgs& a, int s, int v,
     if (a.rk == RK4) {
         if (s == 0) {
             ACC[it] = K;
-            y = fma(0.5 * dt, K, un);
+            y = fma(a.hdt, K, un);
         } else if (s < 3) {
             ACC[it] = fma(2.0, K, ACC[it]);
-            y = fma(s == 1 ? 0.5 * dt : dt, K, un);
+            y = fma(s == 1 ? a.hdt : dt, K, un);
         } else {
-            y = fma(dt * (1.0 / 6.0), ACC[it] + K, un);
+            y = fma(a.dt6, ACC[it] + K, un);
         }
     } else if (a.rk == RK3TVD) {
         const double xs = fma(dt, K, x);
@@ -104,7 +104,7 @@ __device__ __forceinline__ double point_update(const StageArgs& a, int s, int v,
             ACC[it] = K;
             y = fma(dt, K, un);
         } else {
-            y = fma(0.5 * dt, ACC[it] + K, un);
+            y = fma(a.hdt, ACC[it] + K, un);
         }
     }
     X[it] = y;  // next stage argument (u^{n+1} after the last stage)
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                         double Q[NV];
 #pragma unroll
                         for (int v = 0; v < NV; ++v) Q[v] = X[v * B + it];
-                        E[it] = exp(-a.prm[5] / P::temperature(a, Q));
+                        E[it] = at_exp(-a.prm[5] * at_rcp(P::temperature(a, Q)));
                     }
                 }
             }

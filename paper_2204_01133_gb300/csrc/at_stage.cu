@@ -140,12 +140,12 @@ __device__ __forceinline__ void rk_update(const StageArgs& a, const Cx& cx, int 
     if (a.rk == RK4) {
         if (cx.stage == 0) {
             a.acc[idx] = K;
-            y = fma(0.5 * dt, K, un);
+            y = fma(a.hdt, K, un);
         } else if (cx.stage < 3) {
             a.acc[idx] = fma(2.0, K, in.ac);
-            y = fma(cx.stage == 1 ? 0.5 * dt : dt, K, un);
+            y = fma(cx.stage == 1 ? a.hdt : dt, K, un);
         } else {
-            y = fma(dt * (1.0 / 6.0), in.ac + K, un);
+            y = fma(a.dt6, in.ac + K, un);
         }
     } else if (a.rk == RK3TVD) {
         const double xs = fma(dt, K, x);
@@ -161,7 +161,7 @@ __device__ __forceinline__ void rk_update(const StageArgs& a, const Cx& cx, int 
             a.acc[idx] = K;
             y = fma(dt, K, un);
         } else {
-            y = fma(0.5 * dt, in.ac + K, un);
+            y = fma(a.hdt, in.ac + K, un);
         }
     }
     cx.Y[idx] = y;
@@ -236,7 +236,7 @@ __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx,
 #pragma unroll
                 for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[c + o], K);
             }
-            if (v == 3) K = fma(-a.prm[4] * x, exp(-a.prm[5] / G[7 * W2 + c]), K);
+            if (v == 3) K = fma(-a.prm[4] * x, at_exp(-a.prm[5] * at_rcp(G[7 * W2 + c])), K);
         }
         rk_update(a, cx, v, j, chunk * a.Tw + jl, pe, K, x, in);
     }
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(256, PDE == ADVDIFF ? 6 : 5) stage_central(con
 //    s_i the second difference and r_0, r_2 built from s_0, s_2) and eps as
 //    12 eps: the weights omega_i = alpha_i / sum alpha are unchanged by a
 //    common factor of the indicators and eps;
-//  * the three weights share one division: alpha_i ~ gamma_i prod_{j!=i}
+//  * the three weights share one reciprocal: alpha_i ~ gamma_i prod_{j!=i}
 //    d_j^2, with gamma_i and the candidates' 1/6 folded into constants.
 // eps12 = 12 eps.
 // ---------------------------------------------------------------------------
@@ -287,7 +287,7 @@ __device__ __forceinline__ double weno5(double f0, double f1, double f2, double 
     const double a0 = e1 * e2, a1 = e0 * e2, a2 = e0 * e1;   // alpha_i / gamma_i, common factor dropped
     const double num = fma(a0, g0, fma(a1, g1, a2 * g2));
     const double den = fma(0.6, a0, fma(3.6, a1, 1.8 * a2)); // 6 sum gamma_i a_i
-    return num / den;
+    return num * at_rcp(den);
 }
 
 // ---------------------------------------------------------------------------
@@ -349,9 +349,9 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
         if constexpr (PDE == EULER) {
             if (v == 3) {
                 const double Q[4] = {G[4 * W2 + c], G[5 * W2 + c], G[6 * W2 + c], G[7 * W2 + c]};
-                const double u = Q[1] / Q[0];
+                const double u = Q[1] * at_rcp(Q[0]);
                 const double p = P::pressure(a, Q, u);
-                K = fma(-a.prm[1] * Q[3], exp(-a.prm[2] * Q[0] / p), K);
+                K = fma(-a.prm[1] * Q[3], at_exp(-a.prm[2] * Q[0] * at_rcp(p)), K);
             }
         }
         rk_update(a, cx, v, j, chunk * Tw + jl, pe, K, x, rk_load(a, cx, v * a.N + j));

@@ -4,7 +4,7 @@
 // measures the FP64 FMA rate the GPU sustains: every thread runs 8
 // independent fma chains, so the pipe, not latency, limits the rate.  Used
 // by the benchmark to put the roofline denominator next to the nominal one.
-// It also exports the stage kernels' table-driven exponential for testing.
+// It also exports the stage kernels' exponential and reciprocal for testing.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -111,21 +111,25 @@ extern "C" int at_probe_fp64_fma(int device, void* stream, int iters, int reps, 
 }
 
 namespace {
-__global__ void exp_eval(const double* __restrict__ x, double* __restrict__ y, int64_t n, int which)
+__global__ void fn_eval(const double* __restrict__ x, double* __restrict__ y, int64_t n, int which)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = which == 0 ? atk::at_exp(x[i]) : exp(x[i]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        y[i] = which == 0 ? atk::at_exp(v) : which == 1 ? exp(v) : which == 2 ? atk::at_rcp(v) : 1.0 / v;
+    }
 }
 } // namespace
 
-// y[i] = at_exp(x[i]) (which = 0) or CUDA's exp(x[i]) (which = 1) for device
-// arrays of n doubles, on the default stream; synchronous.
-extern "C" int at_probe_exp(const double* x, double* y, int64_t n, int which)
+// y[i] = f(x[i]) for device arrays of n doubles, on the default stream,
+// synchronous: which = 0 the kernels' table-driven exponential at_exp,
+// 1 CUDA's exp, 2 the kernels' Newton reciprocal at_rcp, 3 IEEE 1/x.
+extern "C" int at_probe_fn(const double* x, double* y, int64_t n, int which)
 {
     if (n <= 0) return 0;
+    if (which < 0 || which > 3) return -1;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    exp_eval<<<blocks, 256>>>(x, y, n, which);
+    fn_eval<<<blocks, 256>>>(x, y, n, which);
     if (cudaGetLastError() != cudaSuccess) return -3;
     return cudaDeviceSynchronize() != cudaSuccess ? -3 : 0;
 }

@@ -42,6 +42,16 @@ def test_library_exports_every_declared_symbol(L):
         assert re.search(r"\bT %s$" % f, out, flags=re.M), f
 
 
+def test_probe_library_exports_its_declared_symbols(L):
+    from paper_2204_01133_gb300 import build
+    src = open(os.path.join(ROOT, "include", "at_probe.h")).read()
+    names = sorted(set(re.findall(r"^int (at_probe_[a-z0-9_]+)\s*\(", src, flags=re.M)))
+    assert len(names) == 4
+    out = subprocess.run(["nm", "-D", "--defined-only", build.PROBE], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (at_probe_[a-z0-9_]+)$", out, flags=re.M))
+    assert exported == set(names)
+
+
 def test_library_targets_sm103a_only(L):
     from paper_2204_01133_gb300 import api
     r = subprocess.run(["cuobjdump", "--list-elf", api.LIB_PATH], capture_output=True, text=True)

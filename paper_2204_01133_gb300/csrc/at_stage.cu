@@ -256,6 +256,69 @@ __global__ void __launch_bounds__(256, PDE == ADVDIFF ? 6 : 5) stage_central(con
 }
 
 // ---------------------------------------------------------------------------
+// advection-diffusion on PEs of 32 PPL points: one warp per PE
+//
+// With one variable and a 3-, 5- or 7-point stencil a point carries too
+// little work for a CTA-wide fill and barriers to pay for.  A warp owns one
+// PE; point j of the PE belongs to lane j % 32 (coalesced loads and stores);
+// lanes 0..H-1 synthesise the left buffer points and lanes H..2H-1 the right
+// ones from the ring; the PE's row with its two halos is staged in the
+// warp's slice of shared memory, and the warp synchronises with __syncwarp
+// only.  The arithmetic, and its order, is that of central_window<ADVDIFF, H>.
+// ---------------------------------------------------------------------------
+template <int H, int PPL>
+__global__ void __launch_bounds__(256, PPL <= 2 ? 6 : (PPL == 4 ? 4 : 3)) stage_advdiff_warp(const StageArgs a)
+{
+    extern __shared__ double sm[];
+    constexpr int B = 32 * PPL;  // the PE size
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int64_t pe = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+    if (pe >= a.P) return;  // whole warps only
+    double* W = sm + wid * (B + 2 * H);  // [H left halo | B own points | H right halo]
+    const Cx cx = launch_cx(a);
+    const int64_t base = pe * B;
+    double x[PPL];
+    RkIn in[PPL];
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) {
+        x[i] = cx.X[base + lane + 32 * i];
+        in[i] = rk_load(a, cx, base + lane + 32 * i);
+    }
+    if (lane < 2 * H) {  // one buffer point: delay draw, delayed ring levels, extrapolation
+        const int side = lane < H ? 0 : 1;
+        const int h = lane - side * H;  // position in the neighbour's edge window
+        const int64_t nbr = side == 0 ? (pe == 0 ? a.P - 1 : pe - 1) : (pe == a.P - 1 ? 0 : pe + 1);
+        const int k = keff_at(a, cx.level, cx.stage, pe, side);
+        if (h == 0) a.dlog[((int64_t)cx.stage * a.P + pe) * 2 + side] = (uint8_t)k;
+        const int nw = (a.mode == AT) ? a.q + 1 : 1;
+        double v[AT_QMAX + 1];
+#pragma unroll
+        for (int l = 0; l <= AT_QMAX; ++l) {
+            v[l] = 0.0;  // a level with weight 0 is not part of the scheme (and may not exist yet)
+            if (l < nw && ((a.mode == AT) ? a.w[k][l] : 1.0) != 0.0)
+                v[l] = a.ring[ring_index(a, cx.level - k - l, cx.stage, nbr, 1 - side, h, 0)];
+        }
+        double acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * v[0];
+#pragma unroll
+        for (int l = 1; l <= AT_QMAX; ++l)
+            if (l < nw) acc = fma(a.w[k][l], v[l], acc);
+        W[side == 0 ? h : H + B + h] = acc;
+    }
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) W[H + lane + 32 * i] = x[i];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) {
+        const int j = lane + 32 * i;
+        double K = 0.0;
+#pragma unroll
+        for (int o = -H; o <= H; ++o) K = fma(a.cm[o + H], W[H + j + o], K);
+        rk_update(a, cx, 0, base + j, j, pe, K, x[i], in[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // WENO5-JS reconstruction at the right edge of f[2] from f[0..4]
 // (candidates of Eq. atRecon at k = 0, ideal weights {1/10, 3/5, 3/10},
 // indicators of Eq. betaS, weights of Eq. omg with power 2), arranged for
@@ -515,6 +578,24 @@ cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaSt
     b.win_smem = (int)(smem1 / sizeof(double));
     const dim3 grid((unsigned)(windows / m)), block(b1 * m);
     const size_t smem = smem1 * m;
+    // advection-diffusion on whole PEs of 32, 64, 128 or 256 points: one warp per PE
+    if (pde == atk::ADVDIFF && a.wpp == 1 && (a.B == 32 || a.B == 64 || a.B == 128 || a.B == 256)) {
+        const unsigned g8 = (unsigned)((a.P + 7) / 8);
+        const size_t sw = sizeof(double) * 8 * (size_t)(a.B + 2 * a.H);
+        const int ppl = a.B / 32;
+#define AT_WARP_LAUNCH(HH)                                                                              \
+    do {                                                                                                \
+        if (ppl == 1) atk::stage_advdiff_warp<HH, 1><<<g8, 256, sw, st>>>(b);                           \
+        else if (ppl == 2) atk::stage_advdiff_warp<HH, 2><<<g8, 256, sw, st>>>(b);                      \
+        else if (ppl == 4) atk::stage_advdiff_warp<HH, 4><<<g8, 256, sw, st>>>(b);                      \
+        else atk::stage_advdiff_warp<HH, 8><<<g8, 256, sw, st>>>(b);                                    \
+    } while (0)
+        if (order == 2) AT_WARP_LAUNCH(1);
+        else if (order == 4) AT_WARP_LAUNCH(2);
+        else AT_WARP_LAUNCH(3);
+#undef AT_WARP_LAUNCH
+        return cudaGetLastError();
+    }
     switch (pde) {
     case atk::ADVDIFF:
         if (order == 2) atk::stage_central<atk::ADVDIFF, 1><<<grid, block, smem, st>>>(b);

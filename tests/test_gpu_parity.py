@@ -104,6 +104,18 @@ def test_advdiff_edge_shapes(pe_size, n):
     parity(pb, u0, 60)
 
 
+@pytest.mark.parametrize("pe_size,pes,order,mode,rk,cfl", [
+    (32, 5, 6, "at", "rk4", 0.01), (32, 1, 4, "at", "rk4", 0.05), (64, 13, 4, "sync", "rk4", 0.05),
+    (128, 11, 2, "as", "rk3tvd", 0.05), (256, 9, 4, "at", "rk2", 0.04), (64, 17, 6, "as", "rk4", 0.01)])
+def test_advdiff_warp_per_pe_kernel(pe_size, pes, order, mode, rk, cfl):
+    """PEs of 32, 64, 128 or 256 points take the one-warp-per-PE kernel on the
+    per-stage path: PE counts that leave warps of the last CTA idle, a single
+    PE, every order, mode and RK scheme."""
+    pb, u0 = W.advdiff(n=pe_size * pes, pe_size=pe_size, order=order, mode=mode, k_max=3, seed=4, cfl=cfl,
+                       rk=rk)
+    parity(pb, u0, 120, path="stage")
+
+
 @pytest.mark.parametrize("path", ["stage", "persistent"])
 @pytest.mark.parametrize("case", ["flame", "ignition"])
 def test_rns_literal_size(case, path):
@@ -166,6 +178,44 @@ def test_detonation_full_size_sampled_pes():
         tol = max(TOL_RUN, 20.0 * self_drift(spb, sub, steps)) if p in (0, 1) else TOL_RUN
         assert rel_err(g[:, p * B:(p + 1) * B], ref) <= tol, p
         assert np.array_equal(gd[:, p, :], o.delays()[:, 2, :])
+
+
+def _sampled_full_size(pb, u0, steps, pes):
+    """Run the full problem on the GPU, then recompute the given PEs with the
+    oracle on a 5-PE window (global PE indices in the delay counter).  After
+    `steps` steps only points within S H steps of the window's outer edges can
+    differ, which stays outside the middle PE for the step counts used."""
+    from paper_2204_01133_gb300.api import Solver
+    P, B = pb["n"] // pb["pe_size"], pb["pe_size"]
+    s = Solver(pb, u0)
+    s.run(steps)
+    g = s.read_state()
+    gd = s.read_delays()
+    s.close()
+    for p in pes:
+        idx = np.arange(p - 2, p + 3) % P
+        sub = np.concatenate([u0[:, i * B:(i + 1) * B] for i in idx], axis=1)
+        o = oracle.Oracle(dict(pb, n=5 * B, pe_base=p - 2, pe_total=P), sub)
+        assert o.run(steps) == 0
+        assert rel_err(g[:, p * B:(p + 1) * B], o.state()[:, 2 * B:3 * B]) <= TOL_RUN, p
+        assert np.array_equal(gd[:, p, :], o.delays()[:, 2, :])
+
+
+def test_advdiff_full_size_sampled_pes():
+    """Advection-diffusion at N = 2^27 (2^21 PEs of 64), the size and launch
+    configuration of the HBM benchmark run; 12 steps move information at most
+    96 points, less than two PEs."""
+    pb, u0 = W.advdiff(n=1 << 27, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075)
+    P = pb["n"] // pb["pe_size"]
+    _sampled_full_size(pb, u0, 12, (0, 1, 123457, P - 1))
+
+
+def test_rns_full_size_sampled_pes():
+    """Reacting N-S flame at N = 2^24 (2^18 PEs of 64), per-stage launches as
+    benchmarked; 6 steps move information at most 72 points."""
+    pb, u0 = W.rns(case="flame", n=1 << 24, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003)
+    P = pb["n"] // pb["pe_size"]
+    _sampled_full_size(pb, u0, 6, (0, 77777, P // 2, P - 1))
 
 
 def test_deterministic_and_seeded():

@@ -36,6 +36,8 @@ WORKLOADS = {
                                 dt=0.003),
     "advdiff-n2048": dict(kind="advdiff", n=2048, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075),
     "advdiff-n134217728": dict(kind="advdiff", n=1 << 27, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075),
+    # a quarter of the HBM run, for counter captures (inputs still larger than L2)
+    "advdiff-n33554432": dict(kind="advdiff", n=1 << 25, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075),
     "detonation-n16777216": dict(kind="detonation", n=1 << 24, pe_size=1024, mode="at", k_max=4, seed=0),
     "rns-flame-n16777216": dict(kind="rns", case="flame", n=1 << 24, pe_size=64, mode="at", k_max=4, seed=0,
                                 dt=0.003),

@@ -61,8 +61,13 @@ typedef enum {
  *   AT_ADV_WENO u_t + c u_x = 0 with WENO5 (the order test of Sec. 3);
  *               prm = {c, eps}
  *   AT_BURGERS  u_t + (u^2/2)_x = 0 with WENO5 (the nonlinear order test of
- *               Sec. 3); prm = {0, eps}                                     */
-enum { AT_ADVDIFF = 0, AT_RNS = 1, AT_EULER = 2, AT_ADV_WENO = 3, AT_BURGERS = 4 };
+ *               Sec. 3); prm = {0, eps}
+ *   AT_RNS_CHAIN the AT_RNS equations with every product derivative
+ *               expanded by the chain rule, as in the paper's 1-D solver
+ *               (Sec. 4): only rho, u, p, rho E, Y and T are differentiated
+ *               (and extrapolated at buffer points).  Not conservative.
+ *               Same state and prm as AT_RNS; per-stage path only.        */
+enum { AT_ADVDIFF = 0, AT_RNS = 1, AT_EULER = 2, AT_ADV_WENO = 3, AT_BURGERS = 4, AT_RNS_CHAIN = 5 };
 /* RK schemes (Sec. 2.3): Heun RK2 (Eq. rk2), Shu-Osher TVD RK3, classic RK4 */
 enum { AT_RK2 = 0, AT_RK3TVD = 1, AT_RK4 = 2 };
 /* Boundary treatment (Sec. 2.1, 2.2, 3): synchronous; standard scheme on
@@ -91,7 +96,7 @@ enum {
 };
 
 typedef struct {
-    int32_t pde;      /* AT_ADVDIFF | AT_RNS | AT_EULER | AT_ADV_WENO | AT_BURGERS    */
+    int32_t pde;      /* AT_ADVDIFF | AT_RNS | AT_EULER | AT_ADV_WENO | AT_BURGERS | AT_RNS_CHAIN */
     int32_t order;    /* 2 | 4 | 6 for central PDEs; ignored for WENO5                */
     int32_t rk;       /* AT_RK2 | AT_RK3TVD | AT_RK4                                  */
     int32_t pe_size;  /* points per PE, >= 2 x halo width (order/2, or 3 for WENO5)   */
@@ -149,7 +154,8 @@ int at_set_problem(at_ctx* ctx, const at_problem* pb, double* state_dev, const d
  * with the edge windows of the current state (level 0). */
 int at_set_delays(at_ctx* ctx, const at_delays* dl);
 
-/* Enqueue nsteps full RK steps (S stage kernels each) on the stream. */
+/* Enqueue nsteps full RK steps (S stage kernels each) on the stream.  A
+ * solve holds at most 2^31 - 2 steps in total (AT_EINVAL beyond). */
 int at_step(at_ctx* ctx, int64_t nsteps);
 
 /* at_step, then synchronise the stream and return AT_EUNSTABLE if a

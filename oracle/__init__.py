@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "at_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-_PDE = {"advdiff": 0, "rns": 1, "euler": 2, "adv_weno": 3, "burgers": 4}
+_PDE = {"advdiff": 0, "rns": 1, "euler": 2, "adv_weno": 3, "burgers": 4, "rns_chain": 5}
 _RK = {"rk2": 0, "rk3tvd": 1, "rk4": 2}
 _MODE = {"sync": 0, "as": 1, "at": 2}
 _DIST = {"uniform": 0, "table": 1, "geometric": 2}

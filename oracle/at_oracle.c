@@ -223,7 +223,7 @@ double orc_weno5_js(const double v[5], double eps)
 /* ------------------------------------------------------------------ */
 /* Physics: derived quantities of one state vector                     */
 /* ------------------------------------------------------------------ */
-static int nvar_of(int pde) { return (pde == ORC_RNS || pde == ORC_EULER) ? 4 : 1; }
+static int nvar_of(int pde) { return (pde == ORC_RNS || pde == ORC_EULER || pde == ORC_RNS_CHAIN) ? 4 : 1; }
 
 static double* field(const orc_ctx* c, int64_t level, int s)
 {
@@ -240,6 +240,8 @@ static void state_at(const orc_ctx* c, const double* f, int64_t m, double* Q)
 /* ADVDIFF: [u].  ADV_WENO: [c u, u].  BURGERS: [u^2 / 2, u].
  * RNS (Eq. convEq with two species, R = 1, p = rho T):
  *   [rho u, rho u^2 + p, u (rho E + p), rho u Y, u, u^2, T, Y]
+ * RNS_CHAIN (the primitive quantities whose derivatives the chain-rule
+ * form of Sec. 4 takes): [rho, u, p, rho E, Y, T]
  * EULER: [rho u, rho u^2 + p, u (rho E + p), rho u Y, rho, rho u, rho E, rho Y] */
 static void derive(const orc_ctx* c, const double* Q, double* g)
 {
@@ -268,6 +270,18 @@ static void derive(const orc_ctx* c, const double* Q, double* g)
         g[5] = u * u;
         g[6] = p / rho;
         g[7] = Q[3] / rho;
+        break;
+    }
+    case ORC_RNS_CHAIN: {
+        double gam = pr[0], qc = pr[6];
+        double rho = Q[0], u = Q[1] / rho;
+        double p = (gam - 1.0) * (Q[2] - 0.5 * Q[1] * u - qc * Q[3]);
+        g[0] = rho;
+        g[1] = u;
+        g[2] = p;
+        g[3] = Q[2];
+        g[4] = Q[3] / rho;
+        g[5] = p / rho;
         break;
     }
     case ORC_EULER: {
@@ -387,7 +401,7 @@ static void rhs_point(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t
     const double* pr = c->pb.prm;
     const double dx = c->pb.dx;
     int pde = c->pb.pde;
-    if (pde == ORC_ADVDIFF || pde == ORC_RNS) {
+    if (pde == ORC_ADVDIFF || pde == ORC_RNS || pde == ORC_RNS_CHAIN) {
         const double *d1, *d2;
         double d1den, d2den;
         central_tables(c->pb.order, &d1, &d1den, &d2, &d2den);
@@ -406,6 +420,29 @@ static void rhs_point(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t
         }
         if (pde == ORC_ADVDIFF) {
             K[0] = -pr[0] * D1[0] + pr[1] * D2[0];
+        } else if (pde == ORC_RNS_CHAIN) {
+            /* Eq. ge with every derivative of a product expanded by the chain
+             * rule (Sec. 4), so that only the primitives rho, u, p, rho E, Y
+             * and T are differentiated (and extrapolated at buffer points);
+             * the factors multiplying the derivatives are the point's own
+             * current values.  tau = 4/3 mu u_x, (tau u)_x = 4/3 mu (u_x^2 +
+             * u u_xx), q = -lam T_x + q_c J_F, J_F = -rhoD Y_x. */
+            double gam = pr[0], mu = pr[1], Pr = pr[2], Le = pr[3], A = pr[4], Ea = pr[5], qc = pr[6];
+            double cp = gam / (gam - 1.0);
+            double lam = mu * cp / Pr;
+            double rhoD = lam / (cp * Le);
+            double Q[4], g[MAXD];
+            state_at(c, field(c, level, s), j, Q);
+            derive(c, Q, g);
+            double rho = g[0], u = g[1], p_ = g[2], rE = g[3], Y = g[4], T = g[5];
+            double rho_x = D1[0], u_x = D1[1], p_x = D1[2], rE_x = D1[3], Y_x = D1[4];
+            double u_xx = D2[1], Y_xx = D2[4], T_xx = D2[5];
+            double wdot = A * Q[3] * exp(-Ea / T);
+            K[0] = -(rho_x * u + rho * u_x);
+            K[1] = -(rho_x * u * u + 2.0 * rho * u * u_x) - p_x + (4.0 / 3.0) * mu * u_xx;
+            K[2] = -(u_x * (rE + p_) + u * (rE_x + p_x)) + (4.0 / 3.0) * mu * (u_x * u_x + u * u_xx)
+                   + lam * T_xx + qc * rhoD * Y_xx;
+            K[3] = -(rho_x * u * Y + rho * u_x * Y + rho * u * Y_x) + rhoD * Y_xx - wdot;
         } else {
             double gam = pr[0], mu = pr[1], Pr = pr[2], Le = pr[3], A = pr[4], Ea = pr[5], qc = pr[6];
             double cp = gam / (gam - 1.0);
@@ -529,7 +566,7 @@ orc_ctx* orc_create(const orc_problem* pb, const double* init)
     if (!pb || !init) return NULL;
     if (pb->pe_size <= 0 || pb->n <= 0 || pb->n % pb->pe_size) return NULL;
     if (pb->k_max < 0 || pb->k_max > 15) return NULL;
-    if (pb->pde < 0 || pb->pde > 4) return NULL;
+    if (pb->pde < 0 || pb->pde > 5) return NULL;
     orc_ctx* c = (orc_ctx*)calloc(1, sizeof *c);
     if (!c) return NULL;
     c->pb = *pb;
@@ -546,7 +583,8 @@ orc_ctx* orc_create(const orc_problem* pb, const double* init)
         c->H = pb->order / 2;
         c->q = pb->order / 2;
     }
-    c->nder = (pb->pde == ORC_ADVDIFF) ? 1 : ((pb->pde == ORC_ADV_WENO || pb->pde == ORC_BURGERS) ? 2 : 8);
+    c->nder = (pb->pde == ORC_ADVDIFF) ? 1
+              : ((pb->pde == ORC_ADV_WENO || pb->pde == ORC_BURGERS) ? 2 : (pb->pde == ORC_RNS_CHAIN ? 6 : 8));
     if (pb->pe_size < 2 * c->H) {
         free(c);
         return NULL;

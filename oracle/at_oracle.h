@@ -20,13 +20,13 @@
 extern "C" {
 #endif
 
-enum { ORC_ADVDIFF = 0, ORC_RNS = 1, ORC_EULER = 2, ORC_ADV_WENO = 3, ORC_BURGERS = 4 };
+enum { ORC_ADVDIFF = 0, ORC_RNS = 1, ORC_EULER = 2, ORC_ADV_WENO = 3, ORC_BURGERS = 4, ORC_RNS_CHAIN = 5 };
 enum { ORC_RK2 = 0, ORC_RK3TVD = 1, ORC_RK4 = 2 };
 enum { ORC_SYNC = 0, ORC_AS = 1, ORC_AT = 2 };
 enum { ORC_UNIFORM = 0, ORC_TABLE = 1, ORC_GEOMETRIC = 2 };
 
 typedef struct {
-    int pde;          /* ORC_ADVDIFF | ORC_RNS | ORC_EULER | ORC_ADV_WENO | ORC_BURGERS */
+    int pde;          /* ORC_ADVDIFF | ORC_RNS | ORC_EULER | ORC_ADV_WENO | ORC_BURGERS | ORC_RNS_CHAIN */
     int order;        /* central order 2|4|6 (ADVDIFF, RNS); ignored for WENO  */
     int rk;           /* ORC_RK2 | ORC_RK3TVD | ORC_RK4                        */
     int64_t n;        /* grid points (periodic), n % pe_size == 0              */

@@ -19,12 +19,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libat_gb300.so")
 
 AT_OK, AT_EINVAL, AT_ENOMEM, AT_ECUDA, AT_EUNSTABLE, AT_ETIMEOUT, AT_ESTATE = 0, -1, -2, -3, -4, -5, -6
-PDE = {"advdiff": 0, "rns": 1, "euler": 2, "adv_weno": 3, "burgers": 4}
+PDE = {"advdiff": 0, "rns": 1, "euler": 2, "adv_weno": 3, "burgers": 4, "rns_chain": 5}
 RK = {"rk2": 0, "rk3tvd": 1, "rk4": 2}
 MODE = {"sync": 0, "as": 1, "at": 2}
 DIST = {"uniform": 0, "table": 1, "geometric": 2}
 READ_STATE, READ_DELAYS, READ_RING, READ_STATS = 0, 1, 2, 3
-NVAR = {"advdiff": 1, "adv_weno": 1, "burgers": 1, "rns": 4, "euler": 4}
+NVAR = {"advdiff": 1, "adv_weno": 1, "burgers": 1, "rns": 4, "euler": 4, "rns_chain": 4}
 STAGES = {"rk2": 2, "rk3tvd": 3, "rk4": 4}
 
 # every symbol include/at.h declares

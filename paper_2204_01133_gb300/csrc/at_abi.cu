@@ -39,6 +39,9 @@ cudaError_t atk_launch_batch_status(const atk::StageArgs* tab, const int* slots,
 // spare ring levels beyond k_max + q + 1: how far a PE of the persistent
 // path may run ahead of a neighbour before it must wait to reuse a slot
 static const int kRingSlack = 2;
+// Levels stay below 2^31 so that the kernels take ring slots with 32-bit
+// arithmetic (a solve of more steps is refused).
+static const int64_t kMaxLevel = ((int64_t)1 << 31) - 2;
 
 namespace {
 
@@ -69,7 +72,7 @@ struct Layout {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int nvar_of(int pde) { return (pde == AT_RNS || pde == AT_EULER) ? 4 : 1; }
+int nvar_of(int pde) { return (pde == AT_RNS || pde == AT_EULER || pde == AT_RNS_CHAIN) ? 4 : 1; }
 bool is_weno(int pde) { return pde == AT_EULER || pde == AT_ADV_WENO || pde == AT_BURGERS; }
 int stages_of(int rk) { return rk == AT_RK2 ? 2 : (rk == AT_RK3TVD ? 3 : 4); }
 
@@ -88,7 +91,7 @@ int window_of(int B, int H)
 int check_problem(const at_problem* pb)
 {
     if (!pb) return fail(AT_EINVAL, "problem is NULL");
-    if (pb->pde < 0 || pb->pde > 4) return fail(AT_EINVAL, "unknown pde %d", pb->pde);
+    if (pb->pde < 0 || pb->pde > 5) return fail(AT_EINVAL, "unknown pde %d", pb->pde);
     if (pb->rk < 0 || pb->rk > 2) return fail(AT_EINVAL, "unknown rk %d", pb->rk);
     if (!is_weno(pb->pde) && pb->order != 2 && pb->order != 4 && pb->order != 6)
         return fail(AT_EINVAL, "central order must be 2, 4 or 6 (got %d)", pb->order);
@@ -231,7 +234,15 @@ atk::StageArgs build_args(const at_problem* pb, const at_delays* dl, const Layou
     a.hdt = 0.5 * pb->dt;
     a.dt6 = pb->dt * (1.0 / 6.0);
     thresholds(dl, a.thr);
-    for (int k = 0; k <= dl->k_max; ++k) extrap_weights(L.q, k, a.w[k]);
+    for (int k = 0; k <= dl->k_max; ++k) {
+        extrap_weights(L.q, k, a.w[k]);
+        a.wnz[k] = 1;  // AS and SYNC read the delayed level only
+        if (dl->mode == AT_AT) {
+            a.wnz[k] = 0;
+            for (int l = 0; l <= L.q; ++l)
+                if (a.w[k][l] != 0.0) a.wnz[k] |= (uint8_t)(1u << l);
+        }
+    }
     for (int i = 0; i < 16; ++i) a.prm[i] = pb->prm[i];
     const double dx = pb->dx;
     if (!is_weno(pb->pde)) {
@@ -444,6 +455,9 @@ int at_step(at_ctx* c, int64_t nsteps)
     if (!c) return fail(AT_EINVAL, "context is NULL");
     if (!c->have_problem || !c->have_delays) return fail(AT_ESTATE, "at_set_problem and at_set_delays must come first");
     if (nsteps < 0) return fail(AT_EINVAL, "nsteps must be >= 0");
+    if (nsteps > kMaxLevel - c->level)
+        return fail(AT_EINVAL, "a solve is limited to %lld steps (level %lld, %lld more asked)", (long long)kMaxLevel,
+                    (long long)c->level, (long long)nsteps);
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     const Layout& L = c->L;
@@ -610,7 +624,7 @@ int at_destroy(at_ctx* c)
 // batched solves
 // ---------------------------------------------------------------------------
 namespace {
-const int kVariants = 9;
+const int kVariants = 12;
 
 struct BatchTable {  // carving of the caller's table memory
     size_t off_args, off_lvl, off_left, off_order, off_slots, off_status, off_queue, off_wslot, off_widx, total;
@@ -842,6 +856,7 @@ int at_batch_bind(at_batch* b, int64_t slot, const at_instance* in)
     if (st == AT_OK) st = check_delays(&in->dl);
     if (st != AT_OK) return st;
     if (in->nsteps < 0) return fail(AT_EINVAL, "nsteps must be >= 0");
+    if (in->nsteps > kMaxLevel) return fail(AT_EINVAL, "a solve is limited to %lld steps", (long long)kMaxLevel);
     if (!in->state_dev || !in->workspace_dev || ((uintptr_t)in->state_dev & 15) || ((uintptr_t)in->workspace_dev & 255))
         return fail(AT_EINVAL, "state (16-B aligned) and workspace (256-B aligned) must be device memory");
     const Layout L = layout(&in->pb, &in->dl);

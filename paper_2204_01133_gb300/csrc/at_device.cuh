@@ -15,7 +15,7 @@
 
 namespace atk {
 
-enum { ADVDIFF = 0, RNS = 1, EULER = 2, ADV_WENO = 3, BURGERS = 4 };
+enum { ADVDIFF = 0, RNS = 1, EULER = 2, ADV_WENO = 3, BURGERS = 4, RNS_CHAIN = 5 };
 enum { RK2 = 0, RK3TVD = 1, RK4 = 2 };
 enum { SYNC = 0, AS = 1, AT = 2 };
 
@@ -39,6 +39,7 @@ struct StageArgs {
     double dt, hdt, dt6;                      // dt, dt/2, dt/6 (formed once on the host)
     uint64_t thr[AT_KMAX_LIMIT];              // Philox word-0 thresholds
     double w[AT_KMAX_LIMIT + 1][AT_QMAX + 1]; // extrapolation weights by delay
+    uint8_t wnz[AT_KMAX_LIMIT + 1];           // bit l: level l enters at delay k (weight != 0)
     double c1[2 * AT_HMAX + 1];               // -d1_m / dx  (central)
     double c2[2 * AT_HMAX + 1];               //  d2_m / dx^2 (central)
     double cm[2 * AT_HMAX + 1];               // merged advection-diffusion taps
@@ -149,11 +150,15 @@ __device__ __forceinline__ bool nonfinite(double v)
     return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
 }
 
+// Ring element of (level, stage, PE, side, point h of the edge window,
+// variable v).  Levels read or written are never negative (start-up clamp)
+// and stay below 2^31 (the library refuses longer runs), so the slot comes
+// from a 32-bit remainder: a 64-bit one is a long software sequence that
+// occupies the FP64 pipe.
 __device__ __forceinline__ int64_t ring_index(const StageArgs& a, int64_t level, int stage, int64_t pe, int side,
                                               int h, int v)
 {
-    int64_t r = level % a.R;
-    if (r < 0) r += a.R;
+    const int64_t r = (int64_t)((uint32_t)level % (uint32_t)a.R);
     return ((((r * a.S + stage) * a.P + pe) * 2 + side) * a.H + h) * a.nvar + v;
 }
 
@@ -203,6 +208,27 @@ struct Phys<RNS> {
         const double u = Q[1] * rinv;
         const double p = gm1 * (Q[2] - fma(0.5 * Q[1], u, qc * Q[3]));
         return p * rinv;
+    }
+};
+
+// Reacting Navier-Stokes in chain-rule form (Sec. 4): the product
+// derivatives are expanded, so only the primitives g = [rho, u, p, rho E, Y,
+// T] are differentiated (and extrapolated at buffer points).
+template <>
+struct Phys<RNS_CHAIN> {
+    static constexpr int NV = 4, ND = 6;
+    __device__ static void derive(const StageArgs& a, const double* Q, double* g)
+    {
+        const double gm1 = a.prm[0] - 1.0, qc = a.prm[6];
+        const double rinv = at_rcp(Q[0]);
+        const double u = Q[1] * rinv;
+        const double p = gm1 * (Q[2] - fma(0.5 * Q[1], u, qc * Q[3]));
+        g[0] = Q[0];
+        g[1] = u;
+        g[2] = p;
+        g[3] = Q[2];
+        g[4] = Q[3] * rinv;
+        g[5] = p * rinv;
     }
 };
 

@@ -176,9 +176,9 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
     for (int64_t n = level0; n < level0 + nsteps; ++n) {
         for (int s = 0; s < S; ++s) {
             const bool last = (s == S - 1);
-            const int64_t I = n * S + s + 1;  // the stage argument this stage produces
-            const int64_t Ln = I / S;
-            const int sn = (int)(I - Ln * S);
+            // the stage argument this stage produces: (level Ln, stage sn) = index n S + s + 1
+            const int64_t Ln = last ? n + 1 : n;
+            const int sn = last ? 0 : s + 1;
             // (A)
             if (warp == hwarp) {
                 if (lane < 2) {
@@ -200,10 +200,9 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                         const int side = hp < H ? 0 : 1;
                         const int h = side == 0 ? hp : hp - H;
                         const int k = s_k[side];
-                        const double wl = (a.mode == AT) ? a.w[k][l] : 1.0;
                         double g[ND];
                         double Q[NV];
-                        if (wl != 0.0) {
+                        if ((a.wnz[k] >> l) & 1) {
                             const int64_t base = ring_index(a, n - k - l, s, nbr[side], 1 - side, h, 0);
 #pragma unroll
                             for (int v = 0; v < NV; ++v) Q[v] = __ldcg(a.ring + base + v);
@@ -270,7 +269,7 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                 }
             }
             __syncthreads();
-            if (threadIdx.x == 0 && pe != a.withhold_pe) store_release(a.done + pe, I);
+            if (threadIdx.x == 0 && pe != a.withhold_pe) store_release(a.done + pe, n * S + s + 1);
         }
     }
 out:

@@ -83,8 +83,7 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
             const int64_t nbr = side == 0 ? (pe == 0 ? a.P - 1 : pe - 1) : (pe == a.P - 1 ? 0 : pe + 1);
             const int k = keff_at(a, cx.level, cx.stage, pe, side);
             if (h == 0 && l == 0) a.dlog[((int64_t)cx.stage * a.P + pe) * 2 + side] = (uint8_t)k;
-            const double wl = (a.mode == AT) ? a.w[k][l] : 1.0;
-            if (wl != 0.0) {  // a level with weight 0 is not part of the scheme (and may not exist yet)
+            if ((a.wnz[k] >> l) & 1) {  // a level with weight 0 is not part of the scheme (and may not exist yet)
                 const int64_t base = ring_index(a, cx.level - k - l, cx.stage, nbr, 1 - side, h, 0);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) Q[v] = a.ring[base + v];
@@ -183,6 +182,51 @@ __device__ __forceinline__ void rk_update(const StageArgs& a, const Cx& cx, int 
 // ---------------------------------------------------------------------------
 // central stencils: advection-diffusion and reacting Navier-Stokes
 // ---------------------------------------------------------------------------
+// Reacting N-S in chain-rule form (Sec. 4) at own point j (window column c):
+// with m_f = sum_o c1_o f_{j+o} = -f_x and f_xx from the c2 taps,
+//   K_rho  = -(rho_x u + rho u_x)
+//   K_rhou = -(rho_x u^2 + 2 rho u u_x) - p_x + 4/3 mu u_xx
+//   K_rhoE = -(u_x (rho E + p) + u ((rho E)_x + p_x)) + 4/3 mu (u_x^2 + u u_xx)
+//            + lam T_xx + q_c rhoD Y_xx
+//   K_rhoY = -(rho_x u Y + rho u_x Y + rho u Y_x) + rhoD Y_xx - A rho Y exp(-Ea/T)
+// (tau = 4/3 mu u_x, q = -lam T_x + q_c J_F, J_F = -rhoD Y_x), the factors
+// being the point's own current values; then the four RK updates.
+template <int H>
+__device__ __forceinline__ void chain_point(const StageArgs& a, const Cx& cx, const double* G, int W2, int64_t pe,
+                                            int jpe, int64_t j, int c)
+{
+    double m[5];  // -d/dx of rho, u, p, rho E, Y
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        double t = 0.0;
+#pragma unroll
+        for (int o = -H; o <= H; ++o)
+            if (o != 0) t = fma(a.c1[o + H], G[q * W2 + c + o], t);
+        m[q] = t;
+    }
+    double uxx = 0.0, Yxx = 0.0, Txx = 0.0;
+#pragma unroll
+    for (int o = -H; o <= H; ++o) {
+        uxx = fma(a.c2[o + H], G[1 * W2 + c + o], uxx);
+        Yxx = fma(a.c2[o + H], G[4 * W2 + c + o], Yxx);
+        Txx = fma(a.c2[o + H], G[5 * W2 + c + o], Txx);
+    }
+    const double rho = G[c], u = G[W2 + c], p = G[2 * W2 + c], rE = G[3 * W2 + c], Y = G[4 * W2 + c];
+    const double T = G[5 * W2 + c];
+    const double ru = rho * u;
+    double K[4];
+    K[0] = fma(m[0], u, rho * m[1]);
+    K[1] = fma(m[0] * u, u, fma(2.0 * ru, m[1], fma(a.k0, uxx, m[2])));
+    K[2] = fma(m[1], rE + p, fma(u, m[3] + m[2], fma(a.k0, fma(m[1], m[1], u * uxx), fma(a.k2, Txx, a.prm[6] * a.k3 * Yxx))));
+    const double x3 = cx.X[3 * a.N + j];
+    K[3] = fma(m[0] * u, Y, fma(rho * m[1], Y, fma(ru, m[4], fma(a.k3, Yxx, -a.prm[4] * x3 * at_exp(-a.prm[5] * at_rcp(T))))));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const double x = v == 3 ? x3 : cx.X[v * a.N + j];
+        rk_update(a, cx, v, j, jpe, pe, K[v], x, rk_load(a, cx, v * a.N + j));
+    }
+}
+
 template <int PDE, int H>
 __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx, int64_t win, double* sm, int lt,
                                                int gs)
@@ -192,9 +236,16 @@ __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx,
     const int W2 = a.Tw + 2 * H;
     double* G = sm;
     double* HS = G + P::ND * W2;
-    const int64_t pe = win / a.wpp;
+    const int64_t pe = a.wpp == 1 ? win : win / a.wpp;  // a 64-bit division only where PEs hold several windows
     const int chunk = (int)(win - pe * a.wpp);
     const int64_t t0 = pe * a.B + (int64_t)chunk * a.Tw;
+    if constexpr (PDE == RNS_CHAIN) {  // one item per point: its derivatives feed all four equations
+        fill_window<PDE, false>(a, cx, G, nullptr, HS, pe, chunk, t0, W2, lt, gs);
+        __syncthreads();
+        for (int jl = lt; jl < a.Tw; jl += gs)
+            chain_point<H>(a, cx, G, W2, pe, chunk * a.Tw + jl, t0 + jl, jl + H);
+        return;
+    }
     const int items = NV * a.Tw;
     // advection-diffusion (few FP64 operations per byte): the pointwise
     // operands of the thread's first update item are loaded before the fill,
@@ -296,7 +347,7 @@ __global__ void __launch_bounds__(256, PPL <= 2 ? 6 : (PPL == 4 ? 4 : 3)) stage_
 #pragma unroll
         for (int l = 0; l <= AT_QMAX; ++l) {
             v[l] = 0.0;  // a level with weight 0 is not part of the scheme (and may not exist yet)
-            if (l < nw && ((a.mode == AT) ? a.w[k][l] : 1.0) != 0.0)
+            if (l < nw && ((a.wnz[k] >> l) & 1))
                 v[l] = a.ring[ring_index(a, cx.level - k - l, cx.stage, nbr, 1 - side, h, 0)];
         }
         double acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * v[0];
@@ -370,7 +421,7 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
     double* LAM = SP + W2;
     double* REC = LAM + E;
     double* HS = REC + NV * 2 * E;
-    const int64_t pe = win / a.wpp;
+    const int64_t pe = a.wpp == 1 ? win : win / a.wpp;  // a 64-bit division only where PEs hold several windows
     const int chunk = (int)(win - pe * a.wpp);
     const int64_t t0 = pe * a.B + (int64_t)chunk * Tw;
     fill_window<PDE, true>(a, cx, G, SP, HS, pe, chunk, t0, W2, threadIdx.x, blockDim.x);
@@ -544,6 +595,7 @@ size_t atk_stage_smem_bytes(int pde, int Tw, int H)
     switch (pde) {
     case atk::ADVDIFF: return sizeof(double) * (W2 + hs * 1);
     case atk::RNS: return sizeof(double) * (8 * W2 + hs * 8);
+    case atk::RNS_CHAIN: return sizeof(double) * (6 * W2 + hs * 6);
     case atk::EULER: return sizeof(double) * (9 * W2 + E + 8 * E + hs * 8);
     default: return sizeof(double) * (3 * W2 + E + 2 * E + hs * 2);
     }
@@ -566,7 +618,7 @@ cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaSt
     // central stencils on small windows: several windows per CTA (whole PEs
     // only, dividing the window count), so a CTA carries up to 256 threads
     int m = 1;
-    if ((pde == atk::ADVDIFF || pde == atk::RNS) && a.wpp == 1) {
+    if ((pde == atk::ADVDIFF || pde == atk::RNS || pde == atk::RNS_CHAIN) && a.wpp == 1) {
         for (int c = 4; c >= 2; c /= 2)
             if (c * b1 <= 256 && windows % c == 0) {
                 m = c;
@@ -606,6 +658,11 @@ cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaSt
         if (order == 2) atk::stage_central<atk::RNS, 1><<<grid, block, smem, st>>>(b);
         else if (order == 4) atk::stage_central<atk::RNS, 2><<<grid, block, smem, st>>>(b);
         else atk::stage_central<atk::RNS, 3><<<grid, block, smem, st>>>(b);
+        break;
+    case atk::RNS_CHAIN:
+        if (order == 2) atk::stage_central<atk::RNS_CHAIN, 1><<<grid, block, smem, st>>>(b);
+        else if (order == 4) atk::stage_central<atk::RNS_CHAIN, 2><<<grid, block, smem, st>>>(b);
+        else atk::stage_central<atk::RNS_CHAIN, 3><<<grid, block, smem, st>>>(b);
         break;
     case atk::EULER: atk::stage_weno<atk::EULER><<<grid, block, smem, st>>>(b); break;
     case atk::BURGERS: atk::stage_weno<atk::BURGERS><<<grid, block, smem, st>>>(b); break;
@@ -658,6 +715,7 @@ int atk_batch_variant(int pde, int order)
     if (pde == atk::ADVDIFF) return order / 2 - 1;
     if (pde == atk::RNS) return 3 + order / 2 - 1;
     if (pde == atk::BURGERS) return 8;
+    if (pde == atk::RNS_CHAIN) return 9 + order / 2 - 1;
     return pde == atk::EULER ? 6 : 7;
 }
 
@@ -672,6 +730,9 @@ static void* batch_fn(int variant)
     case 5: return (void*)atk::batch_run<atk::RNS, 3, false>;
     case 6: return (void*)atk::batch_run<atk::EULER, 3, true>;
     case 8: return (void*)atk::batch_run<atk::BURGERS, 3, true>;
+    case 9: return (void*)atk::batch_run<atk::RNS_CHAIN, 1, false>;
+    case 10: return (void*)atk::batch_run<atk::RNS_CHAIN, 2, false>;
+    case 11: return (void*)atk::batch_run<atk::RNS_CHAIN, 3, false>;
     default: return (void*)atk::batch_run<atk::ADV_WENO, 3, true>;
     }
 }
@@ -698,6 +759,9 @@ static void* batch_stage_fn(int variant)
     case 5: return (void*)atk::batch_stage<atk::RNS, 3, false>;
     case 6: return (void*)atk::batch_stage<atk::EULER, 3, true>;
     case 8: return (void*)atk::batch_stage<atk::BURGERS, 3, true>;
+    case 9: return (void*)atk::batch_stage<atk::RNS_CHAIN, 1, false>;
+    case 10: return (void*)atk::batch_stage<atk::RNS_CHAIN, 2, false>;
+    case 11: return (void*)atk::batch_stage<atk::RNS_CHAIN, 3, false>;
     default: return (void*)atk::batch_stage<atk::ADV_WENO, 3, true>;
     }
 }

@@ -147,10 +147,13 @@ def rns_conserved(rho, u, T, Y, prm) -> np.ndarray:
 
 
 def rns(case="flame", n=16384, pe_size=64, order=6, mode="at", k_max=4, dist="uniform", prob=(),
-        seed=0, per_stage=1, dt=RNS_DT, T_init=3.0, Y_init=1.0, prm=None, T_unburnt=1.0, instance=0):
+        seed=0, per_stage=1, dt=RNS_DT, T_init=3.0, Y_init=1.0, prm=None, T_unburnt=1.0, instance=0,
+        form="flux"):
     """Premixed flame from a periodic double-tanh burnt region in unburnt gas
     at ``T_unburnt``, or homogeneous autoignition at ``T_init`` with a 1 %
-    Gaussian temperature bump."""
+    Gaussian temperature bump.  ``form`` = "flux" differentiates the flux
+    vector (conservative); "chain" expands the product derivatives by the
+    chain rule and differentiates the primitives (Sec. 4)."""
     prm = list(prm) if prm is not None else rns_prm()
     dx = 1.0
     x = np.arange(n, dtype=np.float64) * dx
@@ -172,7 +175,10 @@ def rns(case="flame", n=16384, pe_size=64, order=6, mode="at", k_max=4, dist="un
     rho = p / T
     u = np.zeros(n)
     init = rns_conserved(rho, u, T, Y, prm)
-    pb = base_problem(pde="rns", order=order, rk="rk4", n=n, pe_size=pe_size, dx=dx, dt=dt,
+    if form not in ("flux", "chain"):
+        raise ValueError(form)
+    pb = base_problem(pde="rns" if form == "flux" else "rns_chain", order=order, rk="rk4", n=n,
+                      pe_size=pe_size, dx=dx, dt=dt,
                       prm=prm, mode=mode, k_max=k_max, dist=dist, prob=list(prob), seed=seed,
                       per_stage=per_stage, instance=instance)
     return pb, init

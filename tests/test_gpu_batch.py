@@ -36,6 +36,9 @@ def mixed_instances():
     out.append((dict(pb, instance=81), init, 30))
     pb, init = W.burgers(n=768, pe_size=48, mode="at", k_max=2, seed=7, dt_coef=1.0)
     out.append((dict(pb, instance=82), init, 35))
+    pb, init = W.rns(case="ignition", n=1024, pe_size=32, order=6, mode="at", k_max=3, seed=8, dt=0.003,
+                     instance=83, form="chain")
+    out.append((pb, init, 28))
     return out
 
 

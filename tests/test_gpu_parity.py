@@ -124,6 +124,16 @@ def test_rns_literal_size(case, path):
     parity(pb, u0, 150, path=path)
 
 
+@pytest.mark.parametrize("case,mode,n,B,order", [
+    ("flame", "at", 16384, 64, 6), ("ignition", "at", 16384, 64, 6), ("flame", "sync", 2048, 64, 6),
+    ("flame", "as", 2048, 32, 4), ("ignition", "at", 1536, 48, 2), ("flame", "at", 2048, 32, 4)])
+def test_rns_chain_rule_form(case, mode, n, B, order):
+    """The chain-rule form of Sec. 4 (primitives differentiated and
+    extrapolated), per-stage path, against the oracle's chain-rule RHS."""
+    pb, u0 = W.rns(case=case, n=n, pe_size=B, order=order, mode=mode, k_max=4, seed=3, dt=0.003, form="chain")
+    parity(pb, u0, 150)
+
+
 @pytest.mark.parametrize("mode", ["sync", "as"])
 def test_rns_modes(mode):
     pb, u0 = W.rns(case="flame", n=2048, pe_size=64, mode=mode, k_max=4, seed=2, dt=0.003)

@@ -674,6 +674,60 @@ def test_rns_homogeneous_ignition_matches_ode():
 
 
 # --------------------------------------------------------------------------
+# Reacting N-S right-hand side against the PDE itself (Eq. ge with the
+# constitutive laws of Sec. 4), in both forms: the flux form differentiates
+# the flux vector, the chain-rule form the primitives.  Exact derivatives of
+# smooth periodic fields come from sympy; a dropped term, a wrong sign or a
+# wrong coefficient leaves an O(1) error instead of the stencil's O(dx^6).
+# --------------------------------------------------------------------------
+def _rns_exact(n, L, prm):
+    sp = pytest.importorskip("sympy")
+    gam, mu, Pr, Le, A, Ea, qc = prm
+    cp = gam / (gam - 1.0)
+    lam = mu * cp / Pr
+    rhoD = lam / (cp * Le)
+    x = sp.symbols("x")
+    kap = 2 * sp.pi / L
+    rho = 1 + sp.Rational(1, 5) * sp.sin(kap * x)
+    u = sp.Rational(3, 10) * sp.cos(kap * x)
+    T = 2 + sp.Rational(1, 2) * sp.sin(2 * kap * x + sp.Rational(3, 10))
+    Y = sp.Rational(1, 2) + sp.Rational(1, 5) * sp.cos(kap * x + 1)
+    p = rho * T
+    rE = p / (gam - 1) + rho * u * u / 2 + qc * rho * Y
+    d = lambda f: sp.diff(f, x)
+    tau = sp.Rational(4, 3) * mu * d(u)
+    q = -lam * d(T) - qc * rhoD * d(Y)          # -lam T_x + q_c J_F, J_F = -rhoD Y_x
+    K = [-d(rho * u),
+         -d(rho * u * u + p) + d(tau),
+         -d(u * (rE + p)) + d(tau * u) - d(q),
+         -d(rho * u * Y) + d(rhoD * d(Y)) - A * rho * Y * sp.exp(-Ea / T)]
+    xs = np.arange(n) * (L / n)
+    ev = lambda f: np.asarray(sp.lambdify(x, f, "numpy")(xs), dtype=np.float64) * np.ones(n)
+    exact = np.stack([ev(k) for k in K])
+    state = np.stack([ev(rho), ev(rho * u), ev(rE), ev(rho * Y)])
+    return exact, state
+
+
+@pytest.mark.parametrize("form", ["flux", "chain"])
+@pytest.mark.parametrize("order", [4, 6])
+def test_rns_rhs_converges_to_the_pde(form, order):
+    prm = W.rns_prm()
+    L = 40.0
+    errs = []
+    for n in (64, 128, 256):
+        exact, state = _rns_exact(n, L, prm)
+        pb = W.base_problem(pde="rns" if form == "flux" else "rns_chain", order=order, rk="rk4", n=n,
+                            pe_size=n // 4, dx=L / n, dt=1e-3, prm=prm, mode="sync", k_max=4)
+        o = oracle.Oracle(pb, state)
+        o.set_history(0, 0, state)
+        K = o.rhs(0, 0)
+        errs.append(np.abs(K - exact).max() / np.abs(exact).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 1e-5
+    assert abs(rates[-1] - order) < 0.5, (errs, rates)
+
+
+# --------------------------------------------------------------------------
 # Conservation (flux form, periodic): exact under SYNC
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("case", ["rns", "euler"])

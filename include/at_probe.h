@@ -29,6 +29,14 @@ int at_probe_fp64_fma(int device, void* stream, int iters, int reps, double* tfl
  * warps per SM each running one dependent chain of `iters` steps. */
 int at_probe_fp64_latency(int device, int warps_per_sm, int iters, double* cycles_per_fma);
 
+/* Which pipe an integer operation uses: best-of-`reps` time in ms of a grid
+ * (4 CTAs of 256 threads per SM) whose threads run 8 independent chains of
+ * `kind` (0 FP64 fma, 1 64-bit integer multiply-add, 2 64-bit integer add,
+ * 3 32-bit integer multiply-add) of `iters` steps, beside 8 FP64 fma chains
+ * when with_fp64 != 0.  Sharing the FP64 pipe shows as time(kind, 1) close
+ * to time(0, 0) + time(kind, 0). */
+int at_probe_pipe_mix(int device, int kind, int with_fp64, int iters, int reps, double* ms_best);
+
 /* y[i] = f(x[i]) for device arrays x, y of n doubles (caller-owned device
  * memory, current device): which = 0 the stage kernels' table-driven
  * exponential, 1 CUDA's exp, 2 the stage kernels' Newton reciprocal, 3 IEEE

@@ -43,6 +43,42 @@ __global__ void dfma_chain1(double* out, int iters, double a, double b)
 
 } // namespace
 
+// pipe-sharing probe: every thread runs 8 independent chains of `kind`
+// (0: FP64 fma; 1: 64-bit integer multiply-add; 2: 64-bit integer add;
+// 3: 32-bit integer multiply-add) and, when with_fp64, also the 8 FP64 fma
+// chains of kind 0.  If a kind shares the FP64 pipe, running it beside the
+// fma chains costs about the sum of the two times, otherwise about the max.
+__global__ void __launch_bounds__(256) mixed_chains(double* out, uint64_t* iout, int iters, double a, double b,
+                                                    uint64_t m, uint64_t c, int kind, int with_fp64)
+{
+    double x0 = threadIdx.x * 1e-3, x1 = x0 + 0.1, x2 = x0 + 0.2, x3 = x0 + 0.3;
+    double x4 = x0 + 0.4, x5 = x0 + 0.5, x6 = x0 + 0.6, x7 = x0 + 0.7;
+    uint64_t i0 = threadIdx.x + 1, i1 = i0 + 3, i2 = i0 + 5, i3 = i0 + 7, i4 = i0 + 11, i5 = i0 + 13, i6 = i0 + 17,
+             i7 = i0 + 19;
+    uint32_t j0 = (uint32_t)i0, j1 = j0 + 3, j2 = j0 + 5, j3 = j0 + 7, j4 = j0 + 11, j5 = j0 + 13, j6 = j0 + 17,
+             j7 = j0 + 19;
+    const bool f = with_fp64 || kind == 0;
+    for (int it = 0; it < iters; ++it) {
+        if (f) {
+            x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+            x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+        }
+        if (kind == 1) {
+            i0 = i0 * m + c; i1 = i1 * m + c; i2 = i2 * m + c; i3 = i3 * m + c;
+            i4 = i4 * m + c; i5 = i5 * m + c; i6 = i6 * m + c; i7 = i7 * m + c;
+        } else if (kind == 2) {
+            i0 += c ^ i7; i1 += c ^ i0; i2 += c ^ i1; i3 += c ^ i2;
+            i4 += c ^ i3; i5 += c ^ i4; i6 += c ^ i5; i7 += c ^ i6;
+        } else if (kind == 3) {
+            const uint32_t mm = (uint32_t)m, cc = (uint32_t)c;
+            j0 = j0 * mm + cc; j1 = j1 * mm + cc; j2 = j2 * mm + cc; j3 = j3 * mm + cc;
+            j4 = j4 * mm + cc; j5 = j5 * mm + cc; j6 = j6 * mm + cc; j7 = j7 * mm + cc;
+        }
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+    iout[blockIdx.x * blockDim.x + threadIdx.x] = (i0 ^ i1 ^ i2 ^ i3 ^ i4 ^ i5 ^ i6 ^ i7) + (j0 ^ j1 ^ j2 ^ j3 ^ j4 ^ j5 ^ j6 ^ j7);
+}
+
 // latency probe: `warps` warps per SM, each one dependent fma chain;
 // returns the average SM cycles between two dependent fmas of one warp
 extern "C" int at_probe_fp64_latency(int device, int warps_per_sm, int iters, double* cycles_per_fma)
@@ -132,4 +168,45 @@ extern "C" int at_probe_fn(const double* x, double* y, int64_t n, int which)
     fn_eval<<<blocks, 256>>>(x, y, n, which);
     if (cudaGetLastError() != cudaSuccess) return -3;
     return cudaDeviceSynchronize() != cudaSuccess ? -3 : 0;
+}
+
+// Best-of-`reps` time (ms) of mixed_chains(kind, with_fp64) on a grid of
+// 4 CTAs of 256 threads per SM; see mixed_chains for what the times show.
+extern "C" int at_probe_pipe_mix(int device, int kind, int with_fp64, int iters, int reps, double* ms_best)
+{
+    if (kind < 0 || kind > 3 || iters < 1 || reps < 1) return -1;
+    if (cudaSetDevice(device) != cudaSuccess) return -3;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int blocks = sms * 4, threads = 256;
+    double* out = nullptr;
+    uint64_t* iout = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) return -2;
+    if (cudaMalloc(&iout, sizeof(uint64_t) * blocks * threads) != cudaSuccess) {
+        cudaFree(out);
+        return -2;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    mixed_chains<<<blocks, threads>>>(out, iout, iters / 10 + 1, 0.999999, 1e-7, 0x9E3779B97F4A7C15ull, 12345, kind,
+                                      with_fp64);
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(e0);
+        mixed_chains<<<blocks, threads>>>(out, iout, iters, 0.999999, 1e-7, 0x9E3779B97F4A7C15ull, 12345, kind,
+                                          with_fp64);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t < best) best = t;
+    }
+    const int err = cudaGetLastError() != cudaSuccess ? -3 : 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaFree(iout);
+    *ms_best = best;
+    return err;
 }

@@ -46,7 +46,7 @@ def test_probe_library_exports_its_declared_symbols(L):
     from paper_2204_01133_gb300 import build
     src = open(os.path.join(ROOT, "include", "at_probe.h")).read()
     names = sorted(set(re.findall(r"^int (at_probe_[a-z0-9_]+)\s*\(", src, flags=re.M)))
-    assert len(names) == 4
+    assert len(names) == 5
     out = subprocess.run(["nm", "-D", "--defined-only", build.PROBE], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\bT (at_probe_[a-z0-9_]+)$", out, flags=re.M))
     assert exported == set(names)

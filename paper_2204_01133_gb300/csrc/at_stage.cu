@@ -115,53 +115,63 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
 // ---------------------------------------------------------------------------
 // 3. RK update of this stage, ring push, non-finite check
 // ---------------------------------------------------------------------------
+// The RK scheme and stage of a launch as one kind.  Kernels that take it as
+// a template argument get straight-line update code; with RKS_ANY it is read
+// at run time (the compiler may then predicate the alternatives, and
+// predicated-off FP64 instructions still take FP64 issue slots).
+enum { RKS_ANY = -1, RKS_RK4_0, RKS_RK4_MID, RKS_RK4_LAST, RKS_RK3_0, RKS_RK3_1, RKS_RK3_2, RKS_RK2_0, RKS_RK2_1 };
+
+__host__ __device__ __forceinline__ int rk_stage_kind(int rk, int stage)
+{
+    if (rk == RK4) return stage == 0 ? RKS_RK4_0 : (stage < 3 ? RKS_RK4_MID : RKS_RK4_LAST);
+    if (rk == RK3TVD) return RKS_RK3_0 + stage;
+    return stage == 0 ? RKS_RK2_0 : RKS_RK2_1;
+}
+
 // pointwise operands of one update besides K and the stage argument: u^n and
 // the accumulator, loaded only where the scheme reads them
 struct RkIn {
     double un, ac;
 };
 
+template <int RKS = RKS_ANY>
 __device__ __forceinline__ RkIn rk_load(const StageArgs& a, const Cx& cx, int64_t idx)
 {
+    const int k = RKS >= 0 ? RKS : rk_stage_kind(a.rk, cx.stage);
     RkIn r{0.0, 0.0};
-    if (!(a.rk == RK3TVD && cx.stage == 0)) r.un = cx.u[idx];
-    if (a.rk != RK3TVD && cx.stage > 0) r.ac = a.acc[idx];
+    if (k != RKS_RK3_0) r.un = cx.u[idx];
+    if (k == RKS_RK4_MID || k == RKS_RK4_LAST || k == RKS_RK2_1) r.ac = a.acc[idx];
     return r;
 }
 
+template <int RKS = RKS_ANY>
 __device__ __forceinline__ void rk_update(const StageArgs& a, const Cx& cx, int v, int64_t j, int jpe, int64_t pe,
                                           double K, double x, RkIn in)
 {
+    const int k = RKS >= 0 ? RKS : rk_stage_kind(a.rk, cx.stage);
     const int64_t idx = v * a.N + j;
     const double dt = a.dt;
     const double un = in.un;
     double y;
-    if (a.rk == RK4) {
-        if (cx.stage == 0) {
-            a.acc[idx] = K;
-            y = fma(a.hdt, K, un);
-        } else if (cx.stage < 3) {
-            a.acc[idx] = fma(2.0, K, in.ac);
-            y = fma(cx.stage == 1 ? a.hdt : dt, K, un);
-        } else {
-            y = fma(a.dt6, in.ac + K, un);
-        }
-    } else if (a.rk == RK3TVD) {
-        const double xs = fma(dt, K, x);
-        if (cx.stage == 0) {
-            y = xs;
-        } else if (cx.stage == 1) {
-            y = fma(0.75, un, 0.25 * xs);
-        } else {
-            y = fma(1.0 / 3.0, un, (2.0 / 3.0) * xs);
-        }
-    } else {  // RK2 (Heun)
-        if (cx.stage == 0) {
-            a.acc[idx] = K;
-            y = fma(dt, K, un);
-        } else {
-            y = fma(a.hdt, in.ac + K, un);
-        }
+    if (k == RKS_RK4_0) {
+        a.acc[idx] = K;
+        y = fma(a.hdt, K, un);
+    } else if (k == RKS_RK4_MID) {
+        a.acc[idx] = fma(2.0, K, in.ac);
+        y = fma(cx.stage == 1 ? a.hdt : dt, K, un);
+    } else if (k == RKS_RK4_LAST) {
+        y = fma(a.dt6, in.ac + K, un);
+    } else if (k == RKS_RK3_0) {
+        y = fma(dt, K, x);
+    } else if (k == RKS_RK3_1) {
+        y = fma(0.75, un, 0.25 * fma(dt, K, x));
+    } else if (k == RKS_RK3_2) {
+        y = fma(1.0 / 3.0, un, (2.0 / 3.0) * fma(dt, K, x));
+    } else if (k == RKS_RK2_0) {
+        a.acc[idx] = K;
+        y = fma(dt, K, un);
+    } else {  // RK2 (Heun), second stage
+        y = fma(a.hdt, in.ac + K, un);
     }
     cx.Y[idx] = y;
     if (nonfinite(y)) atomicOr(a.status, 1);
@@ -317,7 +327,7 @@ __global__ void __launch_bounds__(256, PDE == ADVDIFF ? 6 : 5) stage_central(con
 // warp's slice of shared memory, and the warp synchronises with __syncwarp
 // only.  The arithmetic, and its order, is that of central_window<ADVDIFF, H>.
 // ---------------------------------------------------------------------------
-template <int H, int PPL>
+template <int H, int PPL, int RKS>
 __global__ void __launch_bounds__(256, PPL <= 2 ? 6 : (PPL == 4 ? 4 : 3)) stage_advdiff_warp(const StageArgs a)
 {
     extern __shared__ double sm[];
@@ -334,7 +344,7 @@ __global__ void __launch_bounds__(256, PPL <= 2 ? 6 : (PPL == 4 ? 4 : 3)) stage_
 #pragma unroll
     for (int i = 0; i < PPL; ++i) {
         x[i] = cx.X[base + lane + 32 * i];
-        in[i] = rk_load(a, cx, base + lane + 32 * i);
+        in[i] = rk_load<RKS>(a, cx, base + lane + 32 * i);
     }
     if (lane < 2 * H) {  // one buffer point: delay draw, delayed ring levels, extrapolation
         const int side = lane < H ? 0 : 1;
@@ -365,7 +375,7 @@ __global__ void __launch_bounds__(256, PPL <= 2 ? 6 : (PPL == 4 ? 4 : 3)) stage_
         double K = 0.0;
 #pragma unroll
         for (int o = -H; o <= H; ++o) K = fma(a.cm[o + H], W[H + j + o], K);
-        rk_update(a, cx, 0, base + j, j, pe, K, x[i], in[i]);
+        rk_update<RKS>(a, cx, 0, base + j, j, pe, K, x[i], in[i]);
     }
 }
 
@@ -635,16 +645,26 @@ cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaSt
         const unsigned g8 = (unsigned)((a.P + 7) / 8);
         const size_t sw = sizeof(double) * 8 * (size_t)(a.B + 2 * a.H);
         const int ppl = a.B / 32;
-#define AT_WARP_LAUNCH(HH)                                                                              \
+        // classic RK4 (the advection-diffusion configuration) gets one kernel per stage kind
+        const int kind = atk::rk_stage_kind(a.rk, a.stage);
+#define AT_WARP_LAUNCH(HH, PP)                                                                          \
     do {                                                                                                \
-        if (ppl == 1) atk::stage_advdiff_warp<HH, 1><<<g8, 256, sw, st>>>(b);                           \
-        else if (ppl == 2) atk::stage_advdiff_warp<HH, 2><<<g8, 256, sw, st>>>(b);                      \
-        else if (ppl == 4) atk::stage_advdiff_warp<HH, 4><<<g8, 256, sw, st>>>(b);                      \
-        else atk::stage_advdiff_warp<HH, 8><<<g8, 256, sw, st>>>(b);                                    \
+        if (kind == atk::RKS_RK4_0) atk::stage_advdiff_warp<HH, PP, atk::RKS_RK4_0><<<g8, 256, sw, st>>>(b);       \
+        else if (kind == atk::RKS_RK4_MID) atk::stage_advdiff_warp<HH, PP, atk::RKS_RK4_MID><<<g8, 256, sw, st>>>(b); \
+        else if (kind == atk::RKS_RK4_LAST) atk::stage_advdiff_warp<HH, PP, atk::RKS_RK4_LAST><<<g8, 256, sw, st>>>(b); \
+        else atk::stage_advdiff_warp<HH, PP, atk::RKS_ANY><<<g8, 256, sw, st>>>(b);                   \
     } while (0)
-        if (order == 2) AT_WARP_LAUNCH(1);
-        else if (order == 4) AT_WARP_LAUNCH(2);
-        else AT_WARP_LAUNCH(3);
+#define AT_WARP_PPL(HH)                                                                                 \
+    do {                                                                                                \
+        if (ppl == 1) AT_WARP_LAUNCH(HH, 1);                                                            \
+        else if (ppl == 2) AT_WARP_LAUNCH(HH, 2);                                                       \
+        else if (ppl == 4) AT_WARP_LAUNCH(HH, 4);                                                       \
+        else AT_WARP_LAUNCH(HH, 8);                                                                     \
+    } while (0)
+        if (order == 2) AT_WARP_PPL(1);
+        else if (order == 4) AT_WARP_PPL(2);
+        else AT_WARP_PPL(3);
+#undef AT_WARP_PPL
 #undef AT_WARP_LAUNCH
         return cudaGetLastError();
     }

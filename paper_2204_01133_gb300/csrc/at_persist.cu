@@ -115,8 +115,8 @@ __device__ __forceinline__ double point_update(const StageArgs& a, int s, int v,
 // GB300's FP64 unit spends the same time on a warp instruction whatever the
 // number of active lanes, so the work is laid out in whole, uniform warps
 // with fixed roles; two barriers per stage:
-//   (A) warps of the "derive" role: own-point derived quantities;
-//       warps of the "source" role: exp(-Ea/T) of own points;
+//   (A) warps of the "derive" role: own-point derived quantities and the
+//       Arrhenius factor exp(-Ea/T) from the temperature among them;
 //       the halo warp: delays, the bounded neighbour waits, then the buffer
 //       levels from the ring, weighted and summed per buffer point;
 //   (C) the worker warps: stencil, source and RK update of every (point,
@@ -146,21 +146,17 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
     const int nwork = hwarp * 32;                    // threads of the worker warps
     // warps per role in phase A: enough for one point per lane, at most half the workers
     int bw = (B + 31) / 32;
-    if (PDE == RNS && bw > hwarp / 2) bw = hwarp / 2;
     if (bw > hwarp) bw = hwarp;
     if (bw < 1) bw = 1;
     // Roles of the worker warps in phase A.  Warp w runs on SM sub-partition
-    // w % 4 and the halo warp on hwarp % 4.  With 2 + 2 role warps and the halo
-    // warp on sub-partition 0 (a 64-point reacting PE), the two source warps
-    // (the heaviest) take sub-partitions 1 and 2 and both derive warps take 3;
-    // otherwise the derive warps come first and the source warps next.
-    int derive_rank = -1, source_rank = -1;
-    if (PDE == RNS && bw == 2 && hwarp == 8) {
-        if (warp == 1 || warp == 2) source_rank = warp - 1;
-        if (warp == 3 || warp == 7) derive_rank = warp == 3 ? 0 : 1;
-    } else if (warp < hwarp) {
-        if (warp < bw) derive_rank = warp;
-        else if (PDE == RNS && warp < 2 * bw) source_rank = warp - bw;
+    // w % 4 and the halo warp on hwarp % 4 (sub-partition 0 with 8 workers).
+    // The derive warps also form the Arrhenius factor of their points from
+    // the temperature they just derived; they start at warp 1, so that two of
+    // them (a 64-point PE) take sub-partitions 1 and 2, away from the halo warp.
+    int derive_rank = -1;
+    if (warp < hwarp) {
+        const int r = (warp + hwarp - 1) % hwarp;  // warp 1 -> rank 0, warp 2 -> rank 1, ...
+        if (r < bw) derive_rank = r;
     }
 
     for (int i = threadIdx.x; i < NV * B; i += blockDim.x) {
@@ -233,15 +229,7 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                     P::derive(a, Q, g);
 #pragma unroll
                     for (int d = 0; d < ND; ++d) G[d * W2 + H + it] = g[d];
-                }
-            } else if constexpr (PDE == RNS) {
-                if (source_rank >= 0) {
-                    for (int it = source_rank * 32 + lane; it < B; it += bw * 32) {
-                        double Q[NV];
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) Q[v] = X[v * B + it];
-                        E[it] = at_exp(-a.prm[5] * at_rcp(P::temperature(a, Q)));
-                    }
+                    if constexpr (PDE == RNS) E[it] = at_exp(-a.prm[5] * at_rcp(g[7]));  // g[7] = T
                 }
             }
             __syncthreads();

@@ -201,7 +201,7 @@ __device__ __forceinline__ void rk_update(const StageArgs& a, const Cx& cx, int 
 //   K_rhoY = -(rho_x u Y + rho u_x Y + rho u Y_x) + rhoD Y_xx - A rho Y exp(-Ea/T)
 // (tau = 4/3 mu u_x, q = -lam T_x + q_c J_F, J_F = -rhoD Y_x), the factors
 // being the point's own current values; then the four RK updates.
-template <int H>
+template <int H, int RKS>
 __device__ __forceinline__ void chain_point(const StageArgs& a, const Cx& cx, const double* G, int W2, int64_t pe,
                                             int jpe, int64_t j, int c)
 {
@@ -233,11 +233,11 @@ __device__ __forceinline__ void chain_point(const StageArgs& a, const Cx& cx, co
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const double x = v == 3 ? x3 : cx.X[v * a.N + j];
-        rk_update(a, cx, v, j, jpe, pe, K[v], x, rk_load(a, cx, v * a.N + j));
+        rk_update<RKS>(a, cx, v, j, jpe, pe, K[v], x, rk_load<RKS>(a, cx, v * a.N + j));
     }
 }
 
-template <int PDE, int H>
+template <int PDE, int H, int RKS = RKS_ANY>
 __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx, int64_t win, double* sm, int lt,
                                                int gs)
 {
@@ -253,7 +253,7 @@ __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx,
         fill_window<PDE, false>(a, cx, G, nullptr, HS, pe, chunk, t0, W2, lt, gs);
         __syncthreads();
         for (int jl = lt; jl < a.Tw; jl += gs)
-            chain_point<H>(a, cx, G, W2, pe, chunk * a.Tw + jl, t0 + jl, jl + H);
+            chain_point<H, RKS>(a, cx, G, W2, pe, chunk * a.Tw + jl, t0 + jl, jl + H);
         return;
     }
     const int items = NV * a.Tw;
@@ -267,7 +267,7 @@ __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx,
         const int v = lt / a.Tw;
         const int64_t idx = v * a.N + t0 + (lt - v * a.Tw);
         if constexpr (PDE != ADVDIFF) x0 = cx.X[idx];
-        in0 = rk_load(a, cx, idx);
+        in0 = rk_load<RKS>(a, cx, idx);
     }
     fill_window<PDE, false>(a, cx, G, nullptr, HS, pe, chunk, t0, W2, lt, gs);
     __syncthreads();
@@ -280,7 +280,7 @@ __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx,
         RkIn in = in0;
         if (!kPrefetch || it != lt) {
             if constexpr (PDE != ADVDIFF) x = cx.X[v * a.N + j];
-            in = rk_load(a, cx, v * a.N + j);
+            in = rk_load<RKS>(a, cx, v * a.N + j);
         }
         double K = 0.0;
         if constexpr (PDE == ADVDIFF) {
@@ -299,21 +299,21 @@ __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx,
             }
             if (v == 3) K = fma(-a.prm[4] * x, at_exp(-a.prm[5] * at_rcp(G[7 * W2 + c])), K);
         }
-        rk_update(a, cx, v, j, chunk * a.Tw + jl, pe, K, x, in);
+        rk_update<RKS>(a, cx, v, j, chunk * a.Tw + jl, pe, K, x, in);
     }
 }
 
 // One CTA evaluates a.wpc consecutive windows, one thread group each (a.wpc
 // > 1 only when every window spans a whole PE, so all groups pass the same
 // barriers, and a.wpc divides the window count).
-template <int PDE, int H>
+template <int PDE, int H, int RKS>
 __global__ void __launch_bounds__(256, PDE == ADVDIFF ? 6 : 5) stage_central(const StageArgs a)
 {
     extern __shared__ double sm[];
     const int gs = blockDim.x / a.wpc;
     const int g = threadIdx.x / gs;
-    central_window<PDE, H>(a, launch_cx(a), (int64_t)blockIdx.x * a.wpc + g, sm + (size_t)g * a.win_smem,
-                           threadIdx.x - g * gs, gs);
+    central_window<PDE, H, RKS>(a, launch_cx(a), (int64_t)blockIdx.x * a.wpc + g, sm + (size_t)g * a.win_smem,
+                                threadIdx.x - g * gs, gs);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,7 +417,7 @@ __device__ __forceinline__ double weno5(double f0, double f1, double f2, double 
 // ---------------------------------------------------------------------------
 // WENO5 / AT-WENO5 fluxes: reactive Euler and scalar advection
 // ---------------------------------------------------------------------------
-template <int PDE>
+template <int PDE, int RKS = RKS_ANY>
 __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, int64_t win, double* sm)
 {
     using P = Phys<PDE>;
@@ -478,15 +478,15 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
                 K = fma(-a.prm[1] * Q[3], at_exp(-a.prm[2] * Q[0] * at_rcp(p)), K);
             }
         }
-        rk_update(a, cx, v, j, chunk * Tw + jl, pe, K, x, rk_load(a, cx, v * a.N + j));
+        rk_update<RKS>(a, cx, v, j, chunk * Tw + jl, pe, K, x, rk_load<RKS>(a, cx, v * a.N + j));
     }
 }
 
-template <int PDE>
+template <int PDE, int RKS>
 __global__ void __launch_bounds__(256) stage_weno(const StageArgs a)
 {
     extern __shared__ double sm[];
-    weno_window<PDE>(a, launch_cx(a), blockIdx.x, sm);
+    weno_window<PDE, RKS>(a, launch_cx(a), blockIdx.x, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -668,25 +668,37 @@ cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaSt
 #undef AT_WARP_LAUNCH
         return cudaGetLastError();
     }
+    // the benchmarked combinations (6th-order reacting N-S with RK4, reactive
+    // Euler with RK3-TVD) get one kernel per RK stage kind
+    const int kind = atk::rk_stage_kind(a.rk, a.stage);
+    constexpr int ANY = atk::RKS_ANY;
     switch (pde) {
     case atk::ADVDIFF:
-        if (order == 2) atk::stage_central<atk::ADVDIFF, 1><<<grid, block, smem, st>>>(b);
-        else if (order == 4) atk::stage_central<atk::ADVDIFF, 2><<<grid, block, smem, st>>>(b);
-        else atk::stage_central<atk::ADVDIFF, 3><<<grid, block, smem, st>>>(b);
+        if (order == 2) atk::stage_central<atk::ADVDIFF, 1, ANY><<<grid, block, smem, st>>>(b);
+        else if (order == 4) atk::stage_central<atk::ADVDIFF, 2, ANY><<<grid, block, smem, st>>>(b);
+        else atk::stage_central<atk::ADVDIFF, 3, ANY><<<grid, block, smem, st>>>(b);
         break;
     case atk::RNS:
-        if (order == 2) atk::stage_central<atk::RNS, 1><<<grid, block, smem, st>>>(b);
-        else if (order == 4) atk::stage_central<atk::RNS, 2><<<grid, block, smem, st>>>(b);
-        else atk::stage_central<atk::RNS, 3><<<grid, block, smem, st>>>(b);
+        if (order == 2) atk::stage_central<atk::RNS, 1, ANY><<<grid, block, smem, st>>>(b);
+        else if (order == 4) atk::stage_central<atk::RNS, 2, ANY><<<grid, block, smem, st>>>(b);
+        else if (kind == atk::RKS_RK4_0) atk::stage_central<atk::RNS, 3, atk::RKS_RK4_0><<<grid, block, smem, st>>>(b);
+        else if (kind == atk::RKS_RK4_MID) atk::stage_central<atk::RNS, 3, atk::RKS_RK4_MID><<<grid, block, smem, st>>>(b);
+        else if (kind == atk::RKS_RK4_LAST) atk::stage_central<atk::RNS, 3, atk::RKS_RK4_LAST><<<grid, block, smem, st>>>(b);
+        else atk::stage_central<atk::RNS, 3, ANY><<<grid, block, smem, st>>>(b);
         break;
     case atk::RNS_CHAIN:
-        if (order == 2) atk::stage_central<atk::RNS_CHAIN, 1><<<grid, block, smem, st>>>(b);
-        else if (order == 4) atk::stage_central<atk::RNS_CHAIN, 2><<<grid, block, smem, st>>>(b);
-        else atk::stage_central<atk::RNS_CHAIN, 3><<<grid, block, smem, st>>>(b);
+        if (order == 2) atk::stage_central<atk::RNS_CHAIN, 1, ANY><<<grid, block, smem, st>>>(b);
+        else if (order == 4) atk::stage_central<atk::RNS_CHAIN, 2, ANY><<<grid, block, smem, st>>>(b);
+        else atk::stage_central<atk::RNS_CHAIN, 3, ANY><<<grid, block, smem, st>>>(b);
         break;
-    case atk::EULER: atk::stage_weno<atk::EULER><<<grid, block, smem, st>>>(b); break;
-    case atk::BURGERS: atk::stage_weno<atk::BURGERS><<<grid, block, smem, st>>>(b); break;
-    default: atk::stage_weno<atk::ADV_WENO><<<grid, block, smem, st>>>(b); break;
+    case atk::EULER:
+        if (kind == atk::RKS_RK3_0) atk::stage_weno<atk::EULER, atk::RKS_RK3_0><<<grid, block, smem, st>>>(b);
+        else if (kind == atk::RKS_RK3_1) atk::stage_weno<atk::EULER, atk::RKS_RK3_1><<<grid, block, smem, st>>>(b);
+        else if (kind == atk::RKS_RK3_2) atk::stage_weno<atk::EULER, atk::RKS_RK3_2><<<grid, block, smem, st>>>(b);
+        else atk::stage_weno<atk::EULER, ANY><<<grid, block, smem, st>>>(b);
+        break;
+    case atk::BURGERS: atk::stage_weno<atk::BURGERS, ANY><<<grid, block, smem, st>>>(b); break;
+    default: atk::stage_weno<atk::ADV_WENO, ANY><<<grid, block, smem, st>>>(b); break;
     }
     return cudaGetLastError();
 }
@@ -703,26 +715,24 @@ cudaError_t atk_launch_ring_seed(const atk::StageArgs& a, cudaStream_t st)
 
 cudaError_t atk_set_smem_limits()
 {
-    cudaError_t e = cudaSuccess;
+    constexpr int ANY = atk::RKS_ANY;
     const int big = 200 * 1024;
-    e = cudaFuncSetAttribute(atk::stage_weno<atk::EULER>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(atk::stage_weno<atk::ADV_WENO>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(atk::stage_weno<atk::BURGERS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(atk::stage_central<atk::RNS, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(atk::stage_central<atk::RNS, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(atk::stage_central<atk::RNS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e != cudaSuccess) return e;
-    for (auto f : {atk::stage_central<atk::ADVDIFF, 1>, atk::stage_central<atk::ADVDIFF, 2>,
-                   atk::stage_central<atk::ADVDIFF, 3>}) {
-        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    const void* fns[] = {
+        (const void*)atk::stage_weno<atk::EULER, ANY>, (const void*)atk::stage_weno<atk::EULER, atk::RKS_RK3_0>,
+        (const void*)atk::stage_weno<atk::EULER, atk::RKS_RK3_1>, (const void*)atk::stage_weno<atk::EULER, atk::RKS_RK3_2>,
+        (const void*)atk::stage_weno<atk::ADV_WENO, ANY>, (const void*)atk::stage_weno<atk::BURGERS, ANY>,
+        (const void*)atk::stage_central<atk::RNS, 3, ANY>, (const void*)atk::stage_central<atk::RNS, 3, atk::RKS_RK4_0>,
+        (const void*)atk::stage_central<atk::RNS, 3, atk::RKS_RK4_MID>,
+        (const void*)atk::stage_central<atk::RNS, 3, atk::RKS_RK4_LAST>, (const void*)atk::stage_central<atk::RNS, 2, ANY>,
+        (const void*)atk::stage_central<atk::RNS, 1, ANY>, (const void*)atk::stage_central<atk::RNS_CHAIN, 1, ANY>,
+        (const void*)atk::stage_central<atk::RNS_CHAIN, 2, ANY>, (const void*)atk::stage_central<atk::RNS_CHAIN, 3, ANY>,
+        (const void*)atk::stage_central<atk::ADVDIFF, 1, ANY>, (const void*)atk::stage_central<atk::ADVDIFF, 2, ANY>,
+        (const void*)atk::stage_central<atk::ADVDIFF, 3, ANY>};
+    for (const void* f : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
         if (e != cudaSuccess) return e;
     }
-    return e;
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------

@@ -91,8 +91,16 @@ enum {
     AT_OPT_PATH = 0,        /* value: AT_PATH_*                                                  */
     AT_OPT_WAIT_LIMIT = 1,  /* polls (~0.2 us each) before a persistent-path wait gives up with
                                AT_ETIMEOUT; default 4,000,000                                    */
-    AT_OPT_WITHHOLD_PE = 2  /* fault injection: this PE never announces its progress, so its
+    AT_OPT_WITHHOLD_PE = 2, /* fault injection: this PE never announces its progress, so its
                                neighbours' waits run out (-1, the default: none)                 */
+    AT_OPT_ARRIVAL = 3      /* 1: real asynchrony on the persistent path.  Instead of drawing a
+                               delay, each PE boundary uses the freshest stage argument of the
+                               neighbour that has arrived (never older than k_max, or than the
+                               start-up clamp allows: it waits for that), as the CPU PEs of the
+                               paper do.  Runs are then not reproducible; at_set_delay_trace
+                               records the delays so that a run can be replayed (the oracle
+                               does).  0 (default): Philox delays.  AT_EINVAL from at_step if
+                               the persistent path cannot be taken.                             */
 };
 
 typedef struct {
@@ -172,6 +180,14 @@ int at_read(at_ctx* ctx, int what, void* dst, size_t bytes, int dst_on_device);
 
 /* Options (AT_OPT_*); they apply from the next at_step on. */
 int at_set_option(at_ctx* ctx, int key, int64_t value);
+
+/* Delay trace: from the current level on, the kernels write the delay of
+ * every (step, stage, PE, side) of the next max_steps steps into trace_dev,
+ * uint8 [max_steps][stages][P][2] in caller-owned device memory (side 0 =
+ * left boundary of the PE); steps beyond max_steps are not recorded.  NULL or
+ * max_steps <= 0 detaches it.  The buffer is borrowed until it is detached
+ * or the context is destroyed. */
+int at_set_delay_trace(at_ctx* ctx, uint8_t* trace_dev, int64_t max_steps);
 
 /* Tracing: with enable = 1, every kernel launch at_step enqueues afterwards is
  * bracketed by two CUDA events on the stream, and at_read(AT_READ_STATS)

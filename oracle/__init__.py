@@ -95,6 +95,7 @@ def lib():
         L.orc_set_level.argtypes = [ctypes.c_void_p, ctypes.c_int64]
         L.orc_set_state.argtypes = [ctypes.c_void_p, P(ctypes.c_double)]
         L.orc_force_delays.argtypes = [ctypes.c_void_p, P(ctypes.c_int32)]
+        L.orc_set_delay_trace.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]
         _lib = L
     return _lib
 
@@ -204,6 +205,16 @@ class Oracle:
         kf = np.ascontiguousarray(k, dtype=np.int32).reshape(self.P, 2)
         self._kfix = kf
         lib().orc_force_delays(self._h, kf.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+
+    def set_delay_trace(self, trace, n0: int = 0) -> None:
+        """Replay recorded delays: trace[steps][stages][P][2] (uint8) for the
+        levels n0, n0 + 1, ... (None clears)."""
+        if trace is None:
+            lib().orc_set_delay_trace(self._h, None, 0, 0)
+            return
+        t = np.ascontiguousarray(trace, dtype=np.uint8)
+        assert t.ndim == 4 and t.shape[2:] == (self.P, 2), t.shape
+        lib().orc_set_delay_trace(self._h, ctypes.c_void_p(t.ctypes.data), int(n0), int(t.shape[0]))
 
     def draw(self, level: int, stage: int, pe: int, side: int) -> int:
         return int(lib().orc_draw(self._h, int(level), int(stage), int(pe), int(side)))

@@ -62,6 +62,8 @@ struct orc_ctx {
     int32_t* keff; /* delays in use  [S][P][2]        */
     uint8_t* dlog; /* last step's    [S][P][2]        */
     int32_t* kfix; /* forced raw delays [P][2], or NULL to draw them */
+    uint8_t* trace;            /* delays of every (step, stage, PE, side) to replay, or NULL */
+    int64_t trace_n0, trace_steps;
 };
 
 /* ------------------------------------------------------------------ */
@@ -480,11 +482,17 @@ static void rhs_point(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t
     }
 }
 
+/* delays of stage s at `level`: a replayed trace (delays observed in a run
+ * whose delays were not drawn, e.g. taken from arrival order), else forced
+ * ones, else the Philox draw; always through the start-up clamp */
 static void set_keff(orc_ctx* c, int64_t level, int s, const int32_t* kforce)
 {
+    const uint8_t* tr = NULL;
+    if (c->trace && level >= c->trace_n0 && level < c->trace_n0 + c->trace_steps)
+        tr = c->trace + ((size_t)(level - c->trace_n0) * c->S + s) * (size_t)c->P * 2;
     for (int64_t p = 0; p < c->P; ++p)
         for (int side = 0; side < 2; ++side) {
-            int k = kforce ? kforce[p * 2 + side] : orc_draw(c, level, s, p, side);
+            int k = tr ? tr[p * 2 + side] : (kforce ? kforce[p * 2 + side] : orc_draw(c, level, s, p, side));
             c->keff[((size_t)s * c->P + p) * 2 + side] = clamp_k(c, level, k);
         }
 }
@@ -614,6 +622,7 @@ void orc_destroy(orc_ctx* c)
 {
     if (!c) return;
     free(c->kfix);
+    free(c->trace);
     free(c->u);
     free(c->hist);
     free(c->K);
@@ -659,6 +668,18 @@ void orc_set_level(orc_ctx* c, int64_t level) { c->level = level; }
 void orc_set_state(orc_ctx* c, const double* u)
 {
     memcpy(c->u, u, (size_t)c->nvar * c->N * sizeof(double));
+}
+
+void orc_set_delay_trace(orc_ctx* c, const uint8_t* trace, int64_t n0, int64_t nsteps)
+{
+    free(c->trace);
+    c->trace = NULL;
+    if (!trace || nsteps <= 0) return;
+    const size_t bytes = (size_t)nsteps * c->S * (size_t)c->P * 2;
+    c->trace = (uint8_t*)malloc(bytes);
+    memcpy(c->trace, trace, bytes);
+    c->trace_n0 = n0;
+    c->trace_steps = nsteps;
 }
 
 void orc_force_delays(orc_ctx* c, const int32_t* k)

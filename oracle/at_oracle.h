@@ -77,6 +77,9 @@ void orc_set_level(orc_ctx* c, int64_t level);
 void orc_set_state(orc_ctx* c, const double* u /* [nvar][n] */);
 /* fixed raw delays [P][2] for every following step (NULL: draw again) */
 void orc_force_delays(orc_ctx* c, const int32_t* k);
+/* replay recorded delays: trace[nsteps][stages][P][2] holds the delay of
+ * every stage of levels n0 .. n0 + nsteps - 1 (copied; NULL clears) */
+void orc_set_delay_trace(orc_ctx* c, const uint8_t* trace, int64_t n0, int64_t nsteps);
 /* WENO flux F[nvar] at the edge between points i and i+1 as PE `pe` sees it */
 void orc_edge_flux(orc_ctx* c, int64_t level, int stage, const int32_t* kforce, int64_t pe, int64_t i,
                    double* F);

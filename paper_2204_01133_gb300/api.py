@@ -29,11 +29,12 @@ STAGES = {"rk2": 2, "rk3tvd": 3, "rk4": 4}
 
 # every symbol include/at.h declares
 SYMBOLS = ("at_create", "at_workspace_bytes", "at_set_problem", "at_set_delays", "at_step", "at_run",
-           "at_read", "at_profile", "at_set_option", "at_destroy", "at_last_error", "at_run_noalloc",
+           "at_read", "at_profile", "at_set_option", "at_set_delay_trace", "at_destroy", "at_last_error",
+           "at_run_noalloc",
            "at_batch_table_bytes", "at_batch_create", "at_batch_bind", "at_batch_release", "at_batch_set_config",
            "at_batch_step", "at_batch_run", "at_batch_query", "at_batch_destroy")
 PATH_AUTO, PATH_STAGE, PATH_PERSISTENT = 0, 1, 2
-OPT_PATH, OPT_WAIT_LIMIT, OPT_WITHHOLD_PE = 0, 1, 2
+OPT_PATH, OPT_WAIT_LIMIT, OPT_WITHHOLD_PE, OPT_ARRIVAL = 0, 1, 2, 3
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -90,6 +91,8 @@ def lib():
         L.at_profile.argtypes = [vp, ctypes.c_int]
         L.at_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
         L.at_set_option.restype = ctypes.c_int
+        L.at_set_delay_trace.argtypes = [vp, vp, ctypes.c_int64]
+        L.at_set_delay_trace.restype = ctypes.c_int
         L.at_run_noalloc.argtypes = [P(Problem), P(Delays), vp, ctypes.c_int64, ctypes.c_int, vp]
         L.at_run_noalloc.restype = ctypes.c_int
         L.at_last_error.restype = ctypes.c_char_p
@@ -233,6 +236,22 @@ class Solver:
 
     def set_option(self, key: int, value: int):
         check(lib().at_set_option(self._h, int(key), int(value)))
+
+    def trace_delays(self, nsteps: int):
+        """Record the delay of every (step, stage, PE, side) of the next
+        ``nsteps`` steps into a device buffer; ``read_trace()`` returns it
+        as uint8 [nsteps][stages][P][2].  ``nsteps`` = 0 detaches it."""
+        torch = self.torch
+        if nsteps <= 0:
+            check(lib().at_set_delay_trace(self._h, None, 0))
+            self._trace = None
+            return
+        self._trace = torch.zeros((nsteps, self.stages, self.P, 2), dtype=torch.uint8, device=self.u.device)
+        check(lib().at_set_delay_trace(self._h, ctypes.c_void_p(self._trace.data_ptr()), int(nsteps)))
+
+    def read_trace(self) -> np.ndarray:
+        self.torch.cuda.synchronize(self.u.device)
+        return self._trace.cpu().numpy()
 
     def set_path(self, path: str):
         self.set_option(OPT_PATH, {"auto": PATH_AUTO, "stage": PATH_STAGE, "persistent": PATH_PERSISTENT}[path])

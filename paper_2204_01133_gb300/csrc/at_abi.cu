@@ -300,6 +300,9 @@ struct at_ctx {
     int64_t persist_cap = 0;       // PEs one cooperative launch can hold (0: unavailable)
     int64_t wait_limit = 4000000;  // polls of a bounded wait
     int64_t withhold_pe = -1;
+    int arrival = 0;               // at_set_option(AT_OPT_ARRIVAL)
+    uint8_t* trace = nullptr;      // at_set_delay_trace: caller-owned device buffer
+    int64_t trace_n0 = 0, trace_steps = 0;
     // tracing (at_profile)
     bool profile = false;
     std::vector<cudaEvent_t> ev;  // pairs: ev[2i] before, ev[2i+1] after launch i
@@ -469,7 +472,13 @@ int at_step(at_ctx* c, int64_t nsteps)
         return fail(AT_EINVAL, "the persistent path needs a central PDE and at most %lld PEs (have %lld)",
                     (long long)c->persist_cap, (long long)L.P);
     const bool persist = c->path == AT_PATH_PERSISTENT || (c->path == AT_PATH_AUTO && can_persist);
+    if (c->arrival && !persist)
+        return fail(AT_EINVAL, "delays by arrival need the persistent path (a central PDE and at most %lld PEs)",
+                    (long long)c->persist_cap);
     c->last_path = persist ? AT_PATH_PERSISTENT : AT_PATH_STAGE;
+    c->base.trace = c->trace;
+    c->base.trace_n0 = c->trace_n0;
+    c->base.trace_steps = c->trace_steps;
     if (persist) {
         if (nsteps == 0) return AT_OK;
         atk::StageArgs a = c->base;
@@ -477,6 +486,7 @@ int at_step(at_ctx* c, int64_t nsteps)
         a.Y = u;
         a.wait_limit = c->wait_limit;
         a.withhold_pe = c->withhold_pe;
+        a.arrival = c->arrival;
         e = record(c, true);
         if (e == cudaSuccess) e = atk_launch_persist(a, c->pb.pde, c->pb.order, c->level, nsteps, c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
@@ -595,8 +605,27 @@ int at_set_option(at_ctx* c, int key, int64_t value)
     case AT_OPT_WITHHOLD_PE:
         c->withhold_pe = value;
         return AT_OK;
+    case AT_OPT_ARRIVAL:
+        if (value != 0 && value != 1) return fail(AT_EINVAL, "AT_OPT_ARRIVAL takes 0 or 1");
+        c->arrival = (int)value;
+        return AT_OK;
     default: return fail(AT_EINVAL, "unknown option %d", key);
     }
+}
+
+int at_set_delay_trace(at_ctx* c, uint8_t* trace_dev, int64_t max_steps)
+{
+    if (!c) return fail(AT_EINVAL, "context is NULL");
+    if (!trace_dev || max_steps <= 0) {
+        c->trace = nullptr;
+        c->trace_steps = 0;
+        return AT_OK;
+    }
+    if (!c->have_problem) return fail(AT_ESTATE, "at_set_problem must come first");
+    c->trace = trace_dev;
+    c->trace_n0 = c->level;
+    c->trace_steps = max_steps;
+    return AT_OK;
 }
 
 int at_profile(at_ctx* c, int enable)

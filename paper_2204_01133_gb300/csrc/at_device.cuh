@@ -51,6 +51,11 @@ struct StageArgs {
     int64_t wait_limit;  // polls before a wait gives up (bounded spin)
     int64_t withhold_pe; // fault injection: this PE never publishes (-1: none)
     int slack;           // ring levels beyond k_max + q + 1
+    int arrival;         // 1: a delay is the age of the freshest neighbour data that has arrived
+    // delay trace (optional): the delay of every (step, stage, PE, side) of
+    // levels trace_n0 .. trace_n0 + trace_steps - 1, [steps][S][P][2]
+    uint8_t* trace;
+    int64_t trace_n0, trace_steps;
     // batched path: the solve's own buffers (the stage kernels get X/Y/u per launch)
     double* bufA;
     double* bufB;
@@ -93,6 +98,26 @@ __device__ __forceinline__ int keff_at(const StageArgs& a, int64_t level, int st
     int64_t avail = level - qq;
     if (avail < 0) avail = 0;
     return (int64_t)k < avail ? k : (int)avail;
+}
+
+// largest delay the start-up clamp allows at `level` (no level below 0 is read)
+__device__ __forceinline__ int kcap_at(const StageArgs& a, int64_t level)
+{
+    if (a.mode == SYNC) return 0;
+    int64_t avail = level - ((a.mode == AT) ? a.q : 0);
+    if (avail < 0) avail = 0;
+    return avail < a.kmax ? (int)avail : a.kmax;
+}
+
+// record the delay used at (level, stage, PE, side): the per-step log and,
+// when one is attached, the trace
+__device__ __forceinline__ void log_delay(const StageArgs& a, int64_t level, int stage, int64_t pe, int side, int k)
+{
+    a.dlog[((int64_t)stage * a.P + pe) * 2 + side] = (uint8_t)k;
+    if (a.trace) {
+        const int64_t t = level - a.trace_n0;
+        if (t >= 0 && t < a.trace_steps) a.trace[((t * a.S + stage) * a.P + pe) * 2 + side] = (uint8_t)k;
+    }
 }
 
 __device__ __forceinline__ int keff(const StageArgs& a, int64_t pe, int side)

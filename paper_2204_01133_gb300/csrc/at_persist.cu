@@ -179,12 +179,25 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
             if (warp == hwarp) {
                 if (lane < 2) {
                     const int side = lane;
-                    const int k = keff_at(a, n, s, pe, side);
+                    int k;
+                    bool ok;
+                    if (a.arrival) {
+                        // the freshest stage-s argument of the neighbour that has
+                        // arrived, once one recent enough for the clamp is there
+                        const int kc = kcap_at(a, n);
+                        ok = wait_ge(a, a.done + nbr[side], (n - kc) * S + s);
+                        const int64_t m = (load_acquire(a.done + nbr[side]) - s) / S;
+                        k = m >= n ? 0 : (int)(n - m);
+                        if (k > kc) k = kc;  // only if the wait gave up
+                    } else {
+                        // the neighbour's stage-s argument at the drawn level n-k
+                        k = keff_at(a, n, s, pe, side);
+                        ok = wait_ge(a, a.done + nbr[side], (n - k) * S + s);
+                    }
                     s_k[side] = k;
-                    a.dlog[((int64_t)s * a.P + pe) * 2 + side] = (uint8_t)k;
-                    // the neighbour's stage-s argument at level n-k, and the ring slot of (Ln, sn) free
-                    if (!wait_ge(a, a.done + nbr[side], (n - k) * S + s) ||
-                        !wait_ge(a, a.done + nbr[side], (Ln - a.slack - 1) * S + sn + 1))
+                    log_delay(a, n, s, pe, side, k);
+                    // and the ring slot of (Ln, sn) free
+                    if (!ok || !wait_ge(a, a.done + nbr[side], (Ln - a.slack - 1) * S + sn + 1))
                         atomicExch(&s_abort, 1);
                     __threadfence();
                 }

@@ -82,7 +82,7 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
             const int h = side == 0 ? hp : hp - L0;         // position in the neighbour's edge window
             const int64_t nbr = side == 0 ? (pe == 0 ? a.P - 1 : pe - 1) : (pe == a.P - 1 ? 0 : pe + 1);
             const int k = keff_at(a, cx.level, cx.stage, pe, side);
-            if (h == 0 && l == 0) a.dlog[((int64_t)cx.stage * a.P + pe) * 2 + side] = (uint8_t)k;
+            if (h == 0 && l == 0) log_delay(a, cx.level, cx.stage, pe, side, k);
             if ((a.wnz[k] >> l) & 1) {  // a level with weight 0 is not part of the scheme (and may not exist yet)
                 const int64_t base = ring_index(a, cx.level - k - l, cx.stage, nbr, 1 - side, h, 0);
 #pragma unroll
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256, PPL <= 2 ? 6 : (PPL == 4 ? 4 : 3)) stage_
         const int h = lane - side * H;  // position in the neighbour's edge window
         const int64_t nbr = side == 0 ? (pe == 0 ? a.P - 1 : pe - 1) : (pe == a.P - 1 ? 0 : pe + 1);
         const int k = keff_at(a, cx.level, cx.stage, pe, side);
-        if (h == 0) a.dlog[((int64_t)cx.stage * a.P + pe) * 2 + side] = (uint8_t)k;
+        if (h == 0) log_delay(a, cx.level, cx.stage, pe, side, k);
         const int nw = (a.mode == AT) ? a.q + 1 : 1;
         double v[AT_QMAX + 1];
 #pragma unroll

@@ -727,6 +727,27 @@ def test_rns_rhs_converges_to_the_pde(form, order):
     assert abs(rates[-1] - order) < 0.5, (errs, rates)
 
 
+def test_replayed_delay_trace_reproduces_a_run():
+    """The oracle's delay replay (used to check runs whose delays come from
+    arrival order): a run under another seed that replays the recorded delays
+    of a first run reproduces it bit for bit; without the trace it differs."""
+    pb, u0 = W.advdiff(n=512, pe_size=32, mode="at", k_max=3, seed=1, cfl=0.05)
+    a = oracle.Oracle(pb, u0)
+    trace = []
+    for _ in range(40):
+        assert a.run(1) == 0
+        trace.append(a.delays())
+    trace = np.stack(trace)
+    assert len(np.unique(trace)) == 4
+    b = oracle.Oracle(dict(pb, seed=99), u0)
+    b.set_delay_trace(trace, 0)
+    assert b.run(40) == 0
+    assert np.array_equal(a.state(), b.state())
+    c = oracle.Oracle(dict(pb, seed=99), u0)
+    assert c.run(40) == 0
+    assert not np.array_equal(a.state(), c.state())
+
+
 # --------------------------------------------------------------------------
 # Conservation (flux form, periodic): exact under SYNC
 # --------------------------------------------------------------------------

@@ -96,6 +96,8 @@ def lib():
         L.orc_set_state.argtypes = [ctypes.c_void_p, P(ctypes.c_double)]
         L.orc_force_delays.argtypes = [ctypes.c_void_p, P(ctypes.c_int32)]
         L.orc_set_delay_trace.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]
+        L.orc_get_history.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+        L.orc_get_history.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -168,6 +170,14 @@ class Oracle:
     def delays(self) -> np.ndarray:
         out = np.empty((self.stages, self.P, 2), dtype=np.uint8)
         lib().orc_get_delays(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+        return out
+
+    def history(self, level: int, stage: int):
+        """The stored stage argument U^{level,(stage)} [nvar][n], or None if
+        it is no longer (or not yet) kept."""
+        out = np.empty((self.nvar, self.n), dtype=np.float64)
+        if lib().orc_get_history(self._h, int(level), int(stage), ctypes.c_void_p(out.ctypes.data)) != 0:
+            return None
         return out
 
     def set_history(self, level: int, stage: int, field: np.ndarray) -> None:

@@ -647,6 +647,20 @@ void orc_get_delays(const orc_ctx* c, uint8_t* out)
     memcpy(out, c->dlog, (size_t)c->S * c->P * 2);
 }
 
+int orc_get_history(const orc_ctx* c, int64_t level, int stage, double* out)
+{
+    /* kept: every stage of the last R completed steps, and the stage-0
+     * argument of the current level (the state itself) */
+    if (stage < 0 || stage >= c->S) return -1;
+    if (level == c->level && stage == 0) {
+        memcpy(out, c->u, (size_t)c->nvar * c->N * sizeof(double));
+        return 0;
+    }
+    if (level >= c->level || level < c->level - c->R) return -1;
+    memcpy(out, field(c, level, stage), (size_t)c->nvar * c->N * sizeof(double));
+    return 0;
+}
+
 void orc_set_history(orc_ctx* c, int64_t level, int stage, const double* f)
 {
     memcpy(field(c, level, stage), f, (size_t)c->nvar * c->N * sizeof(double));

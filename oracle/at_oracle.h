@@ -62,6 +62,9 @@ void orc_get_state(const orc_ctx* c, double* out /* [nvar][n] */);
 void orc_get_delays(const orc_ctx* c, uint8_t* out);
 
 /* ---- pieces exposed for the pins in tests/ ---- */
+/* copy the stored stage argument U^{level,(stage)} (a full field [nvar][n]);
+ * -1 if that level and stage are not in the kept history */
+int orc_get_history(const orc_ctx* c, int64_t level, int stage, double* out);
 /* overwrite the stored stage argument U^{level,(stage)} (a full field) */
 void orc_set_history(orc_ctx* c, int64_t level, int stage, const double* field);
 /* right-hand side K of stage `stage` at level `level`, reading U^{level,(stage)}

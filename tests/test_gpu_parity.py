@@ -228,6 +228,50 @@ def test_rns_full_size_sampled_pes():
     _sampled_full_size(pb, u0, 6, (0, 77777, P // 2, P - 1))
 
 
+@pytest.mark.parametrize("path,maker", [("stage", "rns"), ("persistent", "rns"), ("stage", "detonation"),
+                                        ("persistent", "advdiff"), ("stage", "advdiff-rk3")])
+def test_ring_holds_the_owners_stage_arguments(path, maker):
+    """The history ring (the per-step message of S stages of Sec. 2.3): after a
+    run, every slot holds the owner PE's edge window of its stage argument
+    U^{m,(s)} as the oracle computes it, for every level both keep."""
+    import ctypes
+    from paper_2204_01133_gb300 import api
+    if maker == "rns":
+        pb, u0 = W.rns(case="flame", n=2048, pe_size=64, mode="at", k_max=4, seed=1, dt=0.003)
+    elif maker == "detonation":
+        pb, u0 = W.detonation(n=4096, pe_size=512, mode="at", k_max=4, seed=2)
+    elif maker == "advdiff":
+        pb, u0 = W.advdiff(n=1024, pe_size=32, mode="as", k_max=3, seed=3, cfl=0.05)
+    else:
+        pb, u0 = W.advdiff(n=960, pe_size=48, order=6, mode="at", k_max=2, seed=4, cfl=0.01, rk="rk3tvd")
+    steps = 25
+    s = api.Solver(pb, u0, path=path)
+    s.run(steps)
+    st = s.stats()
+    R, S, H, nv = st.ring_levels, st.stages, st.halo, st.nvar
+    P, B = pb["n"] // pb["pe_size"], pb["pe_size"]
+    ring = np.empty((R, S, P, 2, H, nv), dtype=np.float64)
+    api.check(api.lib().at_read(s._h, api.READ_RING, ctypes.c_void_p(ring.ctypes.data), ring.nbytes, 0))
+    o = oracle.Oracle(pb, u0)
+    assert o.run(steps) == 0
+    idx = np.arange(P)[:, None] * B
+    left = idx + np.arange(H)[None, :]
+    right = idx + (B - H) + np.arange(H)[None, :]
+    checked = 0
+    for m in range(steps - R + 1, steps + 1):
+        for stage in range(S):
+            if m == steps and stage > 0:
+                continue  # not produced yet
+            U = o.history(m, stage)
+            if U is None:
+                continue
+            g = ring[m % R, stage]                       # [P][2][H][nvar]
+            ref = np.stack([U[:, left], U[:, right]], axis=0).transpose(2, 0, 3, 1)  # [P][2][H][nvar]
+            assert rel_err(g, ref) <= TOL_RUN, (m, stage)
+            checked += 1
+    assert checked >= S * 2
+
+
 def test_deterministic_and_seeded():
     from paper_2204_01133_gb300.api import Solver
     pb, u0 = W.advdiff(n=2048, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075)

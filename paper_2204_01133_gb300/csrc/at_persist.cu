@@ -181,25 +181,29 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                     const int side = lane;
                     int k;
                     bool ok;
+                    // one bounded wait for both conditions on the neighbour's
+                    // progress: the stage-s argument this stage reads has been
+                    // published, and the ring slot of (Ln, sn) this stage writes is
+                    // no longer read by it
+                    const int64_t free_at = (Ln - a.slack - 1) * S + sn + 1;
                     if (a.arrival) {
                         // the freshest stage-s argument of the neighbour that has
                         // arrived, once one recent enough for the clamp is there
                         const int kc = kcap_at(a, n);
-                        ok = wait_ge(a, a.done + nbr[side], (n - kc) * S + s);
+                        const int64_t need = (n - kc) * S + s;
+                        ok = wait_ge(a, a.done + nbr[side], need > free_at ? need : free_at);
                         const int64_t m = (load_acquire(a.done + nbr[side]) - s) / S;
                         k = m >= n ? 0 : (int)(n - m);
                         if (k > kc) k = kc;  // only if the wait gave up
                     } else {
                         // the neighbour's stage-s argument at the drawn level n-k
                         k = keff_at(a, n, s, pe, side);
-                        ok = wait_ge(a, a.done + nbr[side], (n - k) * S + s);
+                        const int64_t need = (n - k) * S + s;
+                        ok = wait_ge(a, a.done + nbr[side], need > free_at ? need : free_at);
                     }
                     s_k[side] = k;
                     log_delay(a, n, s, pe, side, k);
-                    // and the ring slot of (Ln, sn) free
-                    if (!ok || !wait_ge(a, a.done + nbr[side], (Ln - a.slack - 1) * S + sn + 1))
-                        atomicExch(&s_abort, 1);
-                    __threadfence();
+                    if (!ok) atomicExch(&s_abort, 1);
                 }
                 __syncwarp();
                 if (!*(volatile int*)&s_abort) {
@@ -263,14 +267,16 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                         side = 1;
                         h = jl - (B - H);
                     }
-                    if (side >= 0) {
-                        __stcg(a.ring + ring_index(a, Ln, sn, pe, side, h, v), y);
-                        __threadfence();
-                    }
+                    if (side >= 0) __stcg(a.ring + ring_index(a, Ln, sn, pe, side, h, v), y);
                 }
             }
             __syncthreads();
-            if (threadIdx.x == 0 && pe != a.withhold_pe) store_release(a.done + pe, n * S + s + 1);
+            // publish: the barrier orders every thread's ring writes before thread
+            // 0's device-scope fence and release store (both cumulative)
+            if (threadIdx.x == 0 && pe != a.withhold_pe) {
+                __threadfence();
+                store_release(a.done + pe, n * S + s + 1);
+            }
         }
     }
 out:

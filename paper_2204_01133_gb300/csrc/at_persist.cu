@@ -112,16 +112,54 @@ __device__ __forceinline__ double point_update(const StageArgs& a, int s, int v,
     return y;
 }
 
+// named barriers (ids 1..5; 0 is __syncthreads): bar.sync waits until
+// `count` threads have arrived, bar.arrive counts this warp without waiting
+template <int ID>
+__device__ __forceinline__ void bar_sync(int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "r"(count) : "memory");
+}
+template <int ID>
+__device__ __forceinline__ void bar_arrive(int count)
+{
+    asm volatile("bar.arrive %0, %1;" ::"n"(ID), "r"(count) : "memory");
+}
+// the barrier of parity p among a pair (ids B0, B0 + 1), with immediate ids
+template <int B0>
+__device__ __forceinline__ void bar_sync_p(int p, int count)
+{
+    if (p) bar_sync<B0 + 1>(count);
+    else bar_sync<B0>(count);
+}
+template <int B0>
+__device__ __forceinline__ void bar_arrive_p(int p, int count)
+{
+    if (p) bar_arrive<B0 + 1>(count);
+    else bar_arrive<B0>(count);
+}
+
 // GB300's FP64 unit spends the same time on a warp instruction whatever the
 // number of active lanes, so the work is laid out in whole, uniform warps
-// with fixed roles; two barriers per stage:
-//   (A) warps of the "derive" role: own-point derived quantities and the
+// with fixed roles.  Stage t (= step n, stage s) of a PE:
+//   (A) derive warps: own-point derived quantities into G[t % 2] and the
 //       Arrhenius factor exp(-Ea/T) from the temperature among them;
-//       the halo warp: delays, the bounded neighbour waits, then the buffer
-//       levels from the ring, weighted and summed per buffer point;
-//   (C) the worker warps: stencil, source and RK update of every (point,
-//       variable), one variable per warp; the edge points go straight into
-//       the ring.  Then the progress counter is published.
+//   (C) all worker warps: stencil, source and RK update of every (point,
+//       variable), one variable per warp, the edge points straight into the
+//       ring; then the progress counter is published.
+// The halo warp runs one stage ahead of the workers: while they do stage t
+// it takes the delays of stage t + 1, waits (boundedly) for the
+// neighbours' data, fetches the delayed levels from the ring and writes the
+// weighted buffer values into the halo columns of G[(t + 1) % 2], so that
+// its latency hides behind the workers' arithmetic.  Named barriers, by
+// the parity p of the stage:
+//   1 + p  halo of stage t ready      (halo warp arrives, workers sync)
+//   3 + p  G[p] no longer read        (workers arrive after stage t, the
+//                                      halo warp syncs before filling G[p]
+//                                      for stage t + 2)
+//   5      workers' phase C done      (workers only, before publishing)
+// A failed wait records the stage in s_abort_at before the halo warp
+// arrives; the workers stop at that stage and the halo warp matches the one
+// arrival it would otherwise have consumed, so every barrier completes.
 template <int PDE, int H>
 __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_t level0, int64_t nsteps)
 {
@@ -134,25 +172,26 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
     double* U = sm;                // u^n                 [NV][B]
     double* ACC = U + NV * B;      // RK accumulator      [NV][B]
     double* X = ACC + NV * B;      // stage argument      [NV][B]
-    double* G = X + NV * B;        // derived             [ND][W2]
-    double* HS = G + ND * W2;      // halo levels         [2H(q+1)][ND]
+    double* G2 = X + NV * B;       // derived, by stage parity [2][ND][W2]
+    double* HS = G2 + 2 * ND * W2; // halo levels         [2H(q+1)][ND]
     double* E = HS + 2 * H * (AT_QMAX + 1) * ND;  // exp(-Ea/T) of own points [B]
-    __shared__ int s_abort;
+    __shared__ long long s_abort_at;  // first stage whose halo could not be formed
     __shared__ int s_k[2];
+    __shared__ int s_fail;
     const int nw = (a.mode == AT) ? a.q + 1 : 1;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int hwarp = (int)(blockDim.x >> 5) - 1;  // the halo warp
     const int nwork = hwarp * 32;                    // threads of the worker warps
-    // warps per role in phase A: enough for one point per lane, at most half the workers
+    const int nall = nwork + 32;
+    // warps per role in phase A: enough for one point per lane
     int bw = (B + 31) / 32;
     if (bw > hwarp) bw = hwarp;
     if (bw < 1) bw = 1;
     // Roles of the worker warps in phase A.  Warp w runs on SM sub-partition
     // w % 4 and the halo warp on hwarp % 4 (sub-partition 0 with 8 workers).
-    // The derive warps also form the Arrhenius factor of their points from
-    // the temperature they just derived; they start at warp 1, so that two of
-    // them (a 64-point PE) take sub-partitions 1 and 2, away from the halo warp.
+    // The derive warps start at warp 1, so that two of them (a 64-point PE)
+    // take sub-partitions 1 and 2, away from the halo warp.
     int derive_rank = -1;
     if (warp < hwarp) {
         const int r = (warp + hwarp - 1) % hwarp;  // warp 1 -> rank 0, warp 2 -> rank 1, ...
@@ -165,79 +204,112 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
         U[i] = x;
         X[i] = x;
     }
-    if (threadIdx.x == 0) s_abort = 0;
+    if (threadIdx.x == 0) s_abort_at = 0x7fffffffffffffffLL;
     int bad = 0;
     __syncthreads();
+    const int64_t T = nsteps * S;
 
-    for (int64_t n = level0; n < level0 + nsteps; ++n) {
-        for (int s = 0; s < S; ++s) {
+    if (warp == hwarp) {
+        // ---- the halo warp: stage t's buffer values, one stage ahead ----
+        int64_t n = level0;
+        int s = 0;
+        for (int64_t t = 0; t < T; ++t) {
+            const int p = (int)(t & 1);
+            double* G = G2 + p * ND * W2;
             const bool last = (s == S - 1);
-            // the stage argument this stage produces: (level Ln, stage sn) = index n S + s + 1
+            const int64_t Ln = last ? n + 1 : n;  // the stage argument stage t produces: (Ln, sn)
+            const int sn = last ? 0 : s + 1;
+            if (t >= 2) bar_sync_p<3>(p, nall);  // the workers are done with G[p] (stage t - 2)
+            if (lane == 0) s_fail = 0;
+            __syncwarp();
+            if (lane < 2) {
+                const int side = lane;
+                int k;
+                bool ok;
+                // one bounded wait for both conditions on the neighbour's
+                // progress: the stage-s argument this stage reads has been
+                // published, and the ring slot of (Ln, sn) this stage writes is
+                // no longer read by it
+                const int64_t free_at = (Ln - a.slack - 1) * S + sn + 1;
+                if (a.arrival) {
+                    // the freshest stage-s argument of the neighbour that has
+                    // arrived, once one recent enough for the clamp is there
+                    const int kc = kcap_at(a, n);
+                    const int64_t need = (n - kc) * S + s;
+                    ok = wait_ge(a, a.done + nbr[side], need > free_at ? need : free_at);
+                    const int64_t m = (load_acquire(a.done + nbr[side]) - s) / S;
+                    k = m >= n ? 0 : (int)(n - m);
+                    if (k > kc) k = kc;  // only if the wait gave up
+                } else {
+                    // the neighbour's stage-s argument at the drawn level n-k
+                    k = keff_at(a, n, s, pe, side);
+                    const int64_t need = (n - k) * S + s;
+                    ok = wait_ge(a, a.done + nbr[side], need > free_at ? need : free_at);
+                }
+                s_k[side] = k;
+                log_delay(a, n, s, pe, side, k);
+                if (!ok) s_fail = 1;
+            }
+            __syncwarp();
+            const bool failed = *(volatile int*)&s_fail != 0;
+            if (!failed) {
+                const int tt = lane;
+                if (tt < 2 * H * nw) {
+                    const int hp = tt / nw, l = tt - hp * nw;
+                    const int side = hp < H ? 0 : 1;
+                    const int h = side == 0 ? hp : hp - H;
+                    const int k = s_k[side];
+                    double g[ND];
+                    double Q[NV];
+                    if ((a.wnz[k] >> l) & 1) {
+                        const int64_t base = ring_index(a, n - k - l, s, nbr[side], 1 - side, h, 0);
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) Q[v] = __ldcg(a.ring + base + v);
+                        P::derive(a, Q, g);
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) HS[tt * ND + d] = g[d];
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) HS[tt * ND + d] = 0.0;
+                    }
+                }
+                __syncwarp();
+                // weighted sum over levels, in level order: lanes (buffer point, quantity)
+                for (int c = lane; c < 2 * H * ND; c += 32) {
+                    const int hp = c / ND, d = c - hp * ND;
+                    const int k = s_k[hp < H ? 0 : 1];
+                    double acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * HS[(hp * nw) * ND + d];
+                    for (int l = 1; l < nw; ++l) acc = fma(a.w[k][l], HS[(hp * nw + l) * ND + d], acc);
+                    G[d * W2 + (hp < H ? hp : B + hp)] = acc;
+                }
+            } else if (lane == 0) {
+                s_abort_at = t;
+            }
+            __syncwarp();
+            bar_arrive_p<1>(p, nall);  // stage t's halo is ready (or the run stops at t)
+            if (failed) {
+                // the workers arrive on 3 + parity after stage t - 1 and stop at t:
+                // consume that arrival so the barrier completes
+                if (t >= 1 && t + 1 < T) bar_sync_p<3>((int)((t - 1) & 1), nall);
+                break;
+            }
+            if (++s == S) {
+                s = 0;
+                ++n;
+            }
+        }
+    } else {
+        // ---- the worker warps ----
+        int64_t n = level0;
+        int s = 0;
+        for (int64_t t = 0; t < T; ++t) {
+            const int p = (int)(t & 1);
+            double* G = G2 + p * ND * W2;
+            const bool last = (s == S - 1);
             const int64_t Ln = last ? n + 1 : n;
             const int sn = last ? 0 : s + 1;
             // (A)
-            if (warp == hwarp) {
-                if (lane < 2) {
-                    const int side = lane;
-                    int k;
-                    bool ok;
-                    // one bounded wait for both conditions on the neighbour's
-                    // progress: the stage-s argument this stage reads has been
-                    // published, and the ring slot of (Ln, sn) this stage writes is
-                    // no longer read by it
-                    const int64_t free_at = (Ln - a.slack - 1) * S + sn + 1;
-                    if (a.arrival) {
-                        // the freshest stage-s argument of the neighbour that has
-                        // arrived, once one recent enough for the clamp is there
-                        const int kc = kcap_at(a, n);
-                        const int64_t need = (n - kc) * S + s;
-                        ok = wait_ge(a, a.done + nbr[side], need > free_at ? need : free_at);
-                        const int64_t m = (load_acquire(a.done + nbr[side]) - s) / S;
-                        k = m >= n ? 0 : (int)(n - m);
-                        if (k > kc) k = kc;  // only if the wait gave up
-                    } else {
-                        // the neighbour's stage-s argument at the drawn level n-k
-                        k = keff_at(a, n, s, pe, side);
-                        const int64_t need = (n - k) * S + s;
-                        ok = wait_ge(a, a.done + nbr[side], need > free_at ? need : free_at);
-                    }
-                    s_k[side] = k;
-                    log_delay(a, n, s, pe, side, k);
-                    if (!ok) atomicExch(&s_abort, 1);
-                }
-                __syncwarp();
-                if (!*(volatile int*)&s_abort) {
-                    const int t = lane;
-                    if (t < 2 * H * nw) {
-                        const int hp = t / nw, l = t - hp * nw;
-                        const int side = hp < H ? 0 : 1;
-                        const int h = side == 0 ? hp : hp - H;
-                        const int k = s_k[side];
-                        double g[ND];
-                        double Q[NV];
-                        if ((a.wnz[k] >> l) & 1) {
-                            const int64_t base = ring_index(a, n - k - l, s, nbr[side], 1 - side, h, 0);
-#pragma unroll
-                            for (int v = 0; v < NV; ++v) Q[v] = __ldcg(a.ring + base + v);
-                            P::derive(a, Q, g);
-#pragma unroll
-                            for (int d = 0; d < ND; ++d) HS[t * ND + d] = g[d];
-                        } else {
-#pragma unroll
-                            for (int d = 0; d < ND; ++d) HS[t * ND + d] = 0.0;
-                        }
-                    }
-                    __syncwarp();
-                    // weighted sum over levels, in level order: lanes (buffer point, quantity)
-                    for (int c = lane; c < 2 * H * ND; c += 32) {
-                        const int hp = c / ND, d = c - hp * ND;
-                        const int k = s_k[hp < H ? 0 : 1];
-                        double acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * HS[(hp * nw) * ND + d];
-                        for (int l = 1; l < nw; ++l) acc = fma(a.w[k][l], HS[(hp * nw + l) * ND + d], acc);
-                        G[d * W2 + (hp < H ? hp : B + hp)] = acc;
-                    }
-                }
-            } else if (derive_rank >= 0) {
+            if (derive_rank >= 0) {
                 for (int it = derive_rank * 32 + lane; it < B; it += bw * 32) {
                     double g[ND];
                     double Q[NV];
@@ -249,37 +321,38 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                     if constexpr (PDE == RNS) E[it] = at_exp(-a.prm[5] * at_rcp(g[7]));  // g[7] = T
                 }
             }
-            __syncthreads();
-            if (s_abort) goto out;
-
+            bar_sync_p<1>(p, nall);  // own derived quantities and stage t's halo in G[p]
+            if (t >= *(volatile long long*)&s_abort_at) break;
             // (C)
-            if (warp < hwarp) {
-                for (int it = threadIdx.x; it < NV * B; it += nwork) {
-                    const int v = it / B;
-                    const int jl = it - v * B;
-                    const double y = point_update<PDE, H>(a, s, v, jl, G, E, X, U, ACC, W2, B, last);
-                    if (nonfinite(y)) bad = 1;
-                    int side = -1, h = 0;
-                    if (jl < H) {
-                        side = 0;
-                        h = jl;
-                    } else if (jl >= B - H) {
-                        side = 1;
-                        h = jl - (B - H);
-                    }
-                    if (side >= 0) __stcg(a.ring + ring_index(a, Ln, sn, pe, side, h, v), y);
+            for (int it = threadIdx.x; it < NV * B; it += nwork) {
+                const int v = it / B;
+                const int jl = it - v * B;
+                const double y = point_update<PDE, H>(a, s, v, jl, G, E, X, U, ACC, W2, B, last);
+                if (nonfinite(y)) bad = 1;
+                int side = -1, h = 0;
+                if (jl < H) {
+                    side = 0;
+                    h = jl;
+                } else if (jl >= B - H) {
+                    side = 1;
+                    h = jl - (B - H);
                 }
+                if (side >= 0) __stcg(a.ring + ring_index(a, Ln, sn, pe, side, h, v), y);
             }
-            __syncthreads();
-            // publish: the barrier orders every thread's ring writes before thread
+            bar_sync<5>(nwork);
+            // publish: the barrier orders every worker's ring writes before thread
             // 0's device-scope fence and release store (both cumulative)
             if (threadIdx.x == 0 && pe != a.withhold_pe) {
                 __threadfence();
                 store_release(a.done + pe, n * S + s + 1);
             }
+            if (t + 2 < T) bar_arrive_p<3>(p, nall);  // G[p] may be refilled for stage t + 2
+            if (++s == S) {
+                s = 0;
+                ++n;
+            }
         }
     }
-out:
     __syncthreads();
     for (int i = threadIdx.x; i < NV * B; i += blockDim.x) {
         const int v = i / B, j = i - v * B;
@@ -327,7 +400,7 @@ size_t atk_persist_smem_bytes(int pde, int B, int H)
 {
     const int nv = pde == atk::RNS ? 4 : 1, nd = pde == atk::RNS ? 8 : 1;
     return sizeof(double) *
-           ((size_t)3 * nv * B + (size_t)nd * (B + 2 * H) + (size_t)2 * H * (AT_QMAX + 1) * nd + (size_t)B);
+           ((size_t)3 * nv * B + (size_t)2 * nd * (B + 2 * H) + (size_t)2 * H * (AT_QMAX + 1) * nd + (size_t)B);
 }
 
 // worker warps for the PE's points (at least two roles' worth for phase A)

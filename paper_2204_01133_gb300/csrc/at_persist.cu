@@ -341,11 +341,8 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
             }
             bar_sync<5>(nwork);
             // publish: the barrier orders every worker's ring writes before thread
-            // 0's device-scope fence and release store (both cumulative)
-            if (threadIdx.x == 0 && pe != a.withhold_pe) {
-                __threadfence();
-                store_release(a.done + pe, n * S + s + 1);
-            }
+            // 0's device-scope release store, which is cumulative
+            if (threadIdx.x == 0 && pe != a.withhold_pe) store_release(a.done + pe, n * S + s + 1);
             if (t + 2 < T) bar_arrive_p<3>(p, nall);  // G[p] may be refilled for stage t + 2
             if (++s == S) {
                 s = 0;

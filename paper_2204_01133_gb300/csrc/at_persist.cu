@@ -323,10 +323,14 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
             }
             bar_sync_p<1>(p, nall);  // own derived quantities and stage t's halo in G[p]
             if (t >= *(volatile long long*)&s_abort_at) break;
-            // (C)
+            // (C) item (v, jl).  With one warp per 32 points of a variable, warp w
+            // takes variable w % NV: the two warps of the density equation (first
+            // derivatives only, the lightest) then share sub-partition 0 with the
+            // halo warp, which is on the critical path when a drawn delay is 0.
+            const bool by_warp = (nwork == NV * B) && (B % 32 == 0);
             for (int it = threadIdx.x; it < NV * B; it += nwork) {
-                const int v = it / B;
-                const int jl = it - v * B;
+                const int v = by_warp ? warp % NV : it / B;
+                const int jl = by_warp ? (warp / NV) * 32 + lane : it - v * B;
                 const double y = point_update<PDE, H>(a, s, v, jl, G, E, X, U, ACC, W2, B, last);
                 if (nonfinite(y)) bad = 1;
                 int side = -1, h = 0;

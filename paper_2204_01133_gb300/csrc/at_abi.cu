@@ -42,6 +42,9 @@ static const int kRingSlack = 2;
 // Levels stay below 2^31 so that the kernels take ring slots with 32-bit
 // arithmetic (a solve of more steps is refused).
 static const int64_t kMaxLevel = ((int64_t)1 << 31) - 2;
+// the persistent path holds one CTA per PE on the GPU at once; its
+// workspace (ring of derived quantities) is laid out for at most this many
+static const int64_t kPersistMaxPE = 4096;
 
 namespace {
 
@@ -66,8 +69,8 @@ struct Layout {
     int nvar, H, q, S, R;
     int64_t P;
     int Tw, wpp;
-    size_t off_A, off_B, off_acc, off_ring, off_dlog, off_status, off_done, total;
-    size_t ring_elems;
+    size_t off_A, off_B, off_acc, off_ring, off_dlog, off_status, off_done, off_gring, total;
+    size_t ring_elems, gring_elems;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -154,6 +157,13 @@ Layout layout(const at_problem* pb, const at_delays* dl)
     off = align256(off + 256);
     L.off_done = off;    // per-PE progress counters of the persistent path
     off = align256(off + sizeof(int64_t) * (size_t)L.P);
+    // the persistent path's ring of derived quantities of the edge windows
+    // (central PDEs with few enough PEs to take that path)
+    L.gring_elems = 0;
+    if ((pb->pde == AT_ADVDIFF || pb->pde == AT_RNS) && L.P <= kPersistMaxPE)
+        L.gring_elems = (size_t)L.R * L.S * L.P * 2 * L.H * (pb->pde == AT_RNS ? 8 : 1);
+    L.off_gring = off;
+    off = align256(off + sizeof(double) * L.gring_elems);
     L.total = off;
     return L;
 }
@@ -210,6 +220,7 @@ atk::StageArgs build_args(const at_problem* pb, const at_delays* dl, const Layou
     a.status = (int*)(ws + L.off_status);
     a.abort_flag = (int*)(ws + L.off_status + sizeof(int));
     a.done = (int64_t*)(ws + L.off_done);
+    a.gring = L.gring_elems ? (double*)(ws + L.off_gring) : nullptr;
     a.wait_limit = (int64_t)4000000;
     a.withhold_pe = (int64_t)-1;
     a.slack = kRingSlack;
@@ -447,6 +458,7 @@ int at_set_delays(at_ctx* c, const at_delays* dl)
     c->persist_cap = (c->pb.pde == AT_ADVDIFF || c->pb.pde == AT_RNS)
                          ? atk_persist_capacity(c->pb.pde, c->pb.order, c->pb.pe_size, c->device)
                          : 0;
+    if (c->persist_cap > kPersistMaxPE) c->persist_cap = kPersistMaxPE;
     cudaGetLastError();  // an unavailable persistent path is not an error
     c->have_delays = true;
     g_err[0] = 0;

@@ -47,6 +47,7 @@ struct StageArgs {
     double k0, k1, k2, k3;                    // derived physics constants
     // persistent path only
     int64_t* done;       // per PE: stages completed, as the index n*S + s + 1 [P]
+    double* gring;       // derived quantities of the edge windows [R][S][P][2][H][ND]
     int* abort_flag;     // set by the first wait that runs out
     int64_t wait_limit;  // polls before a wait gives up (bounded spin)
     int64_t withhold_pe; // fault injection: this PE never publishes (-1: none)
@@ -185,6 +186,14 @@ __device__ __forceinline__ int64_t ring_index(const StageArgs& a, int64_t level,
 {
     const int64_t r = (int64_t)((uint32_t)level % (uint32_t)a.R);
     return ((((r * a.S + stage) * a.P + pe) * 2 + side) * a.H + h) * a.nvar + v;
+}
+
+// the same slot in the ring of derived quantities (nd per point)
+__device__ __forceinline__ int64_t gring_index(const StageArgs& a, int64_t level, int stage, int64_t pe, int side,
+                                               int h, int nd)
+{
+    const int64_t r = (int64_t)((uint32_t)level % (uint32_t)a.R);
+    return ((((r * a.S + stage) * a.P + pe) * 2 + side) * a.H + h) * nd;
 }
 
 // ---------------------------------------------------------------------------

@@ -146,11 +146,15 @@ __device__ __forceinline__ void bar_arrive_p(int p, int count)
 //   (C) all worker warps: stencil, source and RK update of every (point,
 //       variable), one variable per warp, the edge points straight into the
 //       ring; then the progress counter is published.
-// The halo warp runs one stage ahead of the workers: while they do stage t
-// it takes the delays of stage t + 1, waits (boundedly) for the
-// neighbours' data, fetches the delayed levels from the ring and writes the
+// After a stage, warp 0 derives the new stage argument at the PE's 2H edge
+// points into a ring of derived quantities and publishes the stage.  The
+// halo warp runs one stage ahead of the workers: while they do stage t it
+// takes the delays of stage t + 1, waits (boundedly) for the neighbours'
+// data, reads their derived quantities of the delayed levels and writes the
 // weighted buffer values into the halo columns of G[(t + 1) % 2], so that
-// its latency hides behind the workers' arithmetic.  Named barriers, by
+// its latency hides behind the workers' arithmetic (a drawn delay of 0
+// then costs the neighbour's edge derivation, not a derivation under the
+// contention of the receiving SM).  Named barriers, by
 // the parity p of the stage:
 //   1 + p  halo of stage t ready      (halo warp arrives, workers sync)
 //   3 + p  G[p] no longer read        (workers arrive after stage t, the
@@ -206,7 +210,21 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
     }
     if (threadIdx.x == 0) s_abort_at = 0x7fffffffffffffffLL;
     int bad = 0;
+    // this PE's ring of derived quantities of its edge windows, from its ring
+    // of stage arguments (steps before this launch may have run elsewhere);
+    // the neighbours read it only after the release below
+    for (int i = threadIdx.x; i < a.R * S * 2 * H; i += blockDim.x) {
+        const int h = i % H, side = (i / H) % 2, st = (i / (2 * H)) % S, r = i / (2 * H * S);
+        double Q[NV], g[ND];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Q[v] = a.ring[ring_index(a, r, st, pe, side, h, v)];
+        P::derive(a, Q, g);
+        const int64_t gi = gring_index(a, r, st, pe, side, h, ND);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) a.gring[gi + d] = g[d];
+    }
     __syncthreads();
+    if (threadIdx.x == 0 && pe != a.withhold_pe) store_release(a.done + pe, level0 * S);
     const int64_t T = nsteps * S;
 
     if (warp == hwarp) {
@@ -259,15 +277,11 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                     const int side = hp < H ? 0 : 1;
                     const int h = side == 0 ? hp : hp - H;
                     const int k = s_k[side];
-                    double g[ND];
-                    double Q[NV];
                     if ((a.wnz[k] >> l) & 1) {
-                        const int64_t base = ring_index(a, n - k - l, s, nbr[side], 1 - side, h, 0);
+                        // the neighbour's own derived quantities of that level
+                        const int64_t gi = gring_index(a, n - k - l, s, nbr[side], 1 - side, h, ND);
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) Q[v] = __ldcg(a.ring + base + v);
-                        P::derive(a, Q, g);
-#pragma unroll
-                        for (int d = 0; d < ND; ++d) HS[tt * ND + d] = g[d];
+                        for (int d = 0; d < ND; ++d) HS[tt * ND + d] = __ldcg(a.gring + gi + d);
                     } else {
 #pragma unroll
                         for (int d = 0; d < ND; ++d) HS[tt * ND + d] = 0.0;
@@ -344,9 +358,26 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                 if (side >= 0) __stcg(a.ring + ring_index(a, Ln, sn, pe, side, h, v), y);
             }
             bar_sync<5>(nwork);
-            // publish: the barrier orders every worker's ring writes before thread
-            // 0's device-scope release store, which is cumulative
-            if (threadIdx.x == 0 && pe != a.withhold_pe) store_release(a.done + pe, n * S + s + 1);
+            // the derived quantities of the new stage argument at the edge
+            // points, for the neighbours' halos; then publish: the barriers
+            // order every worker's ring writes before lane 0's device-scope
+            // release store, which is cumulative
+            if (warp == 0) {
+                if (lane < 2 * H) {
+                    const int side = lane < H ? 0 : 1;
+                    const int h = lane - side * H;
+                    const int jl = side == 0 ? h : B - H + h;
+                    double Q[NV], g[ND];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) Q[v] = X[v * B + jl];
+                    P::derive(a, Q, g);
+                    const int64_t gi = gring_index(a, Ln, sn, pe, side, h, ND);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) __stcg(a.gring + gi + d, g[d]);
+                }
+                __syncwarp();
+                if (lane == 0 && pe != a.withhold_pe) store_release(a.done + pe, n * S + s + 1);
+            }
             if (t + 2 < T) bar_arrive_p<3>(p, nall);  // G[p] may be refilled for stage t + 2
             if (++s == S) {
                 s = 0;
@@ -440,7 +471,7 @@ cudaError_t atk_launch_persist(const atk::StageArgs& a, int pde, int order, int6
     void* fn = persist_kernel(pde, order);
     if (!fn) return cudaErrorInvalidValue;
     atk::counters_set<<<(unsigned)((a.P + 255) / 256 < 1024 ? (a.P + 255) / 256 : 1024), 256, 0, st>>>(
-        a.done, a.P, level0 * a.S, a.abort_flag);
+        a.done, a.P, (level0 - a.R) * a.S, a.abort_flag);  // raised to level0 S by each PE's prologue
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = atk_persist_smem_bytes(pde, a.B, order / 2);

@@ -58,7 +58,7 @@ NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal, at 2070 M
 # share of the FP64 roof the kernel's own arithmetic uses.
 FLOPS_PER_POINT_STAGE = {
     ("rns", "stage"): 176.3,         # central6 + AT6, 4 variables (RK4 stage 1 counted)
-    ("rns", "persistent"): 178.7,    # same work, all K steps of one launch
+    ("rns", "persistent"): 179.9,    # same work, all K steps of one launch
     ("detonation", "stage"): 796.9,  # WENO5 + AT-WENO5, 8 reconstructions per edge (RK3 stage 0)
     ("advdiff", "stage"): 13.56,     # 5-tap merged stencil + RK4 update, mean of the 4 stages
     ("advdiff", "persistent"): 13.56,
@@ -70,7 +70,7 @@ BYTES_PER_POINT_STAGE = {"rns": 17 * 4 * 8 / 4, "detonation": 8 * 4 * 8 / 3, "ad
 # dram__bytes_write.sum) from the ncu captures of the current kernels; the
 # advection-diffusion kernel was captured at N = 2^25 and is scaled by 4.
 TRAFFIC_PER_LAUNCH = {
-    "rns-flame-n16384": 1.2053e6,  # persistent launch: the state is read once, writes stay in L2
+    "rns-flame-n16384": 2.5390e6,  # persistent launch: state and rings read once, writes stay in L2
     "rns-flame-n16777216": 1.6618e9 + 1.0869e9,
     "detonation-n16777216": 5.4581e8 + 4.9380e8,
     "advdiff-n134217728": 4 * (8.7079e8 + 5.1163e8),

@@ -83,8 +83,10 @@ enum { AT_READ_STATE = 0, AT_READ_DELAYS = 1, AT_READ_RING = 2, AT_READ_STATS = 
  * kernel per RK stage; AT_PATH_PERSISTENT runs all steps of an at_step call
  * in one cooperative launch with one CTA per PE that synchronises only with
  * its two neighbours (central PDEs, up to as many PEs as the GPU holds at
- * once); AT_PATH_AUTO (default) takes the persistent path when it can.  Both
- * paths compute the same values in the same order.                          */
+ * once; advection-diffusion on at most 64 PEs of 32..256 points runs instead
+ * in one thread-block cluster of up to 16 CTAs with its ring in distributed
+ * shared memory); AT_PATH_AUTO (default) takes the persistent path when it
+ * can.  All paths compute the same values in the same order.               */
 enum { AT_PATH_AUTO = 0, AT_PATH_STAGE = 1, AT_PATH_PERSISTENT = 2 };
 /* at_set_option keys */
 enum {

@@ -24,6 +24,9 @@ cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaSt
 cudaError_t atk_launch_ring_seed(const atk::StageArgs& a, cudaStream_t st);
 cudaError_t atk_set_smem_limits();
 int64_t atk_persist_capacity(int pde, int order, int B, int device);
+int atk_cluster_size(int pde, int order, int B, int64_t P, int R, int S, int device);
+cudaError_t atk_launch_cluster(const atk::StageArgs& a, int order, int csize, int64_t level0, int64_t nsteps,
+                               cudaStream_t st);
 cudaError_t atk_launch_persist(const atk::StageArgs& a, int pde, int order, int64_t level0, int64_t nsteps,
                                cudaStream_t st);
 int atk_batch_variant(int pde, int order);
@@ -309,6 +312,7 @@ struct at_ctx {
     int path = AT_PATH_AUTO;       // at_set_option(AT_OPT_PATH)
     int last_path = 0;             // path of the last at_step
     int64_t persist_cap = 0;       // PEs one cooperative launch can hold (0: unavailable)
+    int cluster_c = 0;             // CTAs of the one-cluster kernel for this problem (0: not used)
     int64_t wait_limit = 4000000;  // polls of a bounded wait
     int64_t withhold_pe = -1;
     int arrival = 0;               // at_set_option(AT_OPT_ARRIVAL)
@@ -459,6 +463,9 @@ int at_set_delays(at_ctx* c, const at_delays* dl)
                          ? atk_persist_capacity(c->pb.pde, c->pb.order, c->pb.pe_size, c->device)
                          : 0;
     if (c->persist_cap > kPersistMaxPE) c->persist_cap = kPersistMaxPE;
+    c->cluster_c = c->pb.pde == AT_ADVDIFF
+                       ? atk_cluster_size(c->pb.pde, c->pb.order, c->pb.pe_size, L.P, L.R, L.S, c->device)
+                       : 0;
     cudaGetLastError();  // an unavailable persistent path is not an error
     c->have_delays = true;
     g_err[0] = 0;
@@ -499,12 +506,17 @@ int at_step(at_ctx* c, int64_t nsteps)
         a.wait_limit = c->wait_limit;
         a.withhold_pe = c->withhold_pe;
         a.arrival = c->arrival;
+        // a small advection-diffusion problem runs in one thread-block cluster
+        // (Philox delays only; fault injection needs the neighbour waits)
+        const bool cluster = c->cluster_c > 0 && !c->arrival && c->withhold_pe < 0;
         e = record(c, true);
-        if (e == cudaSuccess) e = atk_launch_persist(a, c->pb.pde, c->pb.order, c->level, nsteps, c->stream);
+        if (e == cudaSuccess)
+            e = cluster ? atk_launch_cluster(a, c->pb.order, c->cluster_c, c->level, nsteps, c->stream)
+                        : atk_launch_persist(a, c->pb.pde, c->pb.order, c->level, nsteps, c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
         e = record(c, false);
         if (e != cudaSuccess) return cuda_fail(e, "profiling event");
-        c->launched += 2;  // counter reset + the persistent kernel
+        c->launched += cluster ? 1 : 2;  // (counter reset +) the kernel
         c->level += nsteps;
         g_err[0] = 0;
         return AT_OK;

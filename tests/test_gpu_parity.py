@@ -331,6 +331,37 @@ def test_persistent_equals_per_stage_bitwise(maker):
     assert np.array_equal(a_state, c_state) and np.array_equal(a_del, c_del)
 
 
+@pytest.mark.parametrize("pe_size,pes,order,mode,rk", [
+    (64, 32, 4, "at", "rk4"), (32, 5, 6, "at", "rk4"), (128, 12, 2, "as", "rk3tvd"), (256, 3, 4, "at", "rk2"),
+    (64, 64, 4, "sync", "rk4"), (32, 1, 4, "at", "rk4"), (64, 48, 6, "as", "rk4")])
+def test_cluster_kernel_equals_per_stage_bitwise(pe_size, pes, order, mode, rk):
+    """Advection-diffusion on at most 64 PEs of 32..256 points takes the
+    one-cluster kernel on the persistent path (ring in distributed shared
+    memory, one cluster barrier per stage): bit for bit the per-stage
+    result, also over split runs, and within the run bound of the oracle."""
+    cfl = 0.01 if order == 6 else 0.05
+    pb, u0 = W.advdiff(n=pe_size * pes, pe_size=pe_size, order=order, mode=mode, k_max=3, seed=6, cfl=cfl, rk=rk)
+    a_state, a_del = _run(pb, u0, [150], "stage")
+    b_state, b_del = _run(pb, u0, [37, 1, 112], "persistent")
+    assert np.array_equal(a_state, b_state) and np.array_equal(a_del, b_del)
+    parity(pb, u0, 150, path="persistent")
+
+
+def test_cluster_kernel_and_per_stage_alternate():
+    """Switching between the one-cluster kernel and per-stage launches
+    mid-run: the history ring is handed over through global memory."""
+    from paper_2204_01133_gb300.api import Solver
+    pb, u0 = W.advdiff(n=2048, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075)
+    ref, _ = _run(pb, u0, [300], "stage")
+    s = Solver(pb, u0, path="persistent")
+    s.run(100)
+    s.set_path("stage")
+    s.run(50)
+    s.set_path("persistent")
+    s.run(150)
+    assert np.array_equal(s.read_state(), ref)
+
+
 def test_persistent_after_per_stage_steps():
     from paper_2204_01133_gb300.api import Solver
     pb, u0 = W.rns(case="flame", n=16384, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003)

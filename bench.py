@@ -78,11 +78,11 @@ TRAFFIC_PER_LAUNCH = {
 }
 
 
-def kernel_label(kind, path, pb):
+def kernel_label(kind, path, pb, arrival=False):
     """The kernel the library runs for this workload and path (the same rule
     as the library: small advection-diffusion problems take the one-cluster
     kernel on the persistent path)."""
-    if path == "persistent" and kind == "advdiff" and pb["pe_size"] in (32, 64, 128, 256):
+    if path == "persistent" and kind == "advdiff" and not arrival and pb["pe_size"] in (32, 64, 128, 256):
         P = pb["n"] // pb["pe_size"]
         if any(P % c == 0 and P // c <= 4 for c in range(min(P, 16), 0, -1)):
             return "cluster_advdiff"
@@ -469,6 +469,8 @@ def run_ours(args):
     state_bytes = 8 * nvar * n
 
     s = api.Solver(pb, init, device=local, path=args.path)
+    if args.arrival:  # delays by arrival order (persistent path): not reproducible, reported beside
+        s.set_option(api.OPT_ARRIVAL, 1)
     l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     flush = state_bytes < (512 << 20)
     for _ in range(max(args.warmup, 3)):
@@ -528,7 +530,7 @@ def run_ours(args):
         achieved = fl / (launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
-                "kernel": kernel_label(kind, path, pb),
+                "kernel": kernel_label(kind, path, pb, args.arrival),
                 "avg_launch_ms": launch_ms, "launches_timed": int(st.launches_timed),
                 "flops_per_launch": fl, "peak_kind": "nominal FP64 (1.25 TFLOP/s); see peak_measured",
                 "peak_measured": peak_meas, "frac_of_measured": (achieved / peak_meas) if peak_meas else None}
@@ -543,6 +545,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(describe(args.workload, pb), path=path,
+                           delays="arrival order (not reproducible)" if args.arrival else "Philox draws",
                            l2="flushed before the timed region (K steps in one at_step call)" if flush
                            else "inputs larger than L2", parallelism="replicas" if world > 1 else "single"),
             "roofline": roof,
@@ -574,6 +577,8 @@ def main():
     ap.add_argument("--serve-chunk", type=int, default=50, help="steps per serving tick")
     ap.add_argument("--path", default="auto", choices=["auto", "stage", "persistent"],
                     help="execution path of the library (auto: persistent when the PEs fit on the GPU)")
+    ap.add_argument("--arrival", action="store_true",
+                    help="delays by arrival order instead of Philox draws (persistent path, not reproducible)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

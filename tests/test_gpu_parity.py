@@ -333,12 +333,14 @@ def test_persistent_equals_per_stage_bitwise(maker):
 
 @pytest.mark.parametrize("pe_size,pes,order,mode,rk", [
     (64, 32, 4, "at", "rk4"), (32, 5, 6, "at", "rk4"), (128, 12, 2, "as", "rk3tvd"), (256, 3, 4, "at", "rk2"),
-    (64, 64, 4, "sync", "rk4"), (32, 1, 4, "at", "rk4"), (64, 48, 6, "as", "rk4")])
+    (64, 64, 4, "sync", "rk4"), (32, 1, 4, "at", "rk4"), (64, 48, 6, "as", "rk4"), (128, 32, 6, "at", "rk4"),
+    (256, 32, 2, "at", "rk3tvd"), (128, 16, 4, "at", "rk2"), (256, 16, 6, "at", "rk4")])
 def test_cluster_kernel_equals_per_stage_bitwise(pe_size, pes, order, mode, rk):
     """Advection-diffusion on at most 64 PEs of 32..256 points takes the
     one-cluster kernel on the persistent path (ring in distributed shared
-    memory, one cluster barrier per stage): bit for bit the per-stage
-    result, also over split runs, and within the run bound of the oracle."""
+    memory, one cluster barrier per stage; 1 to 4 PEs per CTA, 1 to 8
+    warps per PE): bit for bit the per-stage result, also over split runs,
+    and within the run bound of the oracle."""
     cfl = 0.01 if order == 6 else 0.05
     pb, u0 = W.advdiff(n=pe_size * pes, pe_size=pe_size, order=order, mode=mode, k_max=3, seed=6, cfl=cfl, rk=rk)
     a_state, a_del = _run(pb, u0, [150], "stage")

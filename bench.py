@@ -62,19 +62,23 @@ FLOPS_PER_POINT_STAGE = {
     ("detonation", "stage"): 796.9,  # WENO5 + AT-WENO5, 8 reconstructions per edge (RK3 stage 0)
     ("advdiff", "stage"): 13.56,     # 5-tap merged stencil + RK4 update, mean of the 4 stages
     ("advdiff", "persistent"): 13.56,
+    ("advdiff", "fused"): 13.56,     # the method's work only: the recomputed outer edge points are not counted
 }
 # Algorithmic HBM bytes per point per stage of the per-stage path: the arrays
 # a step reads and writes (RK4: 17 arrays, RK3-TVD: 8) x nvar x 8 B / stages.
 BYTES_PER_POINT_STAGE = {"rns": 17 * 4 * 8 / 4, "detonation": 8 * 4 * 8 / 3, "advdiff": 17 * 8 / 4}
+# the step-fused path reads u^n and writes u^{n+1} once per step (+ the ring)
+BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4}
 # DRAM bytes per launch of the timed kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum) from the ncu captures of the current kernels; the
-# advection-diffusion kernel was captured at N = 2^25 and is scaled by 4.
+# dram__bytes_write.sum) from the ncu captures of the current kernels, by
+# workload and path; the advection-diffusion kernel was captured at N = 2^25
+# and is scaled by 4.
 TRAFFIC_PER_LAUNCH = {
-    "rns-flame-n16384": 2.5390e6,  # persistent launch: state and rings read once, writes stay in L2
-    "rns-flame-n16777216": 1.6618e9 + 1.0869e9,
-    "detonation-n16777216": 5.4581e8 + 4.9380e8,
-    "advdiff-n134217728": 4 * (8.7079e8 + 5.1163e8),
-    "advdiff-n33554432": 8.7079e8 + 5.1163e8,
+    ("rns-flame-n16384", "persistent"): 2.5390e6,  # state and rings read once, writes stay in L2
+    ("rns-flame-n16777216", "stage"): 1.6618e9 + 1.0869e9,
+    ("detonation-n16777216", "stage"): 5.4581e8 + 4.9380e8,
+    ("advdiff-n134217728", "stage"): 4 * (8.7079e8 + 5.1163e8),
+    ("advdiff-n33554432", "stage"): 8.7079e8 + 5.1163e8,
 }
 
 
@@ -82,6 +86,8 @@ def kernel_label(kind, path, pb, arrival=False):
     """The kernel the library runs for this workload and path (the same rule
     as the library: small advection-diffusion problems take the one-cluster
     kernel on the persistent path)."""
+    if path == "fused":
+        return "step_fused_" + kind
     if path == "persistent" and kind == "advdiff" and not arrival and pb["pe_size"] in (32, 64, 128, 256):
         P = pb["n"] // pb["pe_size"]
         if any(P % c == 0 and P // c <= 4 for c in range(min(P, 16), 0, -1)):
@@ -502,9 +508,10 @@ def run_ours(args):
     s.profile(False)
     clk = clocks.stop()
     launches = st.kernels_launched - launched0
-    path = {1: "stage", 2: "persistent"}.get(st.path, "?")
+    path = {1: "stage", 2: "persistent", 3: "fused"}.get(st.path, "?")
     launch_ms = st.stage_ms / max(st.launches_timed, 1)
-    units_per_launch = n * (S * args.steps if path == "persistent" else 1)  # point-stages per launch
+    # point-stages per launch: all K steps (persistent), one step (fused), one stage
+    units_per_launch = n * (S * args.steps if path == "persistent" else S if path == "fused" else 1)
     from paper_2204_01133_gb300 import shard
     ms = shard.max_over_ranks(ms)
     value = world * n * args.steps / (ms * 1e-3)
@@ -529,16 +536,17 @@ def run_ours(args):
         fl = FLOPS_PER_POINT_STAGE[(kind, path)] * units_per_launch  # per launch
         achieved = fl / (launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
+                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, path)),
                 "kernel": kernel_label(kind, path, pb, args.arrival),
                 "avg_launch_ms": launch_ms, "launches_timed": int(st.launches_timed),
                 "flops_per_launch": fl, "peak_kind": "nominal FP64 (1.25 TFLOP/s); see peak_measured",
                 "peak_measured": peak_meas, "frac_of_measured": (achieved / peak_meas) if peak_meas else None}
-        if path == "stage":  # HBM share of the per-stage path (the persistent path keeps the state on chip)
+        if path in ("stage", "fused"):  # HBM share (the persistent path keeps the state on chip)
             hbm_peak = measured_hbm_gbs()
-            gbs = BYTES_PER_POINT_STAGE[kind] * units_per_launch / (launch_ms * 1e-3) / 1e9
+            bpps = (BYTES_PER_POINT_STAGE if path == "stage" else BYTES_PER_POINT_STAGE_FUSED)[kind]
+            gbs = bpps * units_per_launch / (launch_ms * 1e-3) / 1e9
             roof["hbm"] = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                           "bytes_per_launch": BYTES_PER_POINT_STAGE[kind] * units_per_launch,
+                           "bytes_per_launch": bpps * units_per_launch,
                            "peak_kind": "measured copy bandwidth (MEASURED_PEAKS.json)"}
         out = {
             "metric": "grid-pt updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
@@ -575,7 +583,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=48, help="requests in the served burst (serving)")
     ap.add_argument("--serve-budget-gb", type=int, default=16, help="device-memory budget of the server (GB)")
     ap.add_argument("--serve-chunk", type=int, default=50, help="steps per serving tick")
-    ap.add_argument("--path", default="auto", choices=["auto", "stage", "persistent"],
+    ap.add_argument("--path", default="auto", choices=["auto", "stage", "persistent", "fused"],
                     help="execution path of the library (auto: persistent when the PEs fit on the GPU)")
     ap.add_argument("--arrival", action="store_true",
                     help="delays by arrival order instead of Philox draws (persistent path, not reproducible)")

@@ -85,9 +85,16 @@ enum { AT_READ_STATE = 0, AT_READ_DELAYS = 1, AT_READ_RING = 2, AT_READ_STATS = 
  * its two neighbours (central PDEs, up to as many PEs as the GPU holds at
  * once; advection-diffusion on at most 64 PEs of 32..256 points runs instead
  * in one thread-block cluster of up to 16 CTAs with its ring in distributed
- * shared memory); AT_PATH_AUTO (default) takes the persistent path when it
- * can.  All paths compute the same values in the same order.               */
-enum { AT_PATH_AUTO = 0, AT_PATH_STAGE = 1, AT_PATH_PERSISTENT = 2 };
+ * shared memory); AT_PATH_FUSED launches one kernel per step that runs all
+ * its RK stages in one pass over the state, recomputing the edge points of
+ * the neighbours beyond each CTA (advection-diffusion, PEs of 32, 64, 128 or
+ * 256 points and at least stages x halo points; AT_EINVAL from at_step
+ * otherwise; u^{n+1} goes to workspace field A and back, so an odd number of
+ * steps in one call ends with a device copy of the state); AT_PATH_AUTO
+ * (default) takes the persistent path when it can, else the fused path when
+ * it can, else the per-stage path.  All paths compute the same values in the
+ * same order.                                                              */
+enum { AT_PATH_AUTO = 0, AT_PATH_STAGE = 1, AT_PATH_PERSISTENT = 2, AT_PATH_FUSED = 3 };
 /* at_set_option keys */
 enum {
     AT_OPT_PATH = 0,        /* value: AT_PATH_*                                                  */
@@ -134,7 +141,7 @@ typedef struct {
     int32_t halo;      /* halo width H                                                */
     int32_t q;         /* temporal extrapolation degree of the AT halo                */
     int32_t ring_levels;
-    int32_t path;             /* AT_PATH_STAGE or AT_PATH_PERSISTENT: the last at_step */
+    int32_t path;             /* AT_PATH_STAGE, _PERSISTENT or _FUSED: the last at_step */
     int32_t pad_;
     int64_t kernels_launched; /* kernels enqueued by this context so far             */
     int64_t launches_timed;   /* stage kernels timed since at_profile(ctx, 1)        */

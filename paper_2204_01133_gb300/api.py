@@ -33,7 +33,7 @@ SYMBOLS = ("at_create", "at_workspace_bytes", "at_set_problem", "at_set_delays",
            "at_run_noalloc",
            "at_batch_table_bytes", "at_batch_create", "at_batch_bind", "at_batch_release", "at_batch_set_config",
            "at_batch_step", "at_batch_run", "at_batch_query", "at_batch_destroy")
-PATH_AUTO, PATH_STAGE, PATH_PERSISTENT = 0, 1, 2
+PATH_AUTO, PATH_STAGE, PATH_PERSISTENT, PATH_FUSED = 0, 1, 2, 3
 OPT_PATH, OPT_WAIT_LIMIT, OPT_WITHHOLD_PE, OPT_ARRIVAL = 0, 1, 2, 3
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -254,7 +254,8 @@ class Solver:
         return self._trace.cpu().numpy()
 
     def set_path(self, path: str):
-        self.set_option(OPT_PATH, {"auto": PATH_AUTO, "stage": PATH_STAGE, "persistent": PATH_PERSISTENT}[path])
+        self.set_option(OPT_PATH, {"auto": PATH_AUTO, "stage": PATH_STAGE, "persistent": PATH_PERSISTENT,
+                                  "fused": PATH_FUSED}[path])
 
     def profile(self, enable: bool = True):
         check(lib().at_profile(self._h, 1 if enable else 0))

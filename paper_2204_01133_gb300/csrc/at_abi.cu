@@ -27,6 +27,9 @@ int64_t atk_persist_capacity(int pde, int order, int B, int device);
 int atk_cluster_size(int pde, int order, int B, int64_t P, int R, int S, int device);
 cudaError_t atk_launch_cluster(const atk::StageArgs& a, int order, int csize, int64_t level0, int64_t nsteps,
                                cudaStream_t st);
+bool atk_fused_supported(int pde, int order, int B, int S);
+cudaError_t atk_launch_fused(const atk::StageArgs& a, int order, int64_t n, const double* uin, double* uout,
+                             cudaStream_t st);
 cudaError_t atk_launch_persist(const atk::StageArgs& a, int pde, int order, int64_t level0, int64_t nsteps,
                                cudaStream_t st);
 int atk_batch_variant(int pde, int order);
@@ -494,6 +497,41 @@ int at_step(at_ctx* c, int64_t nsteps)
     if (c->arrival && !persist)
         return fail(AT_EINVAL, "delays by arrival need the persistent path (a central PDE and at most %lld PEs)",
                     (long long)c->persist_cap);
+    const bool fused_ok = atk_fused_supported(c->pb.pde, c->pb.order, c->pb.pe_size, L.S);
+    if (c->path == AT_PATH_FUSED || (c->path == AT_PATH_AUTO && !persist && !c->arrival && fused_ok)) {
+        if (!fused_ok)
+            return fail(AT_EINVAL, "the fused path takes advection-diffusion with PEs of 32, 64, 128 or 256 points "
+                                   "and at least stages x halo points");
+        c->last_path = AT_PATH_FUSED;
+        c->base.trace = c->trace;
+        c->base.trace_n0 = c->trace_n0;
+        c->base.trace_steps = c->trace_steps;
+        // u^n and u^{n+1} alternate between the state and workspace field A;
+        // after an odd number of steps the result is copied back
+        const double* cur = u;
+        double* nxt = A;
+        for (int64_t i = 0; i < nsteps; ++i) {
+            atk::StageArgs a = c->base;
+            a.level = c->level;
+            e = record(c, true);
+            if (e == cudaSuccess) e = atk_launch_fused(a, c->pb.order, c->level, cur, nxt, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "fused step kernel launch");
+            e = record(c, false);
+            if (e != cudaSuccess) return cuda_fail(e, "profiling event");
+            ++c->launched;
+            ++c->level;
+            double* t = (double*)cur;
+            cur = nxt;
+            nxt = t;
+        }
+        if (cur != u) {
+            e = cudaMemcpyAsync(u, cur, sizeof(double) * (size_t)L.nvar * c->pb.n, cudaMemcpyDeviceToDevice,
+                                c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "copy of the state after the fused steps");
+        }
+        g_err[0] = 0;
+        return AT_OK;
+    }
     c->last_path = persist ? AT_PATH_PERSISTENT : AT_PATH_STAGE;
     c->base.trace = c->trace;
     c->base.trace_n0 = c->trace_n0;
@@ -619,7 +657,7 @@ int at_set_option(at_ctx* c, int key, int64_t value)
     if (!c) return fail(AT_EINVAL, "context is NULL");
     switch (key) {
     case AT_OPT_PATH:
-        if (value < AT_PATH_AUTO || value > AT_PATH_PERSISTENT) return fail(AT_EINVAL, "unknown path %lld", (long long)value);
+        if (value < AT_PATH_AUTO || value > AT_PATH_FUSED) return fail(AT_EINVAL, "unknown path %lld", (long long)value);
         c->path = (int)value;
         return AT_OK;
     case AT_OPT_WAIT_LIMIT:

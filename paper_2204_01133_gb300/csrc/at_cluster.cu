@@ -88,11 +88,12 @@ __global__ void __launch_bounds__(256) cluster_advdiff(const StageArgs a, int64_
             const double* Xc = X + par * m * B + lp * B;      // this stage's argument of the PE
             double* Xn = X + (1 - par) * m * B + lp * B;      // the next one
             // Before the previous stage's cluster barrier completes: the delays,
-            // the neighbour's older levels (k + l >= 1: written at least a stage
+            // the neighbour's levels for delays k >= 1 (written at least a step
             // ago, and their slots are not written in the stage in flight) and
             // the warp's own points of the stencil row (written by the same
             // lanes in the previous stage).
             int k = 0;
+            double bv = 0.0;
             double v[AT_QMAX + 1];
             if (buf) {
                 k = keff_at(a, n, s, pe, side);
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(256) cluster_advdiff(const StageArgs a, int64_
 #pragma unroll
                 for (int l = 0; l <= AT_QMAX; ++l) {
                     v[l] = 0.0;  // a level with weight 0 is not part of the scheme (and may not exist yet)
-                    if (l < nw && k + l >= 1 && ((a.wnz[k] >> l) & 1)) v[l] = src[ridx(n - k - l, s, nl, 1 - side, h)];
+                    if (k >= 1 && l < nw && ((a.wnz[k] >> l) & 1)) v[l] = src[ridx(n - k - l, s, nl, 1 - side, h)];
                 }
             }
 #pragma unroll
@@ -109,12 +110,18 @@ __global__ void __launch_bounds__(256) cluster_advdiff(const StageArgs a, int64_
             // previous stage
             if (n > level0 || s > 0) cl.barrier_wait();
             if (buf) {
-                if (k == 0 && (a.wnz[0] & 1)) v[0] = src[ridx(n, s, nl, 1 - side, h)];  // this level, just written
-                double acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * v[0];
+                // delay 0: the weights are exact integer ratios (1, +-0, ..., +-0),
+                // so the extrapolation is this level's value, just written, up to
+                // the sign of a zero; the stencil sum starts from +0, where a zero
+                // adds nothing whatever its sign (bitwise the per-stage results)
+                if (k == 0) bv = src[ridx(n, s, nl, 1 - side, h)];
+                else {
+                    bv = ((a.mode == AT) ? a.w[k][0] : 1.0) * v[0];
 #pragma unroll
-                for (int l = 1; l <= AT_QMAX; ++l)
-                    if (l < nw) acc = fma(a.w[k][l], v[l], acc);
-                Wr[side == 0 ? h : H + SW + h] = acc;
+                    for (int l = 1; l <= AT_QMAX; ++l)
+                        if (l < nw) bv = fma(a.w[k][l], v[l], bv);
+                }
+                Wr[side == 0 ? h : H + SW + h] = bv;
             }
             if (halo_l) Wr[lane] = Xc[j0 - H + lane];
             if (halo_r) Wr[H + SW + lane] = Xc[j0 + SW + lane];

@@ -78,13 +78,12 @@ __device__ __forceinline__ double fused_extrap_old(const StageArgs& a, int k, co
     return acc;
 }
 
-// k = 0: the weights are (1, 0, ..., 0) and the value is the neighbour's
-// level-n value cur: 1 x cur, then for AT the terms 0 x 0 added, which turns
-// a -0 into +0 and changes nothing else.  Done with integer instructions.
-__device__ __forceinline__ double fused_extrap_cur(const StageArgs& a, double cur)
-{
-    return (a.mode == AT && __double_as_longlong(cur) == (long long)0x8000000000000000ULL) ? 0.0 : cur;
-}
+// k = 0: the weights are exact integer ratios, (1, +-0, ..., +-0), and the
+// neighbour's level-n value cur comes out unchanged, up to the sign of a zero
+// (1 x cur plus the +-0 terms).  The stencil sum starts from +0, so a zero
+// buffer value adds nothing whatever its sign: taking cur itself gives the
+// per-stage path's results bit for bit, with no FP64 instruction.
+__device__ __forceinline__ double fused_extrap_cur(double cur) { return cur; }
 
 // the buffer value of one edge point of PE nbr's window for a delay k >= 1,
 // from the ring levels n-k-l
@@ -116,7 +115,7 @@ __device__ __forceinline__ double fused_buffer_old(const StageArgs& a, int64_t n
 // buffer values with k >= 1 formed from the ring then (with u^n in flight),
 // one warp instruction for all stages and both sides of a PE; a stage only
 // reads shared memory, and fills a k = 0 buffer point with the neighbour's
-// stage argument (integer instructions).
+// stage argument itself (no FP64 instruction).
 template <int H, int PPL, int RK, int W>
 __global__ void __launch_bounds__(32 * (W + 1)) step_fused_advdiff(const StageArgs a, const double* __restrict__ uin,
                                                                    double* __restrict__ uout, int64_t n)
@@ -192,7 +191,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) step_fused_advdiff(const StageAr
                                       : SROW[(par * 2 + 0) * SW + H + D - H + h];
                     else
                         cur = wid < nW - 1 ? R0[(wid + 1) * RW + H + h] : SROW[(par * 2 + 1) * SW + H + h];
-                    b = fused_extrap_cur(a, cur);
+                    b = fused_extrap_cur(cur);
                 } else {
                     b = BV[((wid * S + s) * 2 + side) * H + h];
                 }
@@ -259,7 +258,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) step_fused_advdiff(const StageAr
                 double b;
                 if (k == 0) {
                     const double* R0 = ROW + par * W * RW;
-                    b = fused_extrap_cur(a, st == 0 ? R0[0 * RW + H + sl] : R0[(nW - 1) * RW + H + B - H + sl]);
+                    b = fused_extrap_cur(st == 0 ? R0[0 * RW + H + sl] : R0[(nW - 1) * RW + H + B - H + sl]);
                 } else {
                     b = SBV[(st * (S - 1) + s) * H + sl];
                 }

@@ -277,24 +277,50 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                     const int side = hp < H ? 0 : 1;
                     const int h = side == 0 ? hp : hp - H;
                     const int k = s_k[side];
-                    if ((a.wnz[k] >> l) & 1) {
+                    if (k >= 1 && ((a.wnz[k] >> l) & 1)) {
                         // the neighbour's own derived quantities of that level
                         const int64_t gi = gring_index(a, n - k - l, s, nbr[side], 1 - side, h, ND);
 #pragma unroll
                         for (int d = 0; d < ND; ++d) HS[tt * ND + d] = __ldcg(a.gring + gi + d);
-                    } else {
+                    } else if (k >= 1) {
 #pragma unroll
                         for (int d = 0; d < ND; ++d) HS[tt * ND + d] = 0.0;
                     }
                 }
                 __syncwarp();
-                // weighted sum over levels, in level order: lanes (buffer point, quantity)
-                for (int c = lane; c < 2 * H * ND; c += 32) {
-                    const int hp = c / ND, d = c - hp * ND;
-                    const int k = s_k[hp < H ? 0 : 1];
-                    double acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * HS[(hp * nw) * ND + d];
-                    for (int l = 1; l < nw; ++l) acc = fma(a.w[k][l], HS[(hp * nw + l) * ND + d], acc);
-                    G[d * W2 + (hp < H ? hp : B + hp)] = acc;
+                // weighted sum over levels, in level order: lanes (buffer point,
+                // quantity).  A side with delay 0 has weights (1, +-0, ...), exact
+                // integer ratios: its buffer values are the neighbour's level-n
+                // quantities themselves, up to the sign of a zero, which no
+                // stencil sum sees (they start from +0 and take the buffer
+                // columns as factors), so they are copied without FP64 work.
+                constexpr int NI = 2 * H * ND, NP = (NI + 31) / 32;
+                double cur[NP];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    const int c = lane + 32 * i;
+                    cur[i] = 0.0;
+                    if (c < NI) {
+                        const int hp = c / ND, d = c - hp * ND;
+                        const int side = hp < H ? 0 : 1;
+                        if (s_k[side] == 0)
+                            cur[i] = __ldcg(a.gring + gring_index(a, n, s, nbr[side], 1 - side,
+                                                                 side == 0 ? hp : hp - H, ND) + d);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    const int c = lane + 32 * i;
+                    if (c < NI) {
+                        const int hp = c / ND, d = c - hp * ND;
+                        const int k = s_k[hp < H ? 0 : 1];
+                        double acc = cur[i];
+                        if (k >= 1) {
+                            acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * HS[(hp * nw) * ND + d];
+                            for (int l = 1; l < nw; ++l) acc = fma(a.w[k][l], HS[(hp * nw + l) * ND + d], acc);
+                        }
+                        G[d * W2 + (hp < H ? hp : B + hp)] = acc;
+                    }
                 }
             } else if (lane == 0) {
                 s_abort_at = t;

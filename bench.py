@@ -58,11 +58,11 @@ NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal, at 2070 M
 # share of the FP64 roof the kernel's own arithmetic uses.
 FLOPS_PER_POINT_STAGE = {
     ("rns", "stage"): 176.3,         # central6 + AT6, 4 variables (RK4 stage 1 counted)
-    ("rns", "persistent"): 179.9,    # same work, all K steps of one launch
+    ("rns", "persistent"): 177.0,    # same work, all K steps of one launch
     ("detonation", "stage"): 796.9,  # WENO5 + AT-WENO5, 8 reconstructions per edge (RK3 stage 0)
     ("advdiff", "stage"): 13.56,     # 5-tap merged stencil + RK4 update, mean of the 4 stages
     ("advdiff", "persistent"): 13.56,
-    ("advdiff", "fused"): 13.56,     # the method's work only: the recomputed outer edge points are not counted
+    ("advdiff", "fused"): 13.56,     # the method's work only (13.65 as executed, with the recomputed edge points)
 }
 # Algorithmic HBM bytes per point per stage of the per-stage path: the arrays
 # a step reads and writes (RK4: 17 arrays, RK3-TVD: 8) x nvar x 8 B / stages.
@@ -71,14 +71,17 @@ BYTES_PER_POINT_STAGE = {"rns": 17 * 4 * 8 / 4, "detonation": 8 * 4 * 8 / 3, "ad
 BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4}
 # DRAM bytes per launch of the timed kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum) from the ncu captures of the current kernels, by
-# workload and path; the advection-diffusion kernel was captured at N = 2^25
-# and is scaled by 4.
+# workload and path; the advection-diffusion kernels were captured at
+# N = 2^25 and are scaled by 4 for N = 2^27.
 TRAFFIC_PER_LAUNCH = {
     ("rns-flame-n16384", "persistent"): 2.5390e6,  # state and rings read once, writes stay in L2
     ("rns-flame-n16777216", "stage"): 1.6618e9 + 1.0869e9,
     ("detonation-n16777216", "stage"): 5.4581e8 + 4.9380e8,
     ("advdiff-n134217728", "stage"): 4 * (8.7079e8 + 5.1163e8),
     ("advdiff-n33554432", "stage"): 8.7079e8 + 5.1163e8,
+    ("advdiff-n134217728", "fused"): 4 * (4.6984e8 + 3.0259e8),  # one step: u^n, u^{n+1}, the ring
+    ("advdiff-n33554432", "fused"): 4.6984e8 + 3.0259e8,
+    ("advdiff-n2048", "persistent"): 7.7824e4,  # one-cluster launch: state and ring read once
 }
 
 

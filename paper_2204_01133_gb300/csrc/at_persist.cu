@@ -271,29 +271,16 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
             __syncwarp();
             const bool failed = *(volatile int*)&s_fail != 0;
             if (!failed) {
-                const int tt = lane;
-                if (tt < 2 * H * nw) {
-                    const int hp = tt / nw, l = tt - hp * nw;
-                    const int side = hp < H ? 0 : 1;
-                    const int h = side == 0 ? hp : hp - H;
-                    const int k = s_k[side];
-                    if (k >= 1 && ((a.wnz[k] >> l) & 1)) {
-                        // the neighbour's own derived quantities of that level
-                        const int64_t gi = gring_index(a, n - k - l, s, nbr[side], 1 - side, h, ND);
-#pragma unroll
-                        for (int d = 0; d < ND; ++d) HS[tt * ND + d] = __ldcg(a.gring + gi + d);
-                    } else if (k >= 1) {
-#pragma unroll
-                        for (int d = 0; d < ND; ++d) HS[tt * ND + d] = 0.0;
-                    }
-                }
-                __syncwarp();
-                // weighted sum over levels, in level order: lanes (buffer point,
-                // quantity).  A side with delay 0 has weights (1, +-0, ...), exact
-                // integer ratios: its buffer values are the neighbour's level-n
-                // quantities themselves, up to the sign of a zero, which no
-                // stencil sum sees (they start from +0 and take the buffer
-                // columns as factors), so they are copied without FP64 work.
+                // A side with delay 0 has weights (1, +-0, ...), exact integer
+                // ratios: its buffer values are the neighbour's level-n quantities
+                // themselves, up to the sign of a zero, which no stencil sum sees
+                // (they start from +0 and take the buffer columns as factors), so
+                // they are copied without FP64 work.  Their loads go first, so
+                // that they are in flight with those of the other side.  (With
+                // one derived quantity the weighted sum is a few instructions on
+                // 2H lanes and the staging of the general case measured faster:
+                // there every side takes it.)
+                constexpr bool copy0 = ND > 1;
                 constexpr int NI = 2 * H * ND, NP = (NI + 31) / 32;
                 double cur[NP];
 #pragma unroll
@@ -303,11 +290,31 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                     if (c < NI) {
                         const int hp = c / ND, d = c - hp * ND;
                         const int side = hp < H ? 0 : 1;
-                        if (s_k[side] == 0)
+                        if (copy0 && s_k[side] == 0)
                             cur[i] = __ldcg(a.gring + gring_index(a, n, s, nbr[side], 1 - side,
                                                                  side == 0 ? hp : hp - H, ND) + d);
                     }
                 }
+                // the other sides: their levels n-k-l into HS
+                const int tt = lane;
+                if (tt < 2 * H * nw) {
+                    const int hp = tt / nw, l = tt - hp * nw;
+                    const int side = hp < H ? 0 : 1;
+                    const int h = side == 0 ? hp : hp - H;
+                    const int k = s_k[side];
+                    const bool staged = !copy0 || k >= 1;
+                    if (staged && ((a.wnz[k] >> l) & 1)) {
+                        // the neighbour's own derived quantities of that level
+                        const int64_t gi = gring_index(a, n - k - l, s, nbr[side], 1 - side, h, ND);
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) HS[tt * ND + d] = __ldcg(a.gring + gi + d);
+                    } else if (staged) {
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) HS[tt * ND + d] = 0.0;
+                    }
+                }
+                __syncwarp();
+                // weighted sum over levels, in level order: lanes (buffer point, quantity)
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
                     const int c = lane + 32 * i;
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_
                         const int hp = c / ND, d = c - hp * ND;
                         const int k = s_k[hp < H ? 0 : 1];
                         double acc = cur[i];
-                        if (k >= 1) {
+                        if (!copy0 || k >= 1) {
                             acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * HS[(hp * nw) * ND + d];
                             for (int l = 1; l < nw; ++l) acc = fma(a.w[k][l], HS[(hp * nw + l) * ND + d], acc);
                         }

@@ -75,7 +75,7 @@ BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4}
 # N = 2^25 and are scaled by 4 for N = 2^27.
 TRAFFIC_PER_LAUNCH = {
     ("rns-flame-n16384", "persistent"): 2.5390e6,  # state and rings read once, writes stay in L2
-    ("rns-flame-n16777216", "stage"): 1.6618e9 + 1.0869e9,
+    ("rns-flame-n16777216", "stage"): 1.6610e9 + 1.0863e9,
     ("detonation-n16777216", "stage"): 5.4581e8 + 4.9380e8,
     ("advdiff-n134217728", "stage"): 4 * (8.7079e8 + 5.1163e8),
     ("advdiff-n33554432", "stage"): 8.7079e8 + 5.1163e8,

@@ -615,6 +615,13 @@ int atk_stage_block(int pde, int Tw)
 {
     int nv = (pde == atk::RNS || pde == atk::EULER) ? 4 : 1;
     int want = (pde == atk::EULER || pde == atk::ADV_WENO || pde == atk::BURGERS) ? 256 : nv * Tw;
+    // reacting N-S: half a thread per (point, variable) item, so that a CTA of
+    // 256 threads takes two whole-PE windows (below).  A window's fill has
+    // fewer items than its update (own points plus ring levels, against 4 per
+    // point), and two windows' fills keep more of the CTA busy before the
+    // barrier (measured on GB300 at N = 2^24, PEs of 64: 15.1 ms per step with
+    // one window per CTA, 13.7 with two or four)
+    if (pde == atk::RNS) want = nv * Tw / 2;
     if (want > 256) want = 256;
     want = ((want + 31) / 32) * 32;
     return want < 32 ? 32 : want;

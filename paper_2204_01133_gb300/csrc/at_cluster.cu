@@ -11,13 +11,18 @@
 // an arrive after the update and a wait before the one read that needs it (the
 // neighbour's level of this step, delay 0); the delays, the neighbour's older
 // levels and the copy of the own points into the stencil row go between the
-// two.  One warp per PE of 32 points, two for larger PEs (each warp half of
-// the points and one side's buffer points), point j of a warp's share on lane
-// j % 32.  The delays, the AT extrapolation, the stencil and the RK update are
-// those of the per-stage kernels, with the same arithmetic in the same order,
-// so results are bitwise equal to them.  The global history ring is read at
-// the start of a launch and written back at its end, so runs can switch
-// between paths between at_step calls.
+// two.  A PE takes 1, 2, 4 or 8 warps (as many as bring the CTA to 8 warps,
+// at most one per 32 points); each warp has its share of the points, point j
+// of the share on lane j % 32, and its own stencil row, the first and last
+// warp of a PE also its left and right buffer points.  The stage argument is
+// double-buffered, so the warps of a PE meet only at the cluster barrier.  The
+// delays, the AT extrapolation, the stencil and the RK update are those of
+// the per-stage kernels, with the same arithmetic in the same order (a delay-0
+// buffer value is the neighbour's value itself: its weights are the exact
+// ratios (1, +-0, ...), which change at most the sign of a zero, and no
+// stencil sum sees that), so results are bitwise equal to them.  The global
+// history ring is read at the start of a launch and written back at its end,
+// so runs can switch between paths between at_step calls.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 

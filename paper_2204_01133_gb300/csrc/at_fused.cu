@@ -156,8 +156,9 @@ __global__ void __launch_bounds__(32 * (W + 1)) step_fused_advdiff(const StageAr
                 ROW[wid * RW + H + lane + 32 * i] = v;
             }
         }
-        // the delays and ring levels of every stage: lane e < 2 S H takes
-        // stage e / 2H, side (e / H) % 2, point e % H of the edge window
+        // the delays of every stage and the buffer values of delays >= 1: lane
+        // e < 2 S H takes stage e / 2H, side (e / H) % 2, point e % H of the
+        // edge window
         if (active && lane < 2 * S * H) {
             const int s = lane / (2 * H), side = (lane / H) & 1, h = lane % H;
             const int64_t nb = side == 0 ? (pe == 0 ? P - 1 : pe - 1) : (pe == P - 1 ? 0 : pe + 1);
@@ -236,8 +237,9 @@ __global__ void __launch_bounds__(32 * (W + 1)) step_fused_advdiff(const StageAr
         }
         // the strips' buffers, on the side facing the CTA: pl's right side
         // (from p0's left window), pr's left side (from plast's right window);
-        // delays and ring levels of every stage, lane e < 2 (S-1) H taking
-        // strip e / ((S-1) H), stage (e / H) % (S-1), point e % H
+        // the delays of every stage and the buffer values of delays >= 1, lane
+        // e < 2 (S-1) H taking strip e / ((S-1) H), stage (e / H) % (S-1),
+        // point e % H
         if (lane < 2 * (S - 1) * H) {
             const int t = lane / ((S - 1) * H), s = (lane / H) % (S - 1), hh = lane % H;
             const int64_t tpe = t == 0 ? pl : pr;

@@ -91,9 +91,11 @@ enum { AT_READ_STATE = 0, AT_READ_DELAYS = 1, AT_READ_RING = 2, AT_READ_STATS = 
  * 256 points and at least stages x halo points; AT_EINVAL from at_step
  * otherwise; u^{n+1} goes to workspace field A and back, so an odd number of
  * steps in one call ends with a device copy of the state); AT_PATH_AUTO
- * (default) takes the persistent path when it can, else the fused path when
- * it can, else the per-stage path.  All paths compute the same values in the
- * same order.                                                              */
+ * (default) takes the one-cluster kernel when it can, else for
+ * advection-diffusion the fused path when it can, else the persistent path
+ * when it can, else the per-stage path (delays by arrival order and
+ * AT_OPT_WITHHOLD_PE keep the persistent path).  All paths compute the same
+ * values in the same order.                                                */
 enum { AT_PATH_AUTO = 0, AT_PATH_STAGE = 1, AT_PATH_PERSISTENT = 2, AT_PATH_FUSED = 3 };
 /* at_set_option keys */
 enum {

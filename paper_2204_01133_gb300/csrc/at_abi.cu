@@ -493,11 +493,18 @@ int at_step(at_ctx* c, int64_t nsteps)
     if (c->path == AT_PATH_PERSISTENT && !can_persist)
         return fail(AT_EINVAL, "the persistent path needs a central PDE and at most %lld PEs (have %lld)",
                     (long long)c->persist_cap, (long long)L.P);
-    const bool persist = c->path == AT_PATH_PERSISTENT || (c->path == AT_PATH_AUTO && can_persist);
+    const bool fused_ok = atk_fused_supported(c->pb.pde, c->pb.order, c->pb.pe_size, L.S);
+    const bool cluster_ok = c->cluster_c > 0 && !c->arrival && c->withhold_pe < 0;
+    bool persist = c->path == AT_PATH_PERSISTENT || (c->path == AT_PATH_AUTO && can_persist);
+    // advection-diffusion beyond one thread-block cluster: the step-fused
+    // kernel is faster than the neighbour-wait kernel (measured on GB300 at
+    // 256 PEs of 64 points: 10.3 against 13.1 us per step); delays by arrival
+    // and withheld progress need the neighbour waits
+    if (c->path == AT_PATH_AUTO && persist && !cluster_ok && fused_ok && !c->arrival && c->withhold_pe < 0)
+        persist = false;
     if (c->arrival && !persist)
         return fail(AT_EINVAL, "delays by arrival need the persistent path (a central PDE and at most %lld PEs)",
                     (long long)c->persist_cap);
-    const bool fused_ok = atk_fused_supported(c->pb.pde, c->pb.order, c->pb.pe_size, L.S);
     if (c->path == AT_PATH_FUSED || (c->path == AT_PATH_AUTO && !persist && !c->arrival && fused_ok)) {
         if (!fused_ok)
             return fail(AT_EINVAL, "the fused path takes advection-diffusion with PEs of 32, 64, 128 or 256 points "
@@ -546,7 +553,7 @@ int at_step(at_ctx* c, int64_t nsteps)
         a.arrival = c->arrival;
         // a small advection-diffusion problem runs in one thread-block cluster
         // (Philox delays only; fault injection needs the neighbour waits)
-        const bool cluster = c->cluster_c > 0 && !c->arrival && c->withhold_pe < 0;
+        const bool cluster = cluster_ok;
         e = record(c, true);
         if (e == cudaSuccess)
             e = cluster ? atk_launch_cluster(a, c->pb.order, c->cluster_c, c->level, nsteps, c->stream)

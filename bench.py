@@ -513,8 +513,11 @@ def run_ours(args):
     launches = st.kernels_launched - launched0
     path = {1: "stage", 2: "persistent", 3: "fused"}.get(st.path, "?")
     launch_ms = st.stage_ms / max(st.launches_timed, 1)
-    # point-stages per launch: all K steps (persistent), one step (fused), one stage
-    units_per_launch = n * (S * args.steps if path == "persistent" else S if path == "fused" else 1)
+    # point-stages per launch: all K steps (persistent; fused when its CTAs
+    # fit one cooperative launch: one timed launch per call), one step (fused
+    # otherwise), one stage
+    fused_steps = max(1, round(args.steps / max(st.launches_timed, 1))) if path == "fused" else 1
+    units_per_launch = n * (S * args.steps if path == "persistent" else S * fused_steps if path == "fused" else 1)
     from paper_2204_01133_gb300 import shard
     ms = shard.max_over_ranks(ms)
     value = world * n * args.steps / (ms * 1e-3)
@@ -540,7 +543,8 @@ def run_ours(args):
         achieved = fl / (launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, path)),
-                "kernel": kernel_label(kind, path, pb, args.arrival),
+                "kernel": ("steps_fused_" + kind) if path == "fused" and fused_steps > 1
+                          else kernel_label(kind, path, pb, args.arrival),
                 "avg_launch_ms": launch_ms, "launches_timed": int(st.launches_timed),
                 "flops_per_launch": fl, "peak_kind": "nominal FP64 (1.25 TFLOP/s); see peak_measured",
                 "peak_measured": peak_meas, "frac_of_measured": (achieved / peak_meas) if peak_meas else None}

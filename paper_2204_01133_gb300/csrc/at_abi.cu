@@ -28,6 +28,9 @@ int atk_cluster_size(int pde, int order, int B, int64_t P, int R, int S, int dev
 cudaError_t atk_launch_cluster(const atk::StageArgs& a, int order, int csize, int64_t level0, int64_t nsteps,
                                cudaStream_t st);
 bool atk_fused_supported(int pde, int order, int B, int S);
+int atk_fused_multi_w(int order, int rk, int B, int S, int64_t P, int device);
+cudaError_t atk_launch_fused_steps(const atk::StageArgs& a, int order, int W, int64_t level0, int64_t nsteps,
+                                   double* b0, double* b1, cudaStream_t st);
 cudaError_t atk_launch_fused(const atk::StageArgs& a, int order, int64_t n, const double* uin, double* uout,
                              cudaStream_t st);
 cudaError_t atk_launch_persist(const atk::StageArgs& a, int pde, int order, int64_t level0, int64_t nsteps,
@@ -316,6 +319,7 @@ struct at_ctx {
     int last_path = 0;             // path of the last at_step
     int64_t persist_cap = 0;       // PEs one cooperative launch can hold (0: unavailable)
     int cluster_c = 0;             // CTAs of the one-cluster kernel for this problem (0: not used)
+    int fused_multi_w = 0;         // PEs per CTA when the fused path's steps fit one cooperative launch
     int64_t wait_limit = 4000000;  // polls of a bounded wait
     int64_t withhold_pe = -1;
     int arrival = 0;               // at_set_option(AT_OPT_ARRIVAL)
@@ -469,6 +473,9 @@ int at_set_delays(at_ctx* c, const at_delays* dl)
     c->cluster_c = c->pb.pde == AT_ADVDIFF
                        ? atk_cluster_size(c->pb.pde, c->pb.order, c->pb.pe_size, L.P, L.R, L.S, c->device)
                        : 0;
+    c->fused_multi_w = atk_fused_supported(c->pb.pde, c->pb.order, c->pb.pe_size, L.S)
+                           ? atk_fused_multi_w(c->pb.order, c->pb.rk, c->pb.pe_size, L.S, L.P, c->device)
+                           : 0;
     cudaGetLastError();  // an unavailable persistent path is not an error
     c->have_delays = true;
     g_err[0] = 0;
@@ -517,6 +524,23 @@ int at_step(at_ctx* c, int64_t nsteps)
         // after an odd number of steps the result is copied back
         const double* cur = u;
         double* nxt = A;
+        if (c->fused_multi_w > 0 && nsteps > 0) {
+            // every CTA resident: all steps in one cooperative launch
+            atk::StageArgs a = c->base;
+            a.level = c->level;
+            a.wait_limit = c->wait_limit;
+            a.withhold_pe = c->withhold_pe;
+            e = record(c, true);
+            if (e == cudaSuccess)
+                e = atk_launch_fused_steps(a, c->pb.order, c->fused_multi_w, c->level, nsteps, u, A, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "fused multi-step kernel launch");
+            e = record(c, false);
+            if (e != cudaSuccess) return cuda_fail(e, "profiling event");
+            c->launched += 2;  // counter reset + the kernel
+            c->level += nsteps;
+            if (nsteps & 1) cur = A;  // the result's buffer
+            nsteps = 0;               // nothing left for the per-step launches
+        }
         for (int64_t i = 0; i < nsteps; ++i) {
             atk::StageArgs a = c->base;
             a.level = c->level;

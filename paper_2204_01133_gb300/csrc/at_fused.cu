@@ -25,6 +25,7 @@
 // The step reads u^n from one buffer and writes u^{n+1} to another (a
 // neighbouring CTA may still read the edge points of u^n); the host
 // alternates the two.
+#include <cuda/atomic>
 #include <cuda_runtime.h>
 
 #include "at_device.cuh"
@@ -95,7 +96,7 @@ __device__ __forceinline__ double fused_buffer_old(const StageArgs& a, int64_t n
 #pragma unroll
     for (int l = 0; l <= AT_QMAX; ++l) {
         v[l] = 0.0;  // a level with weight 0 is not part of the scheme (and may not exist yet)
-        if (l < nw && ((a.wnz[k] >> l) & 1)) v[l] = a.ring[ring_index(a, n - k - l, s, nbr, side, h, 0)];
+        if (l < nw && ((a.wnz[k] >> l) & 1)) v[l] = __ldcg(a.ring + ring_index(a, n - k - l, s, nbr, side, h, 0));
     }
     return fused_extrap_old(a, k, v);
 }
@@ -117,14 +118,13 @@ __device__ __forceinline__ double fused_buffer_old(const StageArgs& a, int64_t n
 // reads shared memory, and fills a k = 0 buffer point with the neighbour's
 // stage argument itself (no FP64 instruction).
 template <int H, int PPL, int RK, int W>
-__global__ void __launch_bounds__(32 * (W + 1)) step_fused_advdiff(const StageArgs a, const double* __restrict__ uin,
-                                                                   double* __restrict__ uout, int64_t n)
+__device__ __forceinline__ void fused_step(const StageArgs& a, const double* __restrict__ uin,
+                                           double* __restrict__ uout, int64_t n, double* sm)
 {
     constexpr int B = 32 * PPL;
     constexpr int S = RkS<RK>::S;
     constexpr int D = S * H;
     constexpr int RW = B + 2 * H, SW = D + 2 * H;
-    extern __shared__ double sm[];
     double* ROW = sm;
     double* SROW = ROW + 2 * W * RW;
     double* SUN = SROW + 2 * 2 * SW;
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) step_fused_advdiff(const StageAr
         const int64_t spe = st == 0 ? pl : pr;
         const int64_t soff = st == 0 ? (int64_t)(B - D) : 0;  // first strip point within spe
         if (sl < D) {
-            const double v = uin[spe * B + soff + sl];
+            const double v = __ldcg(uin + spe * B + soff + sl);  // written by another CTA
             SUN[st * D + sl] = v;
             SROW[(0 * 2 + st) * SW + H + sl] = v;
         }
@@ -284,6 +284,85 @@ __global__ void __launch_bounds__(32 * (W + 1)) step_fused_advdiff(const StageAr
     }
 }
 
+// one step n: u^n from uin, u^{n+1} to uout
+template <int H, int PPL, int RK, int W>
+__global__ void __launch_bounds__(32 * (W + 1)) step_fused_advdiff(const StageArgs a, const double* __restrict__ uin,
+                                                                   double* __restrict__ uout, int64_t n)
+{
+    extern __shared__ double sm[];
+    fused_step<H, PPL, RK, W>(a, uin, uout, n, sm);
+}
+
+__device__ __forceinline__ int64_t fused_load_acquire(int64_t* p)
+{
+    cuda::atomic_ref<int64_t, cuda::thread_scope_device> r(*p);
+    return r.load(cuda::memory_order_acquire);
+}
+
+__device__ __forceinline__ void fused_store_release(int64_t* p, int64_t v)
+{
+    cuda::atomic_ref<int64_t, cuda::thread_scope_device> r(*p);
+    r.store(v, cuda::memory_order_release);
+}
+
+// bounded wait for *ctr >= target; false if it ran out (status bit 2, abort
+// flag raised) or another CTA's wait did
+__device__ bool fused_wait_ge(const StageArgs& a, int64_t* ctr, int64_t target)
+{
+    if (fused_load_acquire(ctr) >= target) return true;
+    for (int64_t it = 0; it < a.wait_limit; ++it) {
+        __nanosleep(128);
+        if (fused_load_acquire(ctr) >= target) return true;
+        if ((it & 63) == 0 && *(volatile int*)a.abort_flag) return false;
+    }
+    atomicOr(a.status, 2);
+    atomicExch(a.abort_flag, 1);
+    return false;
+}
+
+// All steps of an at_step call in one cooperative launch (every CTA
+// resident).  CTA c publishes in done[c] the level it has reached; before
+// step n it waits for its two neighbour CTAs to have finished step n-1.  That
+// one wait covers everything a step reads from outside the CTA: the
+// neighbours' u^n on the strips (written at their step n-1), and ring levels
+// older than n.  It also protects what the step writes: u^{n+1} goes to the
+// buffer that held u^{n-1}, which the neighbours read during their step n-1,
+// and the ring slots of levels n and n+1, which no CTA at step n or n+1 reads
+// (the CTAs are at most one step apart, the ring keeps k_max + q + 3 levels).
+template <int H, int PPL, int RK, int W>
+__global__ void __launch_bounds__(32 * (W + 1)) steps_fused_advdiff(const StageArgs a, double* __restrict__ b0,
+                                                                    double* __restrict__ b1, int64_t level0,
+                                                                    int64_t nsteps)
+{
+    extern __shared__ double sm[];
+    __shared__ int s_fail;
+    const int64_t C = gridDim.x, c = blockIdx.x;
+    const int64_t cl = c == 0 ? C - 1 : c - 1, cr = c == C - 1 ? 0 : c + 1;
+    const bool withheld = a.withhold_pe >= 0 && a.withhold_pe / W == c;  // fault injection: never publishes
+    for (int64_t i = 0; i < nsteps; ++i) {
+        const int64_t n = level0 + i;
+        if (i > 0) {
+            if (threadIdx.x == 0) s_fail = (fused_wait_ge(a, a.done + cl, n) && fused_wait_ge(a, a.done + cr, n)) ? 0 : 1;
+            __syncthreads();
+            if (s_fail) break;
+        }
+        fused_step<H, PPL, RK, W>(a, (i & 1) ? b1 : b0, (i & 1) ? b0 : b1, n, sm);
+        __syncthreads();  // every thread's writes of step n
+        if (threadIdx.x == 0 && !withheld) {
+            __threadfence();
+            fused_store_release(a.done + c, n + 1);
+        }
+    }
+}
+
+// done[c] = level0 for the CTAs of a launch, and the abort flag cleared
+__global__ void fused_counters_set(int64_t* done, int64_t C, int64_t level0, int* abort_flag)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C; i += (int64_t)gridDim.x * blockDim.x)
+        done[i] = level0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *abort_flag = 0;
+}
+
 } // namespace atk
 
 // ---------------------------------------------------------------------------
@@ -319,12 +398,45 @@ void* fused_fn(int H, int rk, int ppl)
     return fused_fn_rk<3>(rk, ppl);
 }
 
-size_t fused_smem(int B, int H, int S)
+// the multi-step kernel with W = 4 or 8 PEs per CTA
+template <int H, int RK, int W>
+void* fused_steps_fn_ppl(int ppl)
+{
+    switch (ppl) {
+    case 1: return (void*)atk::steps_fused_advdiff<H, 1, RK, W>;
+    case 2: return (void*)atk::steps_fused_advdiff<H, 2, RK, W>;
+    case 4: return (void*)atk::steps_fused_advdiff<H, 4, RK, W>;
+    default: return (void*)atk::steps_fused_advdiff<H, 8, RK, W>;
+    }
+}
+
+template <int H, int W>
+void* fused_steps_fn_rk(int rk, int ppl)
+{
+    if (rk == atk::RK4) return fused_steps_fn_ppl<H, atk::RK4, W>(ppl);
+    if (rk == atk::RK3TVD) return fused_steps_fn_ppl<H, atk::RK3TVD, W>(ppl);
+    return fused_steps_fn_ppl<H, atk::RK2, W>(ppl);
+}
+
+template <int W>
+void* fused_steps_fn_h(int H, int rk, int ppl)
+{
+    if (H == 1) return fused_steps_fn_rk<1, W>(rk, ppl);
+    if (H == 2) return fused_steps_fn_rk<2, W>(rk, ppl);
+    return fused_steps_fn_rk<3, W>(rk, ppl);
+}
+
+void* fused_steps_fn(int H, int rk, int ppl, int W)
+{
+    return W == 4 ? fused_steps_fn_h<4>(H, rk, ppl) : fused_steps_fn_h<8>(H, rk, ppl);
+}
+
+size_t fused_smem(int B, int H, int S, int W = kFusedW)
 {
     const int D = S * H;
-    return sizeof(double) * ((size_t)2 * kFusedW * (B + 2 * H) + (size_t)4 * (D + 2 * H) + (size_t)2 * D +
-                             (size_t)kFusedW * S * 2 * H + (size_t)2 * (S - 1) * H) +
-           sizeof(int) * ((size_t)kFusedW * S * 2 + (size_t)2 * (S - 1));
+    return sizeof(double) * ((size_t)2 * W * (B + 2 * H) + (size_t)4 * (D + 2 * H) + (size_t)2 * D +
+                             (size_t)W * S * 2 * H + (size_t)2 * (S - 1) * H) +
+           sizeof(int) * ((size_t)W * S * 2 + (size_t)2 * (S - 1));
 }
 
 } // namespace
@@ -334,6 +446,61 @@ size_t fused_smem(int B, int H, int S)
 bool atk_fused_supported(int pde, int order, int B, int S)
 {
     return pde == atk::ADVDIFF && (B == 32 || B == 64 || B == 128 || B == 256) && B >= S * (order / 2);
+}
+
+// CTAs (of W = 4 or 8 PEs) that one cooperative launch of the multi-step
+// kernel holds at once (0: not available)
+int64_t atk_fused_capacity(int order, int rk, int B, int S, int W, int device)
+{
+    const int H = order / 2;
+    void* fn = fused_steps_fn(H, rk, B / 32, W);
+    const size_t smem = fused_smem(B, H, S, W);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per_sm = 0, sms = 0, coop = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * (W + 1), smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (int64_t)per_sm * sms;
+}
+
+int64_t atk_fused_ctas(int64_t P, int W) { return (P + W - 1) / W; }
+
+// PEs per CTA of the multi-step kernel for P PEs, or 0 when its CTAs do not
+// fit one cooperative launch: 4 where they fit (more SMs share the stages of
+// a small problem), else 8 (measured on GB300, PEs of 64 points, us per
+// step: 2^14 points 7.3 with 4 against 8.9 with 8; 2^18 points 20.6 with 8,
+// where 4 no longer fits and takes one launch per step: 22.5)
+int atk_fused_multi_w(int order, int rk, int B, int S, int64_t P, int device)
+{
+    for (int W = 4; W <= 8; W += 4)
+        if (atk_fused_ctas(P, W) <= atk_fused_capacity(order, rk, B, S, W, device)) return W;
+    return 0;
+}
+
+// steps level0 .. level0 + nsteps - 1 in one cooperative launch of CTAs of W
+// PEs: u^{level0} in b0, the result in b0 (even nsteps) or b1 (odd)
+cudaError_t atk_launch_fused_steps(const atk::StageArgs& a, int order, int W, int64_t level0, int64_t nsteps,
+                                   double* b0, double* b1, cudaStream_t st)
+{
+    const int H = order / 2;
+    const int64_t C = atk_fused_ctas(a.P, W);
+    void* fn = fused_steps_fn(H, a.rk, a.B / 32, W);
+    const size_t smem = fused_smem(a.B, H, a.S, W);
+    atk::fused_counters_set<<<(unsigned)((C + 255) / 256 < 1024 ? (C + 255) / 256 : 1024), 256, 0, st>>>(
+        a.done, C, level0, a.abort_flag);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    atk::StageArgs args = a;
+    void* params[] = {(void*)&args, (void*)&b0, (void*)&b1, (void*)&level0, (void*)&nsteps};
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)C), dim3(32 * (W + 1)), params, smem, st);
 }
 
 // one step n: u^n from uin, u^{n+1} to uout (distinct buffers)

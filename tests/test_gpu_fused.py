@@ -92,3 +92,38 @@ def test_fused_rejects_what_it_does_not_take():
     s.set_option(OPT_ARRIVAL, 1)
     with pytest.raises(RuntimeError):
         s.run(1)
+
+
+def test_fused_per_step_launches_beyond_one_cooperative_launch():
+    """8,192 PEs need more CTAs than the GPU holds at once: one launch per
+    step (the multi-step kernel is not used), bitwise the per-stage path."""
+    pb, u0 = W.advdiff(n=1 << 19, pe_size=64, mode="at", k_max=3, seed=4, cfl=0.075)
+    from paper_2204_01133_gb300.api import Solver
+    s = Solver(pb, u0, path="fused")
+    s.run(3)
+    s.run(2)
+    assert s.stats().kernels_launched == 5  # one launch per step
+    ref, _ = _run(pb, u0, [5], "stage")
+    assert np.array_equal(s.read_state(), ref)
+
+
+def test_fused_wait_runs_out_without_fault():
+    """Fault injection on the multi-step fused kernel: one CTA never publishes
+    its progress, its neighbours' bounded waits run out, at_run reports
+    AT_ETIMEOUT, and the context then runs correctly again."""
+    from paper_2204_01133_gb300 import api
+    pb, u0 = W.advdiff(n=16384, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075)
+    s = api.Solver(pb, u0, path="fused")
+    s.set_option(api.OPT_WAIT_LIMIT, 20000)
+    s.set_option(api.OPT_WITHHOLD_PE, 100)  # a PE in the middle of the ring of CTAs
+    with pytest.raises(api.AtError) as ei:
+        s.run(50)
+    assert ei.value.code == api.AT_ETIMEOUT
+    s.set_option(api.OPT_WITHHOLD_PE, -1)
+    s.set_option(api.OPT_WAIT_LIMIT, 4000000)
+    s.set_problem(u0)
+    s.set_delays()
+    s.set_path("fused")
+    s.run(50)
+    ref, _ = _run(pb, u0, [50], "stage")
+    assert np.array_equal(s.read_state(), ref)

@@ -85,10 +85,12 @@ enum { AT_READ_STATE = 0, AT_READ_DELAYS = 1, AT_READ_RING = 2, AT_READ_STATS = 
  * its two neighbours (central PDEs, up to as many PEs as the GPU holds at
  * once; advection-diffusion on at most 64 PEs of 32..256 points runs instead
  * in one thread-block cluster of up to 16 CTAs with its ring in distributed
- * shared memory); AT_PATH_FUSED launches one kernel per step that runs all
- * its RK stages in one pass over the state, recomputing the edge points of
- * the neighbours beyond each CTA (advection-diffusion, PEs of 32, 64, 128 or
- * 256 points and at least stages x halo points; AT_EINVAL from at_step
+ * shared memory); AT_PATH_FUSED runs all RK stages of a step in one pass
+ * over the state, recomputing the edge points of the neighbours beyond each
+ * CTA: all steps of the call in one cooperative launch whose CTAs wait only
+ * for their neighbour CTAs' previous step when they fit on the GPU at once,
+ * else one launch per step (advection-diffusion, PEs of 32, 64, 128 or 256
+ * points and at least stages x halo points; AT_EINVAL from at_step
  * otherwise; u^{n+1} goes to workspace field A and back, so an odd number of
  * steps in one call ends with a device copy of the state); AT_PATH_AUTO
  * (default) takes the one-cluster kernel when it can, else for
@@ -100,10 +102,12 @@ enum { AT_PATH_AUTO = 0, AT_PATH_STAGE = 1, AT_PATH_PERSISTENT = 2, AT_PATH_FUSE
 /* at_set_option keys */
 enum {
     AT_OPT_PATH = 0,        /* value: AT_PATH_*                                                  */
-    AT_OPT_WAIT_LIMIT = 1,  /* polls (~0.2 us each) before a persistent-path wait gives up with
-                               AT_ETIMEOUT; default 4,000,000                                    */
-    AT_OPT_WITHHOLD_PE = 2, /* fault injection: this PE never announces its progress, so its
-                               neighbours' waits run out (-1, the default: none)                 */
+    AT_OPT_WAIT_LIMIT = 1,  /* polls (~0.2 us each) before a wait of the persistent or the
+                               multi-step fused kernel gives up with AT_ETIMEOUT; default
+                               4,000,000                                                         */
+    AT_OPT_WITHHOLD_PE = 2, /* fault injection: this PE (on the fused path: the CTA holding it)
+                               never announces its progress, so its neighbours' waits run out
+                               (-1, the default: none)                                           */
     AT_OPT_ARRIVAL = 3      /* 1: real asynchrony on the persistent path.  Instead of drawing a
                                delay, each PE boundary uses the freshest stage argument of the
                                neighbour that has arrived (never older than k_max, or than the

@@ -35,6 +35,8 @@ WORKLOADS = {
     "rns-ignition-n16384": dict(kind="rns", case="ignition", n=16384, pe_size=64, mode="at", k_max=4, seed=0,
                                 dt=0.003),
     "advdiff-n2048": dict(kind="advdiff", n=2048, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075),
+    # mid-size: the step-fused path with all steps in one cooperative launch
+    "advdiff-n16384": dict(kind="advdiff", n=16384, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075),
     "advdiff-n134217728": dict(kind="advdiff", n=1 << 27, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075),
     # a quarter of the HBM run, for counter captures (inputs still larger than L2)
     "advdiff-n33554432": dict(kind="advdiff", n=1 << 25, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075),
@@ -82,6 +84,7 @@ TRAFFIC_PER_LAUNCH = {
     ("advdiff-n134217728", "fused"): 4 * (4.6984e8 + 3.0259e8),  # one step: u^n, u^{n+1}, the ring
     ("advdiff-n33554432", "fused"): 4.6984e8 + 3.0259e8,
     ("advdiff-n2048", "persistent"): 7.7824e4,  # one-cluster launch: state and ring read once
+    ("advdiff-n16384", "fused"): 2.8288e5,  # cooperative fused launch: state and ring read once
 }
 
 

@@ -41,7 +41,7 @@ typedef enum {
     AT_ENOMEM = -2,    /* the workspace is smaller than at_workspace_bytes()    */
     AT_ECUDA = -3,     /* a CUDA call failed; at_last_error() has its message   */
     AT_EUNSTABLE = -4, /* a non-finite value appeared in the state              */
-    AT_ETIMEOUT = -5,  /* a bounded device wait of the persistent path ran out  */
+    AT_ETIMEOUT = -5,  /* a bounded device wait (persistent, fused path) ran out */
     AT_ESTATE = -6     /* calls out of order (problem, then delays, then steps) */
 } at_status;
 

@@ -139,3 +139,29 @@ def test_batch_table_and_validation(L):
     assert L.at_batch_create(ctypes.byref(h), 0, None, 16, 64, ctypes.c_void_p(256 + 8), 1 << 20) == api.AT_EINVAL
     assert L.at_batch_create(ctypes.byref(h), 0, None, 16, 64, ctypes.c_void_p(256), 16) == api.AT_ENOMEM
     assert L.at_batch_create(ctypes.byref(h), 0, None, 0, 64, ctypes.c_void_p(256), 1 << 20) == api.AT_EINVAL
+
+
+def test_enum_values_match_the_binding():
+    """Every AT_* enumerator of include/at.h has the value the Python binding
+    passes for it (no GPU needed)."""
+    import re
+    from paper_2204_01133_gb300 import api, batch
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    values = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(AT_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+
+    def binding(name):  # the binding's constant for one enumerator, or None
+        short = name[3:]
+        if short.startswith("BATCH_"):
+            return getattr(batch, short[6:], None)
+        for table in (api.PDE, api.RK, api.MODE, api.DIST):
+            if short.lower() in table:
+                return table[short.lower()]
+        return getattr(api, short, getattr(api, name, None))
+
+    found = {name: binding(name) for name in values}
+    for name, value in values.items():
+        assert found[name] == value, (name, value, found[name])
+    for name in ("AT_PATH_FUSED", "AT_OPT_WITHHOLD_PE", "AT_ETIMEOUT", "AT_READ_STATS", "AT_BATCH_FLAT",
+                 "AT_RNS_CHAIN", "AT_GEOMETRIC"):
+        assert name in values
+    assert len(values) >= 36

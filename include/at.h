@@ -296,7 +296,10 @@ int at_batch_destroy(at_batch* b);
  * the process exits.  Problems whose at_workspace_bytes() exceeds it are
  * rejected with AT_ENOMEM before anything is enqueued.  The first call on a
  * device looks the array's device address up (cudaGetSymbolAddress), so make
- * that first call before any stream capture.  Each call clears the parts of
+ * that first call before any stream capture.  The address is kept for the
+ * life of the process: after cudaDeviceReset on a device the kept address is
+ * stale, so do not call at_run_noalloc on that device again in that process.
+ * Each call clears the parts of
  * the array that must start at zero; all calls share the one array, so calls
  * that overlap on the GPU (other streams, other host threads) race and must
  * be serialised by the caller.  Nothing is allocated: no cudaMalloc, no

@@ -165,3 +165,13 @@ def test_enum_values_match_the_binding():
                  "AT_RNS_CHAIN", "AT_GEOMETRIC"):
         assert name in values
     assert len(values) >= 36
+
+
+def test_noalloc_scratch_size_matches_the_binding():
+    """AT_NOALLOC_SCRATCH_BYTES of include/at.h (a #define, not an
+    enumerator) equals the binding's NOALLOC_SCRATCH_BYTES."""
+    import re
+    from paper_2204_01133_gb300 import api
+    m = re.search(r"#define\s+AT_NOALLOC_SCRATCH_BYTES\s+\(\(size_t\)(\d+)\s*<<\s*(\d+)\)", open(HEADER).read())
+    assert m, "AT_NOALLOC_SCRATCH_BYTES is not of the form ((size_t)A << B)"
+    assert int(m.group(1)) << int(m.group(2)) == api.NOALLOC_SCRATCH_BYTES

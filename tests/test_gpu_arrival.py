@@ -12,7 +12,7 @@ from paper_2204_01133_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL_RUN = 1e-10
+from parity import TOL_RUN, check
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -22,10 +22,6 @@ def _gpu():
         pytest.skip("no GPU")
     from paper_2204_01133_gb300 import build
     build.build()
-
-
-def _rel(g, o):
-    return np.abs(g - o).max() / np.abs(o).max()
 
 
 def _oracle_delays(pb, u0, steps):
@@ -82,7 +78,7 @@ def test_arrival_run_replays_on_the_oracle(maker):
     o = oracle.Oracle(pb, u0)
     o.set_delay_trace(tr, 0)
     assert o.run(steps) == 0
-    assert _rel(g, o.state()) <= TOL_RUN
+    check(pb, g, o.state(), TOL_RUN, "%s replay" % maker)
     print("arrival delays %s: histogram %s" % (maker, np.bincount(tr.ravel(), minlength=pb["k_max"] + 1)))
 
 
@@ -120,4 +116,4 @@ def test_arrival_wait_runs_out_without_fault():
     o = oracle.Oracle(pb, u0)
     o.set_delay_trace(s.read_trace(), 0)
     assert o.run(20) == 0
-    assert _rel(s.read_state(), o.state()) <= TOL_RUN
+    check(pb, s.read_state(), o.state(), TOL_RUN, "after the timeout")

@@ -1,12 +1,15 @@
 """Batched solves on the GPU: every instance of a mixed batch must equal,
 bit for bit, the same instance solved alone through a context (same
 kernels' arithmetic, same delay stream), whatever the chunking, slot reuse,
-launch configuration or graph replay; and the standalone solves are pinned
-to the CPU oracle by test_gpu_parity.py."""
+launch configuration or graph replay; and a seeded sample of instances with
+the shapes of the 4,096-instance reacting batch is checked against the CPU
+oracle directly, in both batch modes."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2204_01133_gb300 import workloads as W
+from parity import TOL_RUN, check
 
 pytestmark = pytest.mark.gpu
 
@@ -124,3 +127,47 @@ def test_flat_mode_window_map_limit():
     assert ei.value.code == api.AT_ENOMEM
     b.release(0)
     b.bind(1, pb, init, 5)  # fits again once the first is released
+
+
+def config2_sample():
+    """Instances with the shapes of the batched reacting workload: the
+    smallest size (N = 256, PEs of 32) at every largest delay 2, 3, 4, as a
+    flame and as an ignition, with T0 (K-equivalent / 300) and the fuel
+    fraction 0.5 phi drawn as the batch draws them; one instance with the
+    largest Philox instance word; the largest size of the mix (N = 8192,
+    PEs of 64)."""
+    rng = np.random.default_rng(2204)
+    out = []
+    for k_max in (2, 3, 4):
+        for case in ("flame", "ignition"):
+            T0 = float(rng.uniform(900.0, 1400.0)) / 300.0
+            phi = float(rng.uniform(0.5, 1.5))
+            out.append(W.rns(case=case, n=256, pe_size=32, mode="at", k_max=k_max, seed=1000 + len(out), dt=0.002,
+                             T_init=T0, T_unburnt=T0, Y_init=0.5 * phi, instance=len(out)))
+    out.append(W.rns(case="flame", n=512, pe_size=64, mode="at", k_max=4, seed=77, dt=0.002, T_init=3.5,
+                     T_unburnt=3.5, Y_init=0.6, instance=0xFFFFFFFF))
+    out.append(W.rns(case="ignition", n=8192, pe_size=64, mode="at", k_max=3, seed=78, dt=0.002, T_init=4.2,
+                     T_unburnt=4.2, Y_init=0.4, instance=4096))
+    return out
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batched_config2_instances_match_the_oracle(mode):
+    """200 RK4 steps of every sampled instance in one batch (instance mode:
+    one CTA per instance; flat mode: one launch per stage over all windows),
+    each against its own oracle run, per variable within the run bound."""
+    from paper_2204_01133_gb300.batch import Batch
+    steps = 200
+    inst = config2_sample()
+    b = Batch(capacity=len(inst))
+    b.set_config(mode, 256, 3, True)
+    for i, (pb, init) in enumerate(inst):
+        b.bind(i, pb, init, steps)
+    while any(b.query(i).left > 0 for i in range(len(inst))):
+        b.run(50)
+    for i, (pb, init) in enumerate(inst):
+        assert b.query(i).status == 0
+        o = oracle.Oracle(pb, init)
+        assert o.run(steps) == 0
+        check(pb, b.state(i).cpu().numpy(), o.state(), TOL_RUN,
+              "batch mode %d instance %d (n=%d, k_max=%d, word %d)" % (mode, i, pb["n"], pb["k_max"], pb["instance"]))

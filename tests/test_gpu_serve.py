@@ -1,8 +1,12 @@
 """Serving: continuous batching admits requests as they arrive, within a
 device-memory budget, overlaps their work on the device, and every result
-is bit-for-bit the one the request gets when solved alone."""
+is bit-for-bit the one the request gets when solved alone; one request of
+each problem type, served in the mix, is checked against the CPU oracle."""
 import numpy as np
 import pytest
+
+import oracle
+from parity import DET_RUN, SERVE_DET, TOL_RUN, check
 
 pytestmark = pytest.mark.gpu
 
@@ -66,3 +70,32 @@ def test_plain_path_matches_too():
     done, _ = serve_plain(small_stream(n=5, seed=9), keep_states=True)
     for r in done:
         assert np.array_equal(np.asarray(r.state), alone(r))
+
+
+@pytest.mark.parametrize("mode,big", [(1, None), (0, 2600)])
+def test_served_requests_match_the_oracle(mode, big):
+    """One request of each type at its rounded size (advection-diffusion
+    2,944 points, reacting flame 2,496, detonation 2,560), arriving together:
+    all as slots of the flat batch, or the two larger ones on contexts of
+    their own beside the batch.  Each result against the oracle run of the
+    same request; the detonation takes its fixed shock bound."""
+    from paper_2204_01133_gb300 import workloads as W
+    from paper_2204_01133_gb300.serve import Server
+    stream = SERVE_ORACLE_STREAM
+    srv = Server(mem_budget=1 << 30, capacity=4, chunk=17, big_points=big, keep_states=True, mode=mode)
+    done, _ = srv.run([dict(d) for d in stream])
+    assert len(done) == 3
+    for r in done:
+        pb, init = W.serving_request(r.kind, r.n, r.seed, instance=r.id)
+        o = oracle.Oracle(pb, init)
+        assert o.run(r.steps) == 0
+        tol = DET_RUN["serve"] if r.kind == "detonation" else TOL_RUN
+        check(pb, np.asarray(r.state), o.state(), tol, "served %s n=%d" % (r.kind, r.n))
+
+
+SERVE_ORACLE_STREAM = [
+    {"id": 0, "arrival": 0.0, "kind": "advdiff", "n": 3000, "steps": 60, "seed": 11},
+    {"id": 1, "arrival": 0.0005, "kind": "rns", "n": 2500, "steps": 60, "seed": 12},
+    {"id": SERVE_DET[2], "arrival": 0.001, "kind": "detonation", "n": SERVE_DET[0], "steps": SERVE_DET[3],
+     "seed": SERVE_DET[1]},
+]

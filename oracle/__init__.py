@@ -46,16 +46,23 @@ class _Problem(ctypes.Structure):
         ("instance", ctypes.c_uint32),
         ("pe_base", ctypes.c_int64),
         ("pe_total", ctypes.c_int64),
+        ("open_ends", ctypes.c_int),
     ]
 
 
 def build(force: bool = False) -> str:
-    """Compile at_oracle.c into liboracle.so (gcc, FP64, no contraction)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    """Compile at_oracle.c into liboracle.so (gcc, FP64, no contraction;
+    OpenMP over PEs where the compiler has it, else single-threaded)."""
+    hdr = os.path.join(_HERE, "at_oracle.h")
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                                                           os.path.getmtime(hdr)):
         return _LIB
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", _LIB, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    r = subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(base + ["-o", tmp, _SRC, "-lm"], check=True)
+    os.replace(tmp, _LIB)
     return _LIB
 
 
@@ -68,6 +75,8 @@ def lib():
         build()
         L = ctypes.CDLL(_LIB)
         P = ctypes.POINTER
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = ctypes.c_int
         L.orc_create.restype = ctypes.c_void_p
         L.orc_create.argtypes = [P(_Problem), P(ctypes.c_double)]
         L.orc_destroy.argtypes = [ctypes.c_void_p]
@@ -98,6 +107,17 @@ def lib():
         L.orc_set_delay_trace.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]
         L.orc_get_history.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
         L.orc_get_history.restype = ctypes.c_int
+        L.orc_stage_begin.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_stage_rhs.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_step_end.argtypes = [ctypes.c_void_p]
+        L.orc_step_end.restype = ctypes.c_int
+        L.orc_get_edges.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, P(ctypes.c_double)]
+        L.orc_get_edges.restype = ctypes.c_int
+        L.orc_set_ext.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]
+        L.orc_delay.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_int]
+        L.orc_delay.restype = ctypes.c_int
+        L.orc_halo.argtypes = [ctypes.c_void_p]
+        L.orc_halo.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -128,6 +148,7 @@ def _problem(pb: dict) -> _Problem:
     s.instance = int(pb.get("instance", 0))
     s.pe_base = int(pb.get("pe_base", 0))
     s.pe_total = int(pb.get("pe_total", 0))
+    s.open_ends = int(pb.get("open_ends", 0))
     return s
 
 
@@ -146,6 +167,7 @@ class Oracle:
         self.stages = L.orc_stages(self._h)
         self.q = L.orc_q(self._h)
         self.ring_levels = L.orc_ring_levels(self._h)
+        self.halo = L.orc_halo(self._h)
         self.n = int(pb["n"])
         self.P = self.n // int(pb["pe_size"])
 
@@ -226,8 +248,41 @@ class Oracle:
         assert t.ndim == 4 and t.shape[2:] == (self.P, 2), t.shape
         lib().orc_set_delay_trace(self._h, ctypes.c_void_p(t.ctypes.data), int(n0), int(t.shape[0]))
 
+    # one RK step stage by stage (a rank of a PE-range split exchanges edge
+    # windows between these calls); run(1) is the same arithmetic
+    def stage_begin(self, stage: int) -> None:
+        lib().orc_stage_begin(self._h, int(stage))
+
+    def stage_rhs(self, stage: int) -> None:
+        lib().orc_stage_rhs(self._h, int(stage))
+
+    def step_end(self) -> int:
+        return int(lib().orc_step_end(self._h))
+
+    def edges(self, level: int, stage: int) -> np.ndarray:
+        """[2][H][nvar]: the window's left and right edge windows of U^{level,(stage)}."""
+        out = np.empty((2, self.halo, self.nvar), dtype=np.float64)
+        if lib().orc_get_edges(self._h, int(level), int(stage), _dptr(out)) != 0:
+            raise ValueError("level %d stage %d is not stored" % (level, stage))
+        return out
+
+    def set_ext(self, level: int, stage: int, side: int, win: np.ndarray) -> None:
+        """Open ends: the [H][nvar] edge window of the PE beyond `side`."""
+        w = np.ascontiguousarray(win, dtype=np.float64).reshape(self.halo, self.nvar)
+        lib().orc_set_ext(self._h, int(level), int(stage), int(side), _dptr(w))
+
+    def delay(self, level: int, stage: int, pe: int, side: int) -> int:
+        """The clamped delay local PE `pe` uses at (level, stage, side)."""
+        return int(lib().orc_delay(self._h, int(level), int(stage), int(pe), int(side)))
+
     def draw(self, level: int, stage: int, pe: int, side: int) -> int:
         return int(lib().orc_draw(self._h, int(level), int(stage), int(pe), int(side)))
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads of the oracle's loops over PEs (0: all cores); returns the
+    count in effect.  Results are the same for any count."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def philox4x32_10(ctr, key):

@@ -46,6 +46,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define MAXD 8 /* most derived quantities per point */
 
@@ -64,6 +67,7 @@ struct orc_ctx {
     int32_t* kfix; /* forced raw delays [P][2], or NULL to draw them */
     uint8_t* trace;            /* delays of every (step, stage, PE, side) to replay, or NULL */
     int64_t trace_n0, trace_steps;
+    double* ext;   /* open ends: edge windows beyond the window [R][S][2][H][nvar] */
 };
 
 /* ------------------------------------------------------------------ */
@@ -325,6 +329,23 @@ static int64_t wrap(const orc_ctx* c, int64_t m)
     return m;
 }
 
+/* the state at buffer position m (unwrapped) of U^{level,(s)}: the stored
+ * field, or with open ends beyond the window the supplied edge window of the
+ * PE there */
+static void buffer_state(const orc_ctx* c, int64_t level, int s, int64_t m, double* Q)
+{
+    if (c->pb.open_ends && (m < 0 || m >= c->N)) {
+        int side = (m < 0) ? 0 : 1;
+        int64_t h = (m < 0) ? m + c->H : m - c->N;
+        int64_t r = level % c->R;
+        if (r < 0) r += c->R;
+        const double* w = c->ext + ((((size_t)r * c->S + s) * 2 + side) * c->H + h) * c->nvar;
+        for (int v = 0; v < c->nvar; ++v) Q[v] = w[v];
+        return;
+    }
+    state_at(c, field(c, level, s), wrap(c, m), Q);
+}
+
 /* derived quantities at global position m (unwrapped), as PE p sees them at
  * stage s of level `level`: own points read U^{level,(s)}; buffer points
  * combine delayed levels with the AT (or AS) weights. */
@@ -339,7 +360,6 @@ static void tap(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t m, do
     }
     int side = (m < lo) ? 0 : 1;
     int k = c->keff[((size_t)s * c->P + p) * 2 + side];
-    int64_t mm = wrap(c, m);
     double w[8];
     int nw;
     if (c->pb.mode == ORC_AT) {
@@ -355,7 +375,7 @@ static void tap(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t m, do
         /* a level with weight 0 (l >= 1 at k = 0) is not part of the scheme;
          * it may not exist yet (start-up), so it is not evaluated at all */
         if (w[l] == 0.0) continue;
-        state_at(c, field(c, level - k - l, s), mm, Q);
+        buffer_state(c, level - k - l, s, m, Q);
         derive(c, Q, gl);
         for (int d = 0; d < c->nder; ++d) g[d] += w[l] * gl[d];
     }
@@ -372,7 +392,7 @@ static double tap_speed(const orc_ctx* c, int64_t level, int s, int64_t p, int64
     } else {
         int side = (m < lo) ? 0 : 1;
         int k = c->keff[((size_t)s * c->P + p) * 2 + side];
-        state_at(c, field(c, level - k, s), wrap(c, m), Q);
+        buffer_state(c, level - k, s, m, Q);
     }
     return wave_speed(c, Q);
 }
@@ -497,16 +517,21 @@ static void set_keff(orc_ctx* c, int64_t level, int s, const int32_t* kforce)
         }
 }
 
+/* The PEs are independent given the delays (each writes K at its own points
+ * only and reads the stored stage arguments), so with OpenMP they are shared
+ * among the host's threads; a point's arithmetic is the same either way. */
 void orc_rhs(orc_ctx* c, int64_t level, int stage, const int32_t* kforce, double* K)
 {
     set_keff(c, level, stage, kforce);
-    double Kp[4];
-    for (int64_t p = 0; p < c->P; ++p)
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < c->P; ++p) {
+        double Kp[4];
         for (int64_t jl = 0; jl < c->B; ++jl) {
             int64_t j = p * c->B + jl;
             rhs_point(c, level, stage, p, j, Kp);
             for (int v = 0; v < c->nvar; ++v) K[(size_t)v * c->N + j] = Kp[v];
         }
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -534,20 +559,30 @@ static void tableau(orc_ctx* c)
     }
 }
 
-static int step(orc_ctx* c)
+void orc_stage_begin(orc_ctx* c, int s)
 {
     int64_t n = c->level;
     size_t nf = (size_t)c->nvar * c->N;
-    for (int s = 0; s < c->S; ++s) {
-        double* U = field(c, n, s);
-        for (size_t i = 0; i < nf; ++i) {
-            double acc = 0.0;
-            for (int r = 0; r < s; ++r) acc += c->a[s][r] * c->K[(size_t)r * nf + i];
-            U[i] = c->u[i] + c->pb.dt * acc;
-        }
-        orc_rhs(c, n, s, c->kfix, c->K + (size_t)s * nf);
+    double* U = field(c, n, s);
+#pragma omp parallel for schedule(static)
+    for (size_t i = 0; i < nf; ++i) {
+        double acc = 0.0;
+        for (int r = 0; r < s; ++r) acc += c->a[s][r] * c->K[(size_t)r * nf + i];
+        U[i] = c->u[i] + c->pb.dt * acc;
     }
+}
+
+void orc_stage_rhs(orc_ctx* c, int s)
+{
+    size_t nf = (size_t)c->nvar * c->N;
+    orc_rhs(c, c->level, s, c->kfix, c->K + (size_t)s * nf);
+}
+
+int orc_step_end(orc_ctx* c)
+{
+    size_t nf = (size_t)c->nvar * c->N;
     int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
     for (size_t i = 0; i < nf; ++i) {
         double acc = 0.0;
         for (int s = 0; s < c->S; ++s) acc += c->b[s] * c->K[(size_t)s * nf + i];
@@ -555,9 +590,45 @@ static int step(orc_ctx* c)
         if (!isfinite(c->u[i])) bad = 1;
     }
     for (size_t i = 0; i < (size_t)c->S * c->P * 2; ++i) c->dlog[i] = (uint8_t)c->keff[i];
-    c->level = n + 1;
+    c->level = c->level + 1;
     return bad ? -4 : 0;
 }
+
+/* one RK step (Eq. rk1): every stage argument, then its right-hand side */
+static int step(orc_ctx* c)
+{
+    for (int s = 0; s < c->S; ++s) {
+        orc_stage_begin(c, s);
+        orc_stage_rhs(c, s);
+    }
+    return orc_step_end(c);
+}
+
+int orc_get_edges(const orc_ctx* c, int64_t level, int s, double* out)
+{
+    if (s < 0 || s >= c->S || level > c->level || level < c->level - c->R + 1) return -1;
+    const double* f = field(c, level, s);
+    for (int side = 0; side < 2; ++side)
+        for (int h = 0; h < c->H; ++h) {
+            int64_t m = side == 0 ? h : c->N - c->H + h;
+            for (int v = 0; v < c->nvar; ++v) out[((size_t)side * c->H + h) * c->nvar + v] = f[(size_t)v * c->N + m];
+        }
+    return 0;
+}
+
+void orc_set_ext(orc_ctx* c, int64_t level, int s, int side, const double* win)
+{
+    int64_t r = level % c->R;
+    if (r < 0) r += c->R;
+    memcpy(c->ext + (((size_t)r * c->S + s) * 2 + side) * c->H * c->nvar, win, (size_t)c->H * c->nvar * sizeof(double));
+}
+
+int orc_delay(const orc_ctx* c, int64_t level, int stage, int64_t pe, int side)
+{
+    return clamp_k(c, level, orc_draw(c, level, stage, pe, side));
+}
+
+int orc_halo(const orc_ctx* c) { return c->H; }
 
 int orc_run(orc_ctx* c, int64_t nsteps)
 {
@@ -606,10 +677,11 @@ orc_ctx* orc_create(const orc_problem* pb, const double* init)
     size_t nf = (size_t)c->nvar * c->N;
     c->u = (double*)malloc(nf * sizeof(double));
     c->hist = (double*)calloc(nf * c->R * c->S, sizeof(double));
+    c->ext = (double*)calloc((size_t)c->R * c->S * 2 * c->H * c->nvar, sizeof(double));
     c->K = (double*)calloc(nf * c->S, sizeof(double));
     c->keff = (int32_t*)calloc((size_t)c->S * c->P * 2, sizeof(int32_t));
     c->dlog = (uint8_t*)calloc((size_t)c->S * c->P * 2, 1);
-    if (!c->u || !c->hist || !c->K || !c->keff || !c->dlog) {
+    if (!c->u || !c->hist || !c->K || !c->keff || !c->dlog || !c->ext) {
         orc_destroy(c);
         return NULL;
     }
@@ -625,10 +697,24 @@ void orc_destroy(orc_ctx* c)
     free(c->trace);
     free(c->u);
     free(c->hist);
+    free(c->ext);
     free(c->K);
     free(c->keff);
     free(c->dlog);
     free(c);
+}
+
+/* Host threads of the OpenMP loops (n < 1: the OpenMP default, all cores);
+ * returns the number of threads that the loops will use (1 without OpenMP). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n >= 1 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 int orc_nvar(const orc_ctx* c) { return c->nvar; }

@@ -43,6 +43,10 @@ typedef struct {
     int64_t pe_base;  /* global index of PE 0 when the problem is a window  */
     int64_t pe_total; /* of a larger domain of pe_total PEs (0: no window);
                          only the delay counter uses them                  */
+    int open_ends;    /* 1: the window's outer PE edges are not periodic: their
+                         buffer points read the edge windows of the PEs
+                         beyond them, supplied with orc_set_ext (a PE range
+                         of one domain split over ranks)                   */
 } orc_problem;
 
 typedef struct orc_ctx orc_ctx;
@@ -60,6 +64,30 @@ int orc_run(orc_ctx* c, int64_t nsteps);
 void orc_get_state(const orc_ctx* c, double* out /* [nvar][n] */);
 /* k_eff of the last completed step, [stages][P][2] (side 0 = left, 1 = right) */
 void orc_get_delays(const orc_ctx* c, uint8_t* out);
+/* host threads for the loops over PEs and points (OpenMP; n < 1: all cores);
+ * returns the thread count in effect.  Results do not depend on it. */
+int orc_set_threads(int n);
+
+/* ---- one RK step stage by stage (what a rank owning a PE range does
+ * between exchanges); orc_run(c, 1) is exactly these calls in order ---- */
+/* form the stage argument U^{n,(s)} of the current level n */
+void orc_stage_begin(orc_ctx* c, int s);
+/* K_s: the right-hand side of stage s (delays drawn, clamped, logged) */
+void orc_stage_rhs(orc_ctx* c, int s);
+/* u^{n+1} from the K_s, level n -> n+1; 0, or -4 on a non-finite value */
+int orc_step_end(orc_ctx* c);
+/* edge windows of U^{level,(s)} at the window's two outer ends:
+ * out[0][h][v] = points 0..H-1, out[1][h][v] = points n-H..n-1; -1 if that
+ * level and stage are not stored */
+int orc_get_edges(const orc_ctx* c, int64_t level, int s, double* out);
+/* open_ends: the edge window of U^{level,(s)} of the PE beyond side `side`
+ * (0: left of point 0, the neighbour's right edge, points in increasing x;
+ * 1: right of point n-1, the neighbour's left edge), [H][nvar] */
+void orc_set_ext(orc_ctx* c, int64_t level, int s, int side, const double* win);
+/* the delay PE `pe` uses at (level, stage, side): the draw through the
+ * start-up clamp (0 in SYNC mode) */
+int orc_delay(const orc_ctx* c, int64_t level, int stage, int64_t pe, int side);
+int orc_halo(const orc_ctx* c);
 
 /* ---- pieces exposed for the pins in tests/ ---- */
 /* copy the stored stage argument U^{level,(stage)} (a full field [nvar][n]);

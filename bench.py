@@ -1,11 +1,13 @@
 """Benchmark: grid-point updates/s of the AT RK-stage right-hand side on GB300.
 
 One step = one full Runge-Kutta step (every stage) over the whole domain of
-the workload, inputs resident in HBM.  Default workload: the reacting
-Navier-Stokes premixed flame, N = 16,384 FP64 points in 256 virtual PEs of
-64, 6th-order central + AT6, classic RK4, delays uniform on {0..4} (Philox
-seed 0).  The timed region is one at_step(K) call; its 512 KB state fits in
-L2, so L2 is flushed (a 256 MiB write) right before it.
+the workload, inputs resident in HBM.  Default workload: the reactive-Euler
+detonation, N = 2^24 FP64 points (4 fields, 512 MiB of state, larger than
+L2) in 16,384 virtual PEs of 1024, WENO5 + AT-WENO5 with local
+Lax-Friedrichs splitting, RK3-TVD, delays geometric (p = 0.5) on {0..4}
+(Philox seed 0): the largest configuration that fits one GPU.  The timed
+region is one at_step(K) call.  Workloads whose state fits in L2 flush it (a
+256 MiB write) right before the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...      # the CPU oracle on host cores
@@ -49,7 +51,7 @@ WORKLOADS = {
     # [512, 262,144], 100..5,000 steps: a burst of --serve-requests requests
     "serving-mixed": dict(kind="serving", rate=2000.0, seed=0),
 }
-DEFAULT = "rns-flame-n16384"
+DEFAULT = "detonation-n16777216"
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal, at 2070 MHz boost
 
 # FP64 flops per point per stage (FMA = 2, add/mul = 1) that the timed kernel
@@ -66,6 +68,16 @@ FLOPS_PER_POINT_STAGE = {
     ("advdiff", "persistent"): 13.56,
     ("advdiff", "fused"): 13.56,     # the method's work only (13.65 as executed, with the recomputed edge points)
 }
+# The method's own FP64 work per point per stage, by operation count (a
+# divide, square root or exponential counts as one operation): the
+# detonation's WENO5 + AT-WENO5 stage ~550 flops + 8 divides + 1 sqrt + 1 exp
+# (two reconstructions per variable and edge, the splitting, the Arrhenius
+# source, the update); the reacting flow's central6 stage ~150 flops + 4
+# divides + 1 exp; advection-diffusion 52 flops per RK4 step.  The executed
+# counts above also hold the instruction sequences of exp and the
+# reciprocals and the AT halo work; achieved / peak on this count is
+# roofline.frac_algorithmic.
+ALG_FLOPS_PER_POINT_STAGE = {"detonation": 560.0, "rns": 155.0, "advdiff": 13.0}
 # Algorithmic HBM bytes per point per stage of the per-stage path: the arrays
 # a step reads and writes (RK4: 17 arrays, RK3-TVD: 8) x nvar x 8 B / stages.
 BYTES_PER_POINT_STAGE = {"rns": 17 * 4 * 8 / 4, "detonation": 8 * 4 * 8 / 3, "advdiff": 17 * 8 / 4}
@@ -86,6 +98,24 @@ TRAFFIC_PER_LAUNCH = {
     ("advdiff-n2048", "persistent"): 7.7824e4,  # one-cluster launch: state and ring read once
     ("advdiff-n16384", "fused"): 2.8288e5,  # cooperative fused launch: state and ring read once
 }
+
+
+# The kernel sources the captured counts above were taken from: sha256 of
+# csrc/*.cu and *.cuh (sorted by name, concatenated).  When the sources
+# change, the counts may no longer hold: the roofline is then marked stale
+# and its traffic is reported as null until the captures are redone.
+PROFILED_SOURCES_SHA256 = "e92dcf6714ac29432d2d567f8ec26336928508b0f0d2031c7e36622ec42ce6f0"
+
+
+def sources_sha256() -> str:
+    import hashlib
+    d = os.path.join(ROOT, "paper_2204_01133_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
 
 
 def kernel_label(kind, path, pb, arrival=False):
@@ -192,11 +222,13 @@ def dist_env():
 
 
 def run_reference(args):
-    """The CPU oracle, as it stands, on this host's cores (single thread)."""
+    """The CPU oracle, as it stands, on this host's cores (OpenMP over PEs,
+    every core)."""
     import oracle
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    cores = oracle.set_threads(0)
     if WORKLOADS[args.workload]["kind"] == "batched":
         from paper_2204_01133_gb300 import workloads as W
         cfg = WORKLOADS[args.workload]
@@ -210,13 +242,13 @@ def run_reference(args):
             o.run(n)
         dt = time.perf_counter() - t0
         value = len(sample) / dt
-        what = "%d random instances of the batch, %d RK4 steps each, single thread" % (len(sample), args.steps)
+        what = "%d random instances of the batch, %d RK4 steps each, %d threads" % (len(sample), args.steps, cores)
         print(json.dumps({
             "impl": "reference", "metric": "batched solves/s", "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "instances": cfg["count"]},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": what},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": what},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
         return
@@ -235,12 +267,12 @@ def run_reference(args):
             nreq += st / d["steps"]
         dt = time.perf_counter() - t0
         value = nreq / dt
-        what = "first 3 requests of the stream, up to 50 of their steps each, single thread"
+        what = "first 3 requests of the stream, up to 50 of their steps each, %d threads" % cores
         print(json.dumps({
             "impl": "reference", "metric": "served solves/s", "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": args.workload},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": what,
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": what,
                              "grid_pt_updates_per_s": pts / dt},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
@@ -257,6 +289,7 @@ def run_reference(args):
         init = init[:, :npe * B].copy()
         sample = "window of %d PEs (%d points) of the %d-point domain, one oracle RK step per step" % (
             npe, npe * B, n)
+    sample += ", %d threads (OpenMP over PEs)" % cores
     o = oracle.Oracle(pb, init)
     o.run(args.warmup)
     t0 = time.perf_counter()
@@ -269,7 +302,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": wl,
-        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -285,7 +318,11 @@ def describe(name, pb):
     return d
 
 
-def cpu_baseline(pb, init, budget_s=12.0):
+def cpu_baseline(pb, init, budget_s=10.0):
+    """The oracle, as it stands, on this host: one thread, then every core
+    (OpenMP over PEs; the arithmetic per point is the same).  Each leg runs a
+    bounded number of RK steps (about ``budget_s`` seconds) on a window of
+    whole PEs for large domains."""
     import oracle
     n = pb["n"]
     sample_pb, sample_init, what = pb, init, "full domain"
@@ -294,17 +331,25 @@ def cpu_baseline(pb, init, budget_s=12.0):
         npe = max(1, 65536 // B)
         sample_pb = dict(pb, n=npe * B, pe_base=0, pe_total=n // B)
         sample_init = init[:, :npe * B].copy()
-        what = "window of %d PEs (%d points)" % (npe, npe * B)
-    o = oracle.Oracle(sample_pb, sample_init)
-    t0 = time.perf_counter()
-    o.run(2)
-    per = (time.perf_counter() - t0) / 2
-    steps = max(2, min(2000, int(budget_s / max(per, 1e-6))))
-    t0 = time.perf_counter()
-    o.run(steps)
-    dt = time.perf_counter() - t0
-    return {"value": sample_pb["n"] * steps / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
-            "sample": "%s, %d RK steps, single thread" % (what, steps)}
+        what = "window of %d PEs (%d points) of the %d-point domain, global PE indices" % (npe, npe * B, n)
+    legs = []
+    for threads in (1, 0):
+        used = oracle.set_threads(threads)
+        o = oracle.Oracle(sample_pb, sample_init)
+        t0 = time.perf_counter()
+        o.run(2)
+        per = (time.perf_counter() - t0) / 2
+        steps = max(2, min(2000, int(budget_s / max(per, 1e-6))))
+        t0 = time.perf_counter()
+        o.run(steps)
+        dt = time.perf_counter() - t0
+        legs.append({"value": sample_pb["n"] * steps / dt, "cores": used, "steps": steps})
+    oracle.set_threads(0)
+    one, allc = legs
+    return {"value": allc["value"], "unit": "updates/s", "cores": allc["cores"], "kind": "oracle",
+            "sample": "%s, %d RK steps on %d threads (OpenMP over PEs)" % (what, allc["steps"], allc["cores"]),
+            "single_thread": {"value": one["value"], "cores": 1,
+                              "sample": "%s, %d RK steps, one thread" % (what, one["steps"])}}
 
 
 def run_batched(args):
@@ -544,8 +589,15 @@ def run_ours(args):
     if rank == 0:
         fl = FLOPS_PER_POINT_STAGE[(kind, path)] * units_per_launch  # per launch
         achieved = fl / (launch_ms * 1e-3) / 1e12
+        stale = sources_sha256() != PROFILED_SOURCES_SHA256
+        alg = ALG_FLOPS_PER_POINT_STAGE[kind] * units_per_launch / (launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, path)),
+                "frac": achieved / NOMINAL_FP64_TFLOPS,
+                "traffic": None if stale else TRAFFIC_PER_LAUNCH.get((args.workload, path)),
+                "stale": stale,
+                "achieved_algorithmic": alg, "frac_algorithmic": alg / NOMINAL_FP64_TFLOPS,
+                "alg_flops_per_point_stage": ALG_FLOPS_PER_POINT_STAGE[kind],
+                "exec_flops_per_point_stage": FLOPS_PER_POINT_STAGE[(kind, path)],
                 "kernel": ("steps_fused_" + kind) if path == "fused" and fused_steps > 1
                           else kernel_label(kind, path, pb, args.arrival),
                 "avg_launch_ms": launch_ms, "launches_timed": int(st.launches_timed),

@@ -43,6 +43,8 @@ WORKLOADS = {
     # a quarter of the HBM run, for counter captures (inputs still larger than L2)
     "advdiff-n33554432": dict(kind="advdiff", n=1 << 25, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075),
     "detonation-n16777216": dict(kind="detonation", n=1 << 24, pe_size=1024, mode="at", k_max=4, seed=0),
+    # half of it, for counter captures (inputs still larger than L2)
+    "detonation-n8388608": dict(kind="detonation", n=1 << 23, pe_size=1024, mode="at", k_max=4, seed=0),
     "rns-flame-n16777216": dict(kind="rns", case="flame", n=1 << 24, pe_size=64, mode="at", k_max=4, seed=0,
                                 dt=0.003),
     # 4,096 reacting instances, N log-uniform in [256, 8192] (9.4 M points), one batched launch

@@ -40,7 +40,8 @@ int at_probe_pipe_mix(int device, int kind, int with_fp64, int iters, int reps, 
 /* y[i] = f(x[i]) for device arrays x, y of n doubles (caller-owned device
  * memory, current device): which = 0 the stage kernels' table-driven
  * exponential, 1 CUDA's exp, 2 the stage kernels' Newton reciprocal, 3 IEEE
- * 1/x.  Runs on the default stream and synchronises the device. */
+ * 1/x, 4 the WENO kernels' cubic-step reciprocal.  Runs on the default
+ * stream and synchronises the device. */
 int at_probe_fn(const double* x, double* y, int64_t n, int which);
 
 #ifdef __cplusplus

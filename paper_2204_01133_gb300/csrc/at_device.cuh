@@ -169,6 +169,21 @@ __device__ __forceinline__ double at_rcp(double x)
     return fma(r, e, r);
 }
 
+// 1/x by one cubic Newton step from the hardware's approximate reciprocal:
+// with e = 1 - x r, 1/x = r (1 + e + e^2 + ...), so r + r (e + e^2) cubes the
+// relative error of r (Householder's method of order 3, e.g. Householder,
+// "The Numerical Treatment of a Single Nonlinear Equation", 1970), one FP64
+// instruction fewer than at_rcp's two quadratic steps, within about an ulp
+// of 1/x for normal, finite, nonzero x.  Used where a reciprocal serves
+// only one product (the WENO weight normalisation).
+__device__ __forceinline__ double at_rcp3(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    const double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+
 // Inf or NaN: exponent field all ones, tested on the high word with integer
 // instructions (the FP64 pipe is the scarce one on this chip)
 __device__ __forceinline__ bool nonfinite(double v)
@@ -295,6 +310,26 @@ struct Phys<EULER> {
         const double p = pressure(a, Q, u);
         return fabs(u) + sqrt(a.prm[0] * p * rinv);
     }
+    // derive() and speed() of one point at once (1/rho, u and p formed once,
+    // by the same operations), and with ARR the Arrhenius factor
+    // exp(-Ea rho / p) of the point's reaction source
+    template <bool ARR>
+    __device__ static void derive_weno(const StageArgs& a, const double* Q, double* g, double& sp, double& arr)
+    {
+        const double rinv = at_rcp(Q[0]);
+        const double u = Q[1] * rinv;
+        const double p = pressure(a, Q, u);
+        g[0] = 0.5 * Q[1];
+        g[1] = 0.5 * fma(Q[1], u, p);
+        g[2] = 0.5 * (u * (Q[2] + p));
+        g[3] = 0.5 * (Q[3] * u);
+        g[4] = Q[0];
+        g[5] = Q[1];
+        g[6] = Q[2];
+        g[7] = Q[3];
+        sp = fabs(u) + sqrt(a.prm[0] * p * rinv);
+        if constexpr (ARR) arr = at_exp(-a.prm[2] * Q[0] * at_rcp(p));
+    }
 };
 
 // Scalar linear advection, WENO form: g = [c u / 2, u].
@@ -307,6 +342,12 @@ struct Phys<ADV_WENO> {
         g[1] = Q[0];
     }
     __device__ static double speed(const StageArgs& a, const double*) { return fabs(a.prm[0]); }
+    template <bool ARR>
+    __device__ static void derive_weno(const StageArgs& a, const double* Q, double* g, double& sp, double&)
+    {
+        derive(a, Q, g);
+        sp = speed(a, Q);
+    }
 };
 
 // Inviscid Burgers, WENO form: g = [u^2 / 4, u] (C/2 with C = u^2/2); speed |u|.
@@ -319,6 +360,12 @@ struct Phys<BURGERS> {
         g[1] = Q[0];
     }
     __device__ static double speed(const StageArgs&, const double* Q) { return fabs(Q[0]); }
+    template <bool ARR>
+    __device__ static void derive_weno(const StageArgs& a, const double* Q, double* g, double& sp, double&)
+    {
+        derive(a, Q, g);
+        sp = speed(a, Q);
+    }
 };
 
 } // namespace atk

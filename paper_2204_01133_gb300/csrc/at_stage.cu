@@ -53,7 +53,7 @@ __device__ __forceinline__ Cx launch_cx(const StageArgs& a) { return Cx{a.level,
 template <int PDE, bool WENO>
 __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, double* __restrict__ G,
                                             double* __restrict__ SP, double* __restrict__ HS, int64_t pe, int chunk,
-                                            int64_t t0, int W2, int lt, int gs)
+                                            int64_t t0, int W2, int lt, int gs, double* __restrict__ ARR = nullptr)
 {
     using P = Phys<PDE>;
     constexpr int NV = P::NV, ND = P::ND;
@@ -71,10 +71,16 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
             const int64_t m = t0 - H + i;
 #pragma unroll
             for (int v = 0; v < NV; ++v) Q[v] = cx.X[v * a.N + m];
-            P::derive(a, Q, g);
+            if constexpr (WENO) {
+                double sp, arr;
+                P::template derive_weno<PDE == EULER>(a, Q, g, sp, arr);
+                SP[i] = sp;
+                if constexpr (PDE == EULER) ARR[i] = arr;  // the reaction source's exp(-Ea rho / p)
+            } else {
+                P::derive(a, Q, g);
+            }
 #pragma unroll
             for (int d = 0; d < ND; ++d) G[d * W2 + i] = g[d];
-            if constexpr (WENO) SP[i] = P::speed(a, Q);
         } else {
             const int t = it - own;
             const int hp = t / nw, l = t - hp * nw;         // buffer point, level
@@ -87,9 +93,16 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
                 const int64_t base = ring_index(a, cx.level - k - l, cx.stage, nbr, 1 - side, h, 0);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) Q[v] = a.ring[base + v];
-                P::derive(a, Q, g);
                 if constexpr (WENO) {
-                    if (l == 0) SP[side == 0 ? h : W2 - R0 + h] = P::speed(a, Q);  // level n-k, not extrapolated
+                    if (l == 0) {  // the wave speed at level n-k, not extrapolated
+                        double sp, unused;
+                        P::template derive_weno<false>(a, Q, g, sp, unused);
+                        SP[side == 0 ? h : W2 - R0 + h] = sp;
+                    } else {
+                        P::derive(a, Q, g);
+                    }
+                } else {
+                    P::derive(a, Q, g);
                 }
 #pragma unroll
                 for (int d = 0; d < ND; ++d) HS[t * ND + d] = g[d];
@@ -384,34 +397,37 @@ __global__ void __launch_bounds__(256, PPL <= 2 ? 6 : (PPL == 4 ? 4 : 3)) stage_
 // (candidates of Eq. atRecon at k = 0, ideal weights {1/10, 3/5, 3/10},
 // indicators of Eq. betaS, weights of Eq. omg with power 2), arranged for
 // few FP64 instructions without changing the mathematics:
-//  * the indicators are formed as 12 beta_i = 13 s_i^2 + 3 r_i^2 (with
-//    s_i the second difference and r_0, r_2 built from s_0, s_2) and eps as
-//    12 eps: the weights omega_i = alpha_i / sum alpha are unchanged by a
-//    common factor of the indicators and eps;
-//  * the three weights share one reciprocal: alpha_i ~ gamma_i prod_{j!=i}
-//    d_j^2, with gamma_i and the candidates' 1/6 folded into constants.
-// eps12 = 12 eps.
+//  * with the second differences s_i (centred on f[i+1]) and the first
+//    differences r_0 = f0 - 4 f1 + 3 f2, r_1 = f1 - f3, r_2 = 3 f2 - 4 f3 + f4,
+//    beta_i = (13 s_i^2 + 3 r_i^2) / 12, so D_i = 4 (eps + beta_i) =
+//    (13/3) s_i^2 + r_i^2 + 4 eps; the weights omega_i = alpha_i / sum alpha
+//    do not change when every eps + beta_i is scaled by the same 4;
+//  * the candidates differ from the middle one by third differences,
+//    p_0 - p_1 = (s_0 - s_1) / 3 and p_2 - p_1 = (s_1 - s_2) / 6, so
+//    sum omega_i p_i = p_1 + omega_0 (p_0 - p_1) + omega_2 (p_2 - p_1);
+//  * alpha_i ~ gamma_i / D_i^2 times the common factor D_0^2 D_1^2 D_2^2, and
+//    numerator and denominator scaled by 60:
+//      num = E_1 (2 E_2 (s_0 - s_1) + 3 E_0 (s_1 - s_2)),
+//      den = E_1 (6 E_2 + 18 E_0) + 36 E_0 E_2,  E_i = D_i^2,
+//    with one reciprocal.
+// eps4 = 4 eps.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double weno5(double f0, double f1, double f2, double f3, double f4, double eps12)
+__device__ __forceinline__ double weno5(double f0, double f1, double f2, double f3, double f4, double eps4)
 {
-    // gamma_i x 6 x candidate: 6 p0 = 2f0 - 7f1 + 11f2, 6 p1 = -f1 + 5f2 + 2f3, 6 p2 = 2f2 + 5f3 - f4
-    const double g0 = fma(0.2, f0, fma(-0.7, f1, 1.1 * f2));   // 0.1 (2 f0 - 7 f1 + 11 f2)
-    const double g1 = fma(-0.6, f1, fma(3.0, f2, 1.2 * f3));   // 0.6 (-f1 + 5 f2 + 2 f3)
-    const double g2 = fma(0.6, f2, fma(1.5, f3, -0.3 * f4));   // 0.3 (2 f2 + 5 f3 - f4)
     const double s0 = fma(-2.0, f1, f0) + f2;
     const double s1 = fma(-2.0, f2, f1) + f3;
     const double s2 = fma(-2.0, f3, f2) + f4;
     const double r0 = fma(2.0, f2 - f1, s0);  // f0 - 4 f1 + 3 f2
     const double r1 = f1 - f3;
     const double r2 = fma(2.0, f2 - f3, s2);  // 3 f2 - 4 f3 + f4
-    const double d0 = fma(13.0 * s0, s0, fma(3.0 * r0, r0, eps12));  // 12 (eps + beta_0)
-    const double d1 = fma(13.0 * s1, s1, fma(3.0 * r1, r1, eps12));
-    const double d2 = fma(13.0 * s2, s2, fma(3.0 * r2, r2, eps12));
+    const double d0 = fma((13.0 / 3.0) * s0, s0, fma(r0, r0, eps4));
+    const double d1 = fma((13.0 / 3.0) * s1, s1, fma(r1, r1, eps4));
+    const double d2 = fma((13.0 / 3.0) * s2, s2, fma(r2, r2, eps4));
     const double e0 = d0 * d0, e1 = d1 * d1, e2 = d2 * d2;
-    const double a0 = e1 * e2, a1 = e0 * e2, a2 = e0 * e1;   // alpha_i / gamma_i, common factor dropped
-    const double num = fma(a0, g0, fma(a1, g1, a2 * g2));
-    const double den = fma(0.6, a0, fma(3.6, a1, 1.8 * a2)); // 6 sum gamma_i a_i
-    return num * at_rcp(den);
+    const double num = e1 * fma(2.0 * e2, s0 - s1, (3.0 * e0) * (s1 - s2));
+    const double den = fma(e1, fma(6.0, e2, 18.0 * e0), 36.0 * (e0 * e2));
+    const double p1 = fma(-1.0 / 6.0, f1, fma(5.0 / 6.0, f2, (1.0 / 3.0) * f3));  // (-f1 + 5 f2 + 2 f3) / 6
+    return fma(num, at_rcp3(den), p1);
 }
 
 // ---------------------------------------------------------------------------
@@ -428,18 +444,19 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
     const int E = Tw + 1;  // edges of the window: edge e sits between points e-1 and e
     double* G = sm;
     double* SP = G + ND * W2;
-    double* LAM = SP + W2;
+    double* ARR = SP + W2;
+    double* LAM = ARR + W2;
     double* REC = LAM + E;
     double* HS = REC + NV * 2 * E;
     const int64_t pe = a.wpp == 1 ? win : win / a.wpp;  // a 64-bit division only where PEs hold several windows
     const int chunk = (int)(win - pe * a.wpp);
     const int64_t t0 = pe * a.B + (int64_t)chunk * Tw;
-    fill_window<PDE, true>(a, cx, G, SP, HS, pe, chunk, t0, W2, threadIdx.x, blockDim.x);
+    fill_window<PDE, true>(a, cx, G, SP, HS, pe, chunk, t0, W2, threadIdx.x, blockDim.x, ARR);
     __syncthreads();
     for (int e = threadIdx.x; e < E; e += blockDim.x)
         LAM[e] = 0.5 * fmax(SP[e - 1 + H], SP[e + H]);  // half the edge's local wave speed
     __syncthreads();
-    const double eps12 = 12.0 * ((PDE == EULER) ? a.prm[4] : a.prm[1]);
+    const double eps4 = 4.0 * ((PDE == EULER) ? a.prm[4] : a.prm[1]);
     const int items = NV * 2 * E;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int r = it / E;
@@ -451,11 +468,11 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
         double rec;
         if ((r & 1) == 0) {  // f+ = C/2 + (lam/2) Q on points e-3..e+1
             rec = weno5(fma(hl, Qv[e], C[e]), fma(hl, Qv[e + 1], C[e + 1]), fma(hl, Qv[e + 2], C[e + 2]),
-                        fma(hl, Qv[e + 3], C[e + 3]), fma(hl, Qv[e + 4], C[e + 4]), eps12);
+                        fma(hl, Qv[e + 3], C[e + 3]), fma(hl, Qv[e + 4], C[e + 4]), eps4);
         } else {  // f- = C/2 - (lam/2) Q on points e+2..e-2 (mirrored)
             rec = weno5(fma(-hl, Qv[e + 5], C[e + 5]), fma(-hl, Qv[e + 4], C[e + 4]),
                         fma(-hl, Qv[e + 3], C[e + 3]), fma(-hl, Qv[e + 2], C[e + 2]),
-                        fma(-hl, Qv[e + 1], C[e + 1]), eps12);
+                        fma(-hl, Qv[e + 1], C[e + 1]), eps4);
         }
         REC[r * E + e] = rec;
     }
@@ -471,19 +488,14 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
         double K = (Fl - Fr) * rdx;
         const double x = G[(NV + v) * W2 + c];
         if constexpr (PDE == EULER) {
-            if (v == 3) {
-                const double Q[4] = {G[4 * W2 + c], G[5 * W2 + c], G[6 * W2 + c], G[7 * W2 + c]};
-                const double u = Q[1] * at_rcp(Q[0]);
-                const double p = P::pressure(a, Q, u);
-                K = fma(-a.prm[1] * Q[3], at_exp(-a.prm[2] * Q[0] * at_rcp(p)), K);
-            }
+            if (v == 3) K = fma(-a.prm[1] * x, ARR[c], K);  // x = rho Y; ARR from the fill
         }
         rk_update<RKS>(a, cx, v, j, chunk * Tw + jl, pe, K, x, rk_load<RKS>(a, cx, v * a.N + j));
     }
 }
 
 template <int PDE, int RKS>
-__global__ void __launch_bounds__(256) stage_weno(const StageArgs a)
+__global__ void __launch_bounds__(256, 5) stage_weno(const StageArgs a)
 {
     extern __shared__ double sm[];
     weno_window<PDE, RKS>(a, launch_cx(a), blockIdx.x, sm);
@@ -606,8 +618,8 @@ size_t atk_stage_smem_bytes(int pde, int Tw, int H)
     case atk::ADVDIFF: return sizeof(double) * (W2 + hs * 1);
     case atk::RNS: return sizeof(double) * (8 * W2 + hs * 8);
     case atk::RNS_CHAIN: return sizeof(double) * (6 * W2 + hs * 6);
-    case atk::EULER: return sizeof(double) * (9 * W2 + E + 8 * E + hs * 8);
-    default: return sizeof(double) * (3 * W2 + E + 2 * E + hs * 2);
+    case atk::EULER: return sizeof(double) * (10 * W2 + E + 8 * E + hs * 8);
+    default: return sizeof(double) * (4 * W2 + E + 2 * E + hs * 2);
     }
 }
 

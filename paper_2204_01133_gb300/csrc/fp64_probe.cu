@@ -151,18 +151,20 @@ __global__ void fn_eval(const double* __restrict__ x, double* __restrict__ y, in
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = x[i];
-        y[i] = which == 0 ? atk::at_exp(v) : which == 1 ? exp(v) : which == 2 ? atk::at_rcp(v) : 1.0 / v;
+        y[i] = which == 0 ? atk::at_exp(v) : which == 1 ? exp(v) : which == 2 ? atk::at_rcp(v)
+             : which == 4 ? atk::at_rcp3(v) : 1.0 / v;
     }
 }
 } // namespace
 
 // y[i] = f(x[i]) for device arrays of n doubles, on the default stream,
 // synchronous: which = 0 the kernels' table-driven exponential at_exp,
-// 1 CUDA's exp, 2 the kernels' Newton reciprocal at_rcp, 3 IEEE 1/x.
+// 1 CUDA's exp, 2 the kernels' Newton reciprocal at_rcp, 3 IEEE 1/x, 4 the
+// kernels' cubic-step reciprocal at_rcp3.
 extern "C" int at_probe_fn(const double* x, double* y, int64_t n, int which)
 {
     if (n <= 0) return 0;
-    if (which < 0 || which > 3) return -1;
+    if (which < 0 || which > 4) return -1;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     fn_eval<<<blocks, 256>>>(x, y, n, which);

@@ -1,6 +1,7 @@
 """The stage kernels' own exponential (Tang's table-driven method, 64
-entries) and reciprocal (two Newton steps from the hardware approximation),
-against the host C library and CUDA, through libat_probe.so."""
+entries) and reciprocals (two Newton steps, or one cubic step, from the
+hardware approximation), against the host C library and CUDA, through
+libat_probe.so."""
 import ctypes
 import math
 import os
@@ -62,7 +63,8 @@ def test_table_exp_matches_cuda_exp_outside_fast_path(probe):
     assert (np.abs(probe(_inputs(), 0) - near) / np.spacing(near)).max() <= 3.0
 
 
-def test_newton_reciprocal_within_one_ulp(probe):
+@pytest.mark.parametrize("which", [2, 4], ids=["two-quadratic-steps", "one-cubic-step"])
+def test_newton_reciprocal_within_one_ulp(probe, which):
     rng = np.random.default_rng(3)
     x = np.concatenate([
         np.exp(rng.uniform(np.log(1e-6), np.log(1e6), 1 << 20)),   # densities, pressures, weight sums
@@ -70,7 +72,8 @@ def test_newton_reciprocal_within_one_ulp(probe):
         2.0 ** np.arange(-60, 61), np.nextafter(2.0 ** np.arange(-60, 61), 0.0),
         1.0 + np.arange(1, 4097) * 2.0 ** -52, 2.0 - np.arange(1, 4097) * 2.0 ** -52,
     ])
-    got = probe(x, 2)
+    x = np.concatenate([x, np.exp(rng.uniform(np.log(1e-30), np.log(1e30), 1 << 18))])  # WENO weight sums
+    got = probe(x, which)
     ref = 1.0 / x                      # IEEE division on the host: correctly rounded
     assert np.array_equal(probe(x, 3), ref)
     ulps = np.abs(got - ref) / np.spacing(np.abs(ref))

@@ -65,7 +65,7 @@ NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal, at 2070 M
 FLOPS_PER_POINT_STAGE = {
     ("rns", "stage"): 176.3,         # central6 + AT6, 4 variables (RK4 stage 1 counted)
     ("rns", "persistent"): 177.0,    # same work, all K steps of one launch
-    ("detonation", "stage"): 796.9,  # WENO5 + AT-WENO5, 8 reconstructions per edge (RK3 stage 0)
+    ("detonation", "stage"): 678.9,  # WENO5 + AT-WENO5, 8 reconstructions per edge (RK3 stage 0)
     ("advdiff", "stage"): 13.56,     # 5-tap merged stencil + RK4 update, mean of the 4 stages
     ("advdiff", "persistent"): 13.56,
     ("advdiff", "fused"): 13.56,     # the method's work only (13.65 as executed, with the recomputed edge points)
@@ -92,7 +92,7 @@ BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4}
 TRAFFIC_PER_LAUNCH = {
     ("rns-flame-n16384", "persistent"): 2.5390e6,  # state and rings read once, writes stay in L2
     ("rns-flame-n16777216", "stage"): 1.6610e9 + 1.0863e9,
-    ("detonation-n16777216", "stage"): 5.4581e8 + 4.9380e8,
+    ("detonation-n16777216", "stage"): 2 * (2.7273e8 + 2.2529e8),  # captured at N = 2^23, x2
     ("advdiff-n134217728", "stage"): 4 * (8.7079e8 + 5.1163e8),
     ("advdiff-n33554432", "stage"): 8.7079e8 + 5.1163e8,
     ("advdiff-n134217728", "fused"): 4 * (4.6984e8 + 3.0259e8),  # one step: u^n, u^{n+1}, the ring
@@ -106,7 +106,7 @@ TRAFFIC_PER_LAUNCH = {
 # csrc/*.cu and *.cuh (sorted by name, concatenated).  When the sources
 # change, the counts may no longer hold: the roofline is then marked stale
 # and its traffic is reported as null until the captures are redone.
-PROFILED_SOURCES_SHA256 = "e92dcf6714ac29432d2d567f8ec26336928508b0f0d2031c7e36622ec42ce6f0"
+PROFILED_SOURCES_SHA256 = "ac787879bc04368984897f205943f9375f3515bb345408ff48fdb57f986b7d55"
 
 
 def sources_sha256() -> str:

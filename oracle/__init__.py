@@ -47,6 +47,7 @@ class _Problem(ctypes.Structure):
         ("pe_base", ctypes.c_int64),
         ("pe_total", ctypes.c_int64),
         ("open_ends", ctypes.c_int),
+        ("history", ctypes.c_int),
     ]
 
 
@@ -149,6 +150,7 @@ def _problem(pb: dict) -> _Problem:
     s.pe_base = int(pb.get("pe_base", 0))
     s.pe_total = int(pb.get("pe_total", 0))
     s.open_ends = int(pb.get("open_ends", 0))
+    s.history = {"stage": 0, "recompute": 1}[pb.get("history", "stage")]
     return s
 
 

@@ -68,6 +68,8 @@ struct orc_ctx {
     uint8_t* trace;            /* delays of every (step, stage, PE, side) to replay, or NULL */
     int64_t trace_n0, trace_steps;
     double* ext;   /* open ends: edge windows beyond the window [R][S][2][H][nvar] */
+    double* syncf; /* reading A: synchronous stage arguments [R][S][nvar][N] */
+    struct orc_ctx* shadow; /* reading A: the same problem in SYNC mode    */
 };
 
 /* ------------------------------------------------------------------ */
@@ -334,6 +336,12 @@ static int64_t wrap(const orc_ctx* c, int64_t m)
  * PE there */
 static void buffer_state(const orc_ctx* c, int64_t level, int s, int64_t m, double* Q)
 {
+    if (c->pb.history == 1) { /* reading A: the synchronous recomputation from u^level */
+        int64_t r = level % c->R;
+        if (r < 0) r += c->R;
+        state_at(c, c->syncf + ((size_t)r * c->S + s) * (size_t)c->nvar * c->N, wrap(c, m), Q);
+        return;
+    }
     if (c->pb.open_ends && (m < 0 || m >= c->N)) {
         int side = (m < 0) ? 0 : 1;
         int64_t h = (m < 0) ? m + c->H : m - c->N;
@@ -559,9 +567,28 @@ static void tableau(orc_ctx* c)
     }
 }
 
+/* Reading A (Sec. 2.3, the receiver forms the stage values at old levels
+ * itself): the stage arguments of level m as a synchronous RK step from the
+ * actual u^m would form them, no delay anywhere (the shadow context runs the
+ * same problem in SYNC mode), kept for every level a buffer point can read. */
+static void sync_stages(orc_ctx* c)
+{
+    orc_ctx* sh = c->shadow;
+    size_t nf = (size_t)c->nvar * c->N;
+    memcpy(sh->u, c->u, nf * sizeof(double));
+    sh->level = c->level;
+    int64_t r = c->level % c->R;
+    for (int s = 0; s < c->S; ++s) {
+        orc_stage_begin(sh, s);
+        memcpy(c->syncf + ((size_t)r * c->S + s) * nf, field(sh, sh->level, s), nf * sizeof(double));
+        if (s < c->S - 1) orc_stage_rhs(sh, s);
+    }
+}
+
 void orc_stage_begin(orc_ctx* c, int s)
 {
     int64_t n = c->level;
+    if (s == 0 && c->pb.history == 1) sync_stages(c);
     size_t nf = (size_t)c->nvar * c->N;
     double* U = field(c, n, s);
 #pragma omp parallel for schedule(static)
@@ -646,6 +673,7 @@ orc_ctx* orc_create(const orc_problem* pb, const double* init)
     if (pb->pe_size <= 0 || pb->n <= 0 || pb->n % pb->pe_size) return NULL;
     if (pb->k_max < 0 || pb->k_max > 15) return NULL;
     if (pb->pde < 0 || pb->pde > 5) return NULL;
+    if (pb->history < 0 || pb->history > 1 || (pb->history == 1 && pb->open_ends)) return NULL;
     orc_ctx* c = (orc_ctx*)calloc(1, sizeof *c);
     if (!c) return NULL;
     c->pb = *pb;
@@ -678,6 +706,18 @@ orc_ctx* orc_create(const orc_problem* pb, const double* init)
     c->u = (double*)malloc(nf * sizeof(double));
     c->hist = (double*)calloc(nf * c->R * c->S, sizeof(double));
     c->ext = (double*)calloc((size_t)c->R * c->S * 2 * c->H * c->nvar, sizeof(double));
+    if (pb->history == 1) {
+        orc_problem spb = *pb;
+        spb.mode = ORC_SYNC;
+        spb.history = 0;
+        spb.open_ends = 0;
+        c->shadow = orc_create(&spb, init);
+        c->syncf = (double*)calloc(nf * c->R * c->S, sizeof(double));
+        if (!c->shadow || !c->syncf) {
+            orc_destroy(c);
+            return NULL;
+        }
+    }
     c->K = (double*)calloc(nf * c->S, sizeof(double));
     c->keff = (int32_t*)calloc((size_t)c->S * c->P * 2, sizeof(int32_t));
     c->dlog = (uint8_t*)calloc((size_t)c->S * c->P * 2, 1);
@@ -698,6 +738,8 @@ void orc_destroy(orc_ctx* c)
     free(c->u);
     free(c->hist);
     free(c->ext);
+    free(c->syncf);
+    orc_destroy(c->shadow);
     free(c->K);
     free(c->keff);
     free(c->dlog);

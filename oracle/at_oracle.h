@@ -47,6 +47,11 @@ typedef struct {
                          buffer points read the edge windows of the PEs
                          beyond them, supplied with orc_set_ext (a PE range
                          of one domain split over ranks)                   */
+    int history;      /* what a buffer point reads at a delayed level m and
+                         stage s (Sec. 2.3): 0 (reading B) the neighbour's
+                         stage argument U^{m,(s)} as the neighbour computed
+                         it; 1 (reading A) the stage argument recomputed
+                         synchronously from the neighbour's u^m            */
 } orc_problem;
 
 typedef struct orc_ctx orc_ctx;

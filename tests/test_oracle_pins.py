@@ -768,3 +768,56 @@ def test_sync_conserves_mass_momentum_energy(case):
         assert abs(tot1 - tot0) <= 1e-12 * scale, (v, tot0, tot1)
     if case == "rns":
         assert s[3].sum() < u0[3].sum()     # fuel is consumed, never produced
+
+
+# --------------------------------------------------------------------------
+# Reading A of the stage history (Sec. 2.3, stage values at buffer points
+# formed by the receiver): a buffer point of stage s at a delayed level m
+# reads the stage argument recomputed synchronously from the neighbour's u^m
+# instead of the one the neighbour computed
+# --------------------------------------------------------------------------
+def _mk(maker, **kw):
+    if maker == "advdiff":
+        return W.advdiff(n=256, pe_size=16, cfl=0.075, **kw)
+    if maker == "rns":
+        return W.rns(case="flame", n=512, pe_size=32, dt=0.003, **kw)
+    return W.detonation(n=2048, pe_size=256, **kw)
+
+
+@pytest.mark.parametrize("maker", ["advdiff", "rns", "euler"])
+def test_reading_a_at_zero_delay_is_reading_b_bitwise(maker):
+    """With no delay the recomputed stage arguments are the ones the
+    neighbour computed (both are the synchronous scheme): A == B bitwise in
+    SYNC mode and in AT mode with k_max = 0; with delays the two differ."""
+    for kw in (dict(mode="sync"), dict(mode="at", k_max=0)):
+        pb, u0 = _mk(maker, **kw)
+        b = oracle.Oracle(pb, u0)
+        a = oracle.Oracle(dict(pb, history="recompute"), u0)
+        assert a.run(20) == 0 and b.run(20) == 0
+        assert np.array_equal(a.state(), b.state())
+    pb, u0 = _mk(maker, mode="at", k_max=3)
+    b = oracle.Oracle(pb, u0)
+    a = oracle.Oracle(dict(pb, history="recompute"), u0)
+    assert a.run(20) == 0 and b.run(20) == 0
+    assert not np.array_equal(a.state(), b.state())
+    assert np.array_equal(a.delays(), b.delays())  # the same draws
+
+
+def test_reading_a_keeps_the_at_order():
+    """AT4 + RK4 on advection-diffusion with reading A converges to the closed
+    form at fourth order (dt ~ dx^2), with errors of the size of reading B's;
+    reading the stage-0 argument u^m at every stage instead (an O(dt)
+    inconsistency of the buffer values in time) would lose that order."""
+    def err(n, hist):
+        dx = 2 * math.pi / n
+        dt = 0.05 * dx * dx / 0.5
+        steps = int(round(0.25 / dt))
+        dt = 0.25 / steps
+        pb, u0 = W.advdiff(n=n, pe_size=16, order=4, c=1.0, a=0.5, mode="at", k_max=3, dt=dt)
+        o = oracle.Oracle(dict(pb, history=hist), u0)
+        assert o.run(steps) == 0
+        return np.abs(o.state() - W.advdiff_exact(pb, 0.25)).max()
+    ea = [err(n, "recompute") for n in (32, 64, 128)]
+    eb = [err(n, "stage") for n in (32, 64, 128)]
+    assert math.log2(ea[1] / ea[2]) > 3.5, ea
+    assert 0.2 < ea[-1] / eb[-1] < 5.0, (ea, eb)

@@ -108,7 +108,7 @@ enum {
     AT_OPT_WITHHOLD_PE = 2, /* fault injection: this PE (on the fused path: the CTA holding it)
                                never announces its progress, so its neighbours' waits run out
                                (-1, the default: none)                                           */
-    AT_OPT_ARRIVAL = 3      /* 1: real asynchrony on the persistent path.  Instead of drawing a
+    AT_OPT_ARRIVAL = 3,     /* 1: real asynchrony on the persistent path.  Instead of drawing a
                                delay, each PE boundary uses the freshest stage argument of the
                                neighbour that has arrived (never older than k_max, or than the
                                start-up clamp allows: it waits for that), as the CPU PEs of the
@@ -116,7 +116,21 @@ enum {
                                records the delays so that a run can be replayed (the oracle
                                does).  0 (default): Philox delays.  AT_EINVAL from at_step if
                                the persistent path cannot be taken.                             */
+    AT_OPT_HISTORY = 4      /* what a buffer point reads at a delayed level m and stage s
+                               (Sec. 2.3; value AT_HIST_*).  AT_HIST_STAGE (default): the
+                               neighbour's stage argument U^{m,(s)} as the neighbour computed it
+                               (the per-step message carries every stage).  AT_HIST_RECOMPUTE:
+                               the stage values formed again from the neighbour's u^m, as a
+                               synchronous RK step from u^m would form them: after each step a
+                               kernel recomputes them on a strip of 2 S H points around every PE
+                               boundary and writes them into the history ring.  Takes
+                               advection-diffusion and the reacting flow in flux form on the
+                               per-stage path (AT_PATH_AUTO picks it); AT_EINVAL from at_step
+                               otherwise.  Both readings give the same values bit for bit when
+                               every delay is 0.  Set it before at_set_delays, which seeds the
+                               ring of level 0 by the chosen reading.                           */
 };
+enum { AT_HIST_STAGE = 0, AT_HIST_RECOMPUTE = 1 };
 
 typedef struct {
     int32_t pde;      /* AT_ADVDIFF | AT_RNS | AT_EULER | AT_ADV_WENO | AT_BURGERS | AT_RNS_CHAIN */

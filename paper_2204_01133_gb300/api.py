@@ -34,7 +34,8 @@ SYMBOLS = ("at_create", "at_workspace_bytes", "at_set_problem", "at_set_delays",
            "at_batch_table_bytes", "at_batch_create", "at_batch_bind", "at_batch_release", "at_batch_set_config",
            "at_batch_step", "at_batch_run", "at_batch_query", "at_batch_destroy")
 PATH_AUTO, PATH_STAGE, PATH_PERSISTENT, PATH_FUSED = 0, 1, 2, 3
-OPT_PATH, OPT_WAIT_LIMIT, OPT_WITHHOLD_PE, OPT_ARRIVAL = 0, 1, 2, 3
+OPT_PATH, OPT_WAIT_LIMIT, OPT_WITHHOLD_PE, OPT_ARRIVAL, OPT_HISTORY = 0, 1, 2, 3, 4
+HIST_STAGE, HIST_RECOMPUTE = 0, 1  # reading B (the neighbour's stage arguments) / A (recomputed from u^m)
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -182,6 +183,11 @@ class Solver:
         self._h = h
         self._pbs = problem_struct(pb)
         self._dls = delays_struct(pb)
+        hist = pb.get("history", "stage")
+        if hist not in ("stage", "recompute"):
+            raise AtError(AT_EINVAL, "history is 'stage' or 'recompute'")
+        if hist == "recompute":  # before at_set_delays, which seeds level 0 of the ring
+            self.set_option(OPT_HISTORY, HIST_RECOMPUTE)
         nbytes = workspace_bytes(pb)
         if nbytes == 0:
             raise AtError(AT_EINVAL, lib().at_last_error().decode())

@@ -22,6 +22,8 @@ size_t atk_stage_smem_bytes(int pde, int Tw, int H);
 int atk_stage_block(int pde, int Tw);
 cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaStream_t st);
 cudaError_t atk_launch_ring_seed(const atk::StageArgs& a, cudaStream_t st);
+cudaError_t atk_launch_ring_recompute(const atk::StageArgs& a, int pde, int order, int rk, const double* um,
+                                      int64_t m, cudaStream_t st);
 cudaError_t atk_set_smem_limits();
 int64_t atk_persist_capacity(int pde, int order, int B, int device);
 int atk_cluster_size(int pde, int order, int B, int64_t P, int R, int S, int device);
@@ -323,6 +325,8 @@ struct at_ctx {
     int64_t wait_limit = 4000000;  // polls of a bounded wait
     int64_t withhold_pe = -1;
     int arrival = 0;               // at_set_option(AT_OPT_ARRIVAL)
+    int hist = AT_HIST_STAGE;      // at_set_option(AT_OPT_HISTORY)
+    int64_t hist_level = -1;       // reading A: the level whose recomputed stage values the ring holds
     uint8_t* trace = nullptr;      // at_set_delay_trace: caller-owned device buffer
     int64_t trace_n0 = 0, trace_steps = 0;
     // tracing (at_profile)
@@ -466,6 +470,7 @@ int at_set_delays(at_ctx* c, const at_delays* dl)
     e = atk_launch_ring_seed(s, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "ring seed launch");
     c->level = 0;
+    c->hist_level = -1;  // reading A recomputes level 0 at the first at_step
     c->persist_cap = (c->pb.pde == AT_ADVDIFF || c->pb.pde == AT_RNS)
                          ? atk_persist_capacity(c->pb.pde, c->pb.order, c->pb.pe_size, c->device)
                          : 0;
@@ -496,11 +501,19 @@ int at_step(at_ctx* c, int64_t nsteps)
     double* A = (double*)(c->ws + L.off_A);
     double* Bf = (double*)(c->ws + L.off_B);
     double* u = c->state;
-    const bool can_persist = c->persist_cap > 0 && L.P <= c->persist_cap;
+    const bool recompute = c->hist == AT_HIST_RECOMPUTE;
+    if (recompute) {
+        if (c->pb.pde != AT_ADVDIFF && c->pb.pde != AT_RNS)
+            return fail(AT_EINVAL, "AT_HIST_RECOMPUTE takes advection-diffusion and the reacting flow in flux form");
+        if (c->path == AT_PATH_PERSISTENT || c->path == AT_PATH_FUSED)
+            return fail(AT_EINVAL, "AT_HIST_RECOMPUTE runs on the per-stage path");
+        if (c->arrival) return fail(AT_EINVAL, "AT_HIST_RECOMPUTE uses drawn delays, not delays by arrival");
+    }
+    const bool can_persist = !recompute && c->persist_cap > 0 && L.P <= c->persist_cap;
     if (c->path == AT_PATH_PERSISTENT && !can_persist)
         return fail(AT_EINVAL, "the persistent path needs a central PDE and at most %lld PEs (have %lld)",
                     (long long)c->persist_cap, (long long)L.P);
-    const bool fused_ok = atk_fused_supported(c->pb.pde, c->pb.order, c->pb.pe_size, L.S);
+    const bool fused_ok = !recompute && atk_fused_supported(c->pb.pde, c->pb.order, c->pb.pe_size, L.S);
     const bool cluster_ok = c->cluster_c > 0 && !c->arrival && c->withhold_pe < 0;
     bool persist = c->path == AT_PATH_PERSISTENT || (c->path == AT_PATH_AUTO && can_persist);
     // advection-diffusion beyond one thread-block cluster: the step-fused
@@ -590,10 +603,29 @@ int at_step(at_ctx* c, int64_t nsteps)
         g_err[0] = 0;
         return AT_OK;
     }
+    // reading A: the stage values of the current level, recomputed from its
+    // u, must be in the ring before its first stage (once per at_set_delays,
+    // then kept up to date after every step below)
+    auto recompute_level = [&](int64_t m) -> cudaError_t {
+        atk::StageArgs a = c->base;
+        a.level = m;
+        cudaError_t er = record(c, true);
+        if (er == cudaSuccess)
+            er = atk_launch_ring_recompute(a, c->pb.pde, c->pb.order, c->pb.rk, u, m, c->stream);
+        if (er == cudaSuccess) er = record(c, false);
+        ++c->launched;
+        c->hist_level = m;
+        return er;
+    };
+    if (recompute && nsteps > 0 && c->hist_level != c->level) {
+        e = recompute_level(c->level);
+        if (e != cudaSuccess) return cuda_fail(e, "stage-history recompute launch");
+    }
     for (int64_t i = 0; i < nsteps; ++i) {
         atk::StageArgs a = c->base;
         a.level = c->level;
         a.u = u;
+        a.hist_recompute = recompute ? 1 : 0;
         for (int s = 0; s < L.S; ++s) {
             a.stage = s;
             // stencil source and output of each stage (ping-pong A/B, last stage in place)
@@ -609,6 +641,10 @@ int at_step(at_ctx* c, int64_t nsteps)
             ++c->launched;
         }
         ++c->level;
+        if (recompute) {
+            e = recompute_level(c->level);
+            if (e != cudaSuccess) return cuda_fail(e, "stage-history recompute launch");
+        }
     }
     g_err[0] = 0;
     return AT_OK;
@@ -701,6 +737,12 @@ int at_set_option(at_ctx* c, int key, int64_t value)
     case AT_OPT_ARRIVAL:
         if (value != 0 && value != 1) return fail(AT_EINVAL, "AT_OPT_ARRIVAL takes 0 or 1");
         c->arrival = (int)value;
+        return AT_OK;
+    case AT_OPT_HISTORY:
+        if (value != AT_HIST_STAGE && value != AT_HIST_RECOMPUTE)
+            return fail(AT_EINVAL, "AT_OPT_HISTORY takes AT_HIST_STAGE or AT_HIST_RECOMPUTE");
+        c->hist = (int)value;
+        c->hist_level = -1;
         return AT_OK;
     default: return fail(AT_EINVAL, "unknown option %d", key);
     }

@@ -53,6 +53,8 @@ struct StageArgs {
     int64_t withhold_pe; // fault injection: this PE never publishes (-1: none)
     int slack;           // ring levels beyond k_max + q + 1
     int arrival;         // 1: a delay is the age of the freshest neighbour data that has arrived
+    int hist_recompute;  // 1: the ring holds stage values recomputed from u^m (reading A); the
+                         //    stage kernels then push nothing into it
     // delay trace (optional): the delay of every (step, stage, PE, side) of
     // levels trace_n0 .. trace_n0 + trace_steps - 1, [steps][S][P][2]
     uint8_t* trace;

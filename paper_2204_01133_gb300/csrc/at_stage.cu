@@ -196,7 +196,7 @@ __device__ __forceinline__ void rk_update(const StageArgs& a, const Cx& cx, int 
         side = 1;
         h = jpe - (a.B - a.H);
     }
-    if (side >= 0) {
+    if (side >= 0 && !a.hist_recompute) {
         const bool last = (cx.stage == a.S - 1);
         a.ring[ring_index(a, last ? cx.level + 1 : cx.level, last ? 0 : cx.stage + 1, pe, side, h, v)] = y;
     }
@@ -605,11 +605,133 @@ __global__ void ring_seed(const StageArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Reading A of the stage history (Sec. 2.3: the stage values a PE's buffer
+// points need are formed from the neighbour's u^m rather than received): for
+// every PE boundary, the stage arguments U^{m,(s)} of the two edge windows
+// next to it, recomputed as a synchronous RK step from u^m would form them,
+// written into the ring at level m for every stage s.  Stage s at the
+// window needs K_{s-1} there, which needs U^{(s-1)} H points further out, so
+// the strip is 2 S H points centred on the boundary (S H on each side) and
+// the points where U^{(r)} is known shrink by H per stage.  One warp per
+// boundary, lane i = strip point i (2 S H <= 32).  The right-hand side and
+// the update are those of the per-stage kernels, operation for operation
+// (the derived quantities, the central taps in the same order, the Arrhenius
+// source, rk_update's formulas), so with no delays the recomputed values are
+// bit for bit the ones the PEs compute themselves.
+// ---------------------------------------------------------------------------
+template <int PDE, int H, int RK>
+__global__ void __launch_bounds__(128) ring_recompute(const StageArgs a, const double* __restrict__ um, int64_t m)
+{
+    using P = Phys<PDE>;
+    constexpr int NV = P::NV, ND = P::ND;
+    constexpr int S = RK == RK4 ? 4 : (RK == RK3TVD ? 3 : 2);
+    constexpr int SH = S * H, W = 2 * SH;
+    __shared__ double sG[4][ND][W];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int64_t b = (int64_t)blockIdx.x * 4 + wid;  // boundary between PE b-1 and PE b
+    if (b >= a.P) return;                              // whole warps only
+    double* G = &sG[wid][0][0];
+    const bool in = lane < W;
+    int64_t j = (b * a.B - SH + lane) % a.N;  // the lane's point (periodic; the strip may wrap)
+    if (j < 0) j += a.N;
+    double un[NV], x[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) un[v] = x[v] = in ? um[v * a.N + j] : 0.0;
+    // the window: points SH-H .. SH+H-1 of the strip; left of the boundary the
+    // right edge window of PE b-1, right of it the left edge window of PE b
+    const bool win = lane >= SH - H && lane < SH + H;
+    const int64_t pe = lane < SH ? (b == 0 ? a.P - 1 : b - 1) : b;
+    const int side = lane < SH ? 1 : 0;
+    const int h = lane < SH ? lane - (SH - H) : lane - SH;
+    const int r0 = (int)((uint32_t)m % (uint32_t)a.R);
+    auto put = [&](int s) {
+        if (win) {
+            const int64_t base = (((((int64_t)r0 * a.S + s) * a.P + pe) * 2 + side) * a.H + h) * a.nvar;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) a.ring[base + v] = x[v];
+        }
+    };
+    put(0);
+#pragma unroll 1
+    for (int r = 0; r < S - 1; ++r) {
+        // U^{(r)} is known on [r H, W - r H): its derived quantities
+        if (lane >= r * H && lane < W - r * H) {
+            double g[ND];
+            P::derive(a, x, g);
+#pragma unroll
+            for (int d = 0; d < ND; ++d) G[d * W + lane] = g[d];
+        }
+        __syncwarp();
+        double y[NV];
+        const bool upd = lane >= (r + 1) * H && lane < W - (r + 1) * H;
+        if (upd) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double K = 0.0;
+                if constexpr (PDE == ADVDIFF) {
+#pragma unroll
+                    for (int o = -H; o <= H; ++o) K = fma(a.cm[o + H], G[lane + o], K);
+                } else {
+                    const double* F = G + v * W;
+#pragma unroll
+                    for (int o = -H; o <= H; ++o)
+                        if (o != 0) K = fma(a.c1[o + H], F[lane + o], K);
+                    if (v > 0) {
+                        const double* D = G + (3 + v) * W;
+#pragma unroll
+                        for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[lane + o], K);
+                    }
+                    if (v == 3) K = fma(-a.prm[4] * x[v], at_exp(-a.prm[5] * at_rcp(G[7 * W + lane])), K);
+                }
+                // the stage-(r+1) argument as rk_update forms it
+                if (RK == RK4) y[v] = fma(r == 2 ? a.dt : a.hdt, K, un[v]);
+                else if (RK == RK3TVD) y[v] = r == 0 ? fma(a.dt, K, x[v]) : fma(0.75, un[v], 0.25 * fma(a.dt, K, x[v]));
+                else y[v] = fma(a.dt, K, un[v]);
+            }
+        }
+        __syncwarp();
+        if (upd) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) x[v] = y[v];
+        }
+        put(r + 1);
+    }
+}
+
 } // namespace atk
 
 // ---------------------------------------------------------------------------
 // host-side launchers (C++ linkage, used by at_abi.cu)
 // ---------------------------------------------------------------------------
+// reading A: the recomputed stage arguments of every PE boundary at level m
+// into the ring (advection-diffusion and the reacting flow in flux form)
+cudaError_t atk_launch_ring_recompute(const atk::StageArgs& a, int pde, int order, int rk, const double* um,
+                                      int64_t m, cudaStream_t st)
+{
+    const dim3 grid((unsigned)((a.P + 3) / 4)), block(128);
+#define AT_RR(PDE, HH)                                                                                   \
+    do {                                                                                                 \
+        if (rk == atk::RK4) atk::ring_recompute<PDE, HH, atk::RK4><<<grid, block, 0, st>>>(a, um, m);      \
+        else if (rk == atk::RK3TVD) atk::ring_recompute<PDE, HH, atk::RK3TVD><<<grid, block, 0, st>>>(a, um, m); \
+        else atk::ring_recompute<PDE, HH, atk::RK2><<<grid, block, 0, st>>>(a, um, m);                   \
+    } while (0)
+    if (pde == atk::ADVDIFF) {
+        if (order == 2) AT_RR(atk::ADVDIFF, 1);
+        else if (order == 4) AT_RR(atk::ADVDIFF, 2);
+        else AT_RR(atk::ADVDIFF, 3);
+    } else if (pde == atk::RNS) {
+        if (order == 2) AT_RR(atk::RNS, 1);
+        else if (order == 4) AT_RR(atk::RNS, 2);
+        else AT_RR(atk::RNS, 3);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+#undef AT_RR
+    return cudaGetLastError();
+}
+
 size_t atk_stage_smem_bytes(int pde, int Tw, int H)
 {
     const size_t W2 = Tw + 2 * H, E = Tw + 1;

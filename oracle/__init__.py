@@ -48,6 +48,7 @@ class _Problem(ctypes.Structure):
         ("pe_total", ctypes.c_int64),
         ("open_ends", ctypes.c_int),
         ("history", ctypes.c_int),
+        ("weno_interp", ctypes.c_int),
     ]
 
 
@@ -100,6 +101,8 @@ def lib():
         L.orc_lagrange_weights.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]
         L.orc_weno5_js.argtypes = [P(ctypes.c_double), ctypes.c_double]
         L.orc_weno5_js.restype = ctypes.c_double
+        L.orc_weno5_interp.argtypes = [P(ctypes.c_double), ctypes.c_double]
+        L.orc_weno5_interp.restype = ctypes.c_double
         L.orc_edge_flux.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, P(ctypes.c_int32),
                                     ctypes.c_int64, ctypes.c_int64, P(ctypes.c_double)]
         L.orc_set_level.argtypes = [ctypes.c_void_p, ctypes.c_int64]
@@ -151,6 +154,7 @@ def _problem(pb: dict) -> _Problem:
     s.pe_total = int(pb.get("pe_total", 0))
     s.open_ends = int(pb.get("open_ends", 0))
     s.history = {"stage": 0, "recompute": 1}[pb.get("history", "stage")]
+    s.weno_interp = {"reconstruct": 0, "interpolate": 1}[pb.get("weno", "reconstruct")]
     return s
 
 
@@ -311,3 +315,8 @@ def lagrange_weights(q: int, k: int):
 def weno5(v, eps: float = 1e-6) -> float:
     a = (ctypes.c_double * 5)(*[float(x) for x in v])
     return float(lib().orc_weno5_js(a, float(eps)))
+
+
+def weno5_interp(v, eps: float = 1e-6) -> float:
+    a = (ctypes.c_double * 5)(*[float(x) for x in v])
+    return float(lib().orc_weno5_interp(a, float(eps)))

@@ -229,6 +229,32 @@ double orc_weno5_js(const double v[5], double eps)
 }
 
 /* ------------------------------------------------------------------ */
+/* WENO5 interpolation of the point value at x_{j+1/2} from            */
+/* v = u_{j-2..j+2}: the third-order interpolants of Eq. interpS on    */
+/* the three candidate stencils, combined by Eq. fullSten with the     */
+/* weights of Eq. omg, ideal weights {1/16, 5/8, 5/16} (their          */
+/* combination is the printed five-point fifth-order interpolant), and */
+/* the smoothness indicators of Eq. betaS.                             */
+/* ------------------------------------------------------------------ */
+double orc_weno5_interp(const double v[5], double eps)
+{
+    double u0 = 3.0 / 8.0 * v[0] - 5.0 / 4.0 * v[1] + 15.0 / 8.0 * v[2];
+    double u1 = -1.0 / 8.0 * v[1] + 3.0 / 4.0 * v[2] + 3.0 / 8.0 * v[3];
+    double u2 = 3.0 / 8.0 * v[2] + 3.0 / 4.0 * v[3] - 1.0 / 8.0 * v[4];
+    double b0 = (4.0 * v[0] * v[0] + (11.0 * v[2] - 19.0 * v[1]) * v[0] + 25.0 * v[1] * v[1]
+                 + 10.0 * v[2] * v[2] - 31.0 * v[1] * v[2]) / 3.0;
+    double b1 = (4.0 * v[1] * v[1] + (5.0 * v[3] - 13.0 * v[2]) * v[1] + 13.0 * v[2] * v[2]
+                 + 4.0 * v[3] * v[3] - 13.0 * v[2] * v[3]) / 3.0;
+    double b2 = (10.0 * v[2] * v[2] + (11.0 * v[4] - 31.0 * v[3]) * v[2] + 25.0 * v[3] * v[3]
+                 + 4.0 * v[4] * v[4] - 19.0 * v[3] * v[4]) / 3.0;
+    double a0 = (1.0 / 16.0) / ((eps + b0) * (eps + b0));
+    double a1 = (5.0 / 8.0) / ((eps + b1) * (eps + b1));
+    double a2 = (5.0 / 16.0) / ((eps + b2) * (eps + b2));
+    double s = a0 + a1 + a2;
+    return (a0 / s) * u0 + (a1 / s) * u1 + (a2 / s) * u2;
+}
+
+/* ------------------------------------------------------------------ */
 /* Physics: derived quantities of one state vector                     */
 /* ------------------------------------------------------------------ */
 static int nvar_of(int pde) { return (pde == ORC_RNS || pde == ORC_EULER || pde == ORC_RNS_CHAIN) ? 4 : 1; }
@@ -422,7 +448,10 @@ static void edge_flux(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t
         }
         double vp[5] = {fp[0], fp[1], fp[2], fp[3], fp[4]};
         double vm[5] = {fm[5], fm[4], fm[3], fm[2], fm[1]};
-        F[v] = orc_weno5_js(vp, eps) + orc_weno5_js(vm, eps);
+        if (c->pb.weno_interp)
+            F[v] = orc_weno5_interp(vp, eps) + orc_weno5_interp(vm, eps);
+        else
+            F[v] = orc_weno5_js(vp, eps) + orc_weno5_js(vm, eps);
     }
 }
 
@@ -495,7 +524,19 @@ static void rhs_point(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t
         double Fr[4], Fl[4];
         edge_flux(c, level, s, p, j, Fr);
         edge_flux(c, level, s, p, j - 1, Fl);
-        for (int v = 0; v < c->nvar; ++v) K[v] = -(Fr[v] - Fl[v]) / dx;
+        if (c->pb.weno_interp) {
+            /* edge point values: the fourth-order staggered difference
+             * f'_j = (9/8 (F_{j+1/2} - F_{j-1/2}) - 1/24 (F_{j+3/2} - F_{j-3/2})) / dx
+             * (the paper gives no derivative formula for interpolated edge
+             * values; this is the reading, see the design notes) */
+            double Fr2[4], Fl2[4];
+            edge_flux(c, level, s, p, j + 1, Fr2);
+            edge_flux(c, level, s, p, j - 2, Fl2);
+            for (int v = 0; v < c->nvar; ++v)
+                K[v] = -(9.0 / 8.0 * (Fr[v] - Fl[v]) - 1.0 / 24.0 * (Fr2[v] - Fl2[v])) / dx;
+        } else {
+            for (int v = 0; v < c->nvar; ++v) K[v] = -(Fr[v] - Fl[v]) / dx;
+        }
         if (pde == ORC_EULER) {
             double A = pr[1], Ea = pr[2];
             double Q[4];
@@ -679,8 +720,12 @@ orc_ctx* orc_create(const orc_problem* pb, const double* init)
     c->pb = *pb;
     c->nvar = nvar_of(pb->pde);
     int weno = (pb->pde == ORC_EULER || pb->pde == ORC_ADV_WENO || pb->pde == ORC_BURGERS);
+    if (pb->weno_interp && !weno) {
+        free(c);
+        return NULL;
+    }
     if (weno) {
-        c->H = 3;
+        c->H = pb->weno_interp ? 4 : 3; /* edges j +- 3/2 reach two more points */
         c->q = 1;
     } else {
         if (pb->order != 2 && pb->order != 4 && pb->order != 6) {

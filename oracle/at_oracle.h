@@ -52,6 +52,11 @@ typedef struct {
                          stage argument U^{m,(s)} as the neighbour computed
                          it; 1 (reading A) the stage argument recomputed
                          synchronously from the neighbour's u^m            */
+    int weno_interp;  /* WENO PDEs: 0 the flux-reconstruction form (Eqs.
+                         atRecon, idRec); 1 the interpolation form (Eqs.
+                         interpS, fullSten, omg: edge values of the split
+                         fluxes, ideal weights {1/16, 5/8, 5/16}) with the
+                         fourth-order staggered difference of edge values */
 } orc_problem;
 
 typedef struct orc_ctx orc_ctx;
@@ -109,6 +114,9 @@ void orc_thresholds(int k_max, int dist, const double* prob, uint64_t* thr);
 int orc_draw(const orc_ctx* c, int64_t level, int stage, int64_t pe, int side);
 void orc_lagrange_weights(int q, int k, double* w);
 double orc_weno5_js(const double v[5], double eps);
+/* WENO5 interpolation of the value at x_{j+1/2} from v = u_{j-2..j+2}
+ * (Eqs. interpS, fullSten, omg; indicators of Eq. betaS) */
+double orc_weno5_interp(const double v[5], double eps);
 void orc_set_level(orc_ctx* c, int64_t level);
 void orc_set_state(orc_ctx* c, const double* u /* [nvar][n] */);
 /* fixed raw delays [P][2] for every following step (NULL: draw again) */

@@ -15,6 +15,10 @@ Physics constants of the workloads (``prm``):
 * ``rns``       [gamma, mu, Pr, Le, A, Ea, q_c]     reacting Navier-Stokes
 * ``euler``     [gamma, A, Ea, Q, eps]              reactive Euler (WENO5)
 
+The WENO problems take ``weno`` = "reconstruct" (flux reconstruction, Eq.
+atRecon) or "interpolate" (edge values by Eqs. interpS/fullSten/omg with the
+fourth-order staggered difference).
+
 All quantities are nondimensional with the unburnt state rho0 = T0 = 1 and a
 gas constant of 1 (p = rho T).
 """
@@ -75,13 +79,13 @@ def advdiff_exact(pb: dict, t: float) -> np.ndarray:
 # x in [-1, 1], u0 = sin^4(pi x + 0.25), c = 5, RK3, dt ~ dx^2).
 # --------------------------------------------------------------------------
 def adv_weno(n=256, pe_size=16, c=5.0, eps=1e-6, mode="at", k_max=1, dist="uniform", prob=(),
-             seed=0, per_stage=1, dt=None, dt_coef=None, rk="rk3tvd"):
+             seed=0, per_stage=1, dt=None, dt_coef=None, rk="rk3tvd", weno="reconstruct"):
     dx = 2.0 / n
     if dt is None:
         dt = dt_coef * dx * dx if dt_coef is not None else 0.5 * dx / abs(c)
     pb = base_problem(pde="adv_weno", rk=rk, n=n, pe_size=pe_size, dx=dx, dt=dt, prm=[c, eps],
                       mode=mode, k_max=k_max, dist=dist, prob=list(prob), seed=seed,
-                      per_stage=per_stage)
+                      per_stage=per_stage, weno=weno)
     x = -1.0 + np.arange(n, dtype=np.float64) * dx
     init = (np.sin(np.pi * x + 0.25) ** 4)[None, :].copy()
     return pb, init
@@ -99,12 +103,12 @@ def adv_weno_exact(pb: dict, t: float) -> np.ndarray:
 # x in [-1, 1], u0 = 0.5 + sin(pi x), RK3, dt ~ dx^2).
 # --------------------------------------------------------------------------
 def burgers(n=256, pe_size=16, eps=1e-6, mode="at", k_max=1, dist="uniform", prob=(), seed=0, per_stage=1,
-            dt=None, dt_coef=None, rk="rk3tvd"):
+            dt=None, dt_coef=None, rk="rk3tvd", weno="reconstruct"):
     dx = 2.0 / n
     if dt is None:
         dt = dt_coef * dx * dx if dt_coef is not None else 0.4 * dx / 1.5
     pb = base_problem(pde="burgers", rk=rk, n=n, pe_size=pe_size, dx=dx, dt=dt, prm=[0.0, eps], mode=mode,
-                      k_max=k_max, dist=dist, prob=list(prob), seed=seed, per_stage=per_stage)
+                      k_max=k_max, dist=dist, prob=list(prob), seed=seed, per_stage=per_stage, weno=weno)
     x = -1.0 + np.arange(n, dtype=np.float64) * dx
     init = (0.5 + np.sin(np.pi * x))[None, :].copy()
     return pb, init
@@ -258,7 +262,7 @@ def euler_conserved(rho, u, p, Y, prm) -> np.ndarray:
 
 
 def detonation(n=1 << 24, pe_size=1024, mode="at", k_max=4, dist="geometric", prob=(0.5,), seed=0,
-               per_stage=1, cfl=0.5, slab=20.0, dt=None, edge_points=5.0):
+               per_stage=1, cfl=0.5, slab=20.0, dt=None, edge_points=5.0, weno="reconstruct"):
     """Slab of von Neumann state over ``slab`` half-reaction lengths (from
     x = 1 to x = 1 + slab) in unburnt gas (rho = p = 1, u = 0, Y = 1);
     periodic.  The slab edges are tanh ramps ``edge_points`` cells wide: the
@@ -282,12 +286,12 @@ def detonation(n=1 << 24, pe_size=1024, mode="at", k_max=4, dist="geometric", pr
         dt = cfl * dx / smax
     pb = base_problem(pde="euler", rk="rk3tvd", n=n, pe_size=pe_size, dx=dx, dt=dt, prm=prm,
                       mode=mode, k_max=k_max, dist=dist, prob=list(prob), seed=seed,
-                      per_stage=per_stage)
+                      per_stage=per_stage, weno=weno)
     return pb, init
 
 
 def entropy_wave(n=256, pe_size=32, mode="sync", k_max=1, dist="uniform", prob=(), seed=0,
-                 u0=1.0, amp=0.2, dt=None, rk="rk3tvd", dt_coef=None):
+                 u0=1.0, amp=0.2, dt=None, rk="rk3tvd", dt_coef=None, weno="reconstruct"):
     """Reactive-Euler density wave at constant u and p with no fuel: the exact
     solution is rho0(x - u0 t); x in [0, 1)."""
     prm = [DET_GAMMA, 0.0, DET_EA, DET_Q, DET_EPS]
@@ -298,7 +302,7 @@ def entropy_wave(n=256, pe_size=32, mode="sync", k_max=1, dist="uniform", prob=(
     if dt is None:
         dt = dt_coef * dx * dx if dt_coef is not None else 0.4 * dx / (u0 + math.sqrt(DET_GAMMA / (1 - amp)))
     pb = base_problem(pde="euler", rk=rk, n=n, pe_size=pe_size, dx=dx, dt=dt, prm=prm, mode=mode,
-                      k_max=k_max, dist=dist, prob=list(prob), seed=seed)
+                      k_max=k_max, dist=dist, prob=list(prob), seed=seed, weno=weno)
     return pb, init
 
 

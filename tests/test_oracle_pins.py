@@ -821,3 +821,78 @@ def test_reading_a_keeps_the_at_order():
     eb = [err(n, "stage") for n in (32, 64, 128)]
     assert math.log2(ea[1] / ea[2]) > 3.5, ea
     assert 0.2 < ea[-1] / eb[-1] < 5.0, (ea, eb)
+
+
+# --------------------------------------------------------------------------
+# The WENO interpolation form (Sec. 3, Eqs. interpS, fullSten, omg)
+# --------------------------------------------------------------------------
+def test_weno_interp_ideal_weights_give_the_printed_interpolant():
+    """With eps far above every indicator the weights are the ideal ones
+    {1/16, 5/8, 5/16}, and the combination is the printed fifth-order
+    interpolant (3/128, -5/32, 45/64, 15/32, -5/128)."""
+    rng = np.random.default_rng(8)
+    for _ in range(50):
+        v = rng.standard_normal(5)
+        got = oracle.weno5_interp(v, eps=1e30)
+        want = 3 / 128 * v[0] - 5 / 32 * v[1] + 45 / 64 * v[2] + 15 / 32 * v[3] - 5 / 128 * v[4]
+        assert abs(got - want) < 1e-14 * (1 + abs(want)), (v, got, want)
+
+
+def test_weno_interp_exact_on_quadratics_and_fifth_order_smooth():
+    """Every candidate interpolates a quadratic exactly, so any weights do;
+    on a smooth function the edge value converges at fifth order."""
+    rng = np.random.default_rng(9)
+    for _ in range(20):
+        c0, c1, c2 = rng.standard_normal(3)
+        q = lambda x: c0 + c1 * x + c2 * x * x
+        v = [q(float(x)) for x in (-2, -1, 0, 1, 2)]
+        assert abs(oracle.weno5_interp(v) - q(0.5)) < 1e-13
+    errs = []
+    for h in (0.1, 0.05, 0.025):
+        x0 = 0.3
+        v = [math.sin(x0 + i * h) for i in (-2, -1, 0, 1, 2)]
+        errs.append(abs(oracle.weno5_interp(v, eps=1e-40) - math.sin(x0 + 0.5 * h)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 4.7, (errs, rates)
+
+
+def test_printed_at_interpolants_are_interps_on_extrapolated_values():
+    """Symbolic: the printed AT interpolants of the five-point stencils (the
+    equation after Eq. stenF) are the synchronous ones of Eq. interpS on the
+    linearly extrapolated buffer values (k+1) u^{n-k} - k u^{n-k-1}."""
+    sp = pytest.importorskip("sympy")
+    k, a, a1, b, b1, c, d = sp.symbols("k a a1 b b1 c d")
+    R = sp.Rational
+    A = (k + 1) * a - k * a1   # u_{j-2} extrapolated
+    Bx = (k + 1) * b - k * b1  # u_{j-1} extrapolated
+    # printed: u~(0) and u~(1) at x_{j+1/2} with buffer points j-2, j-1
+    p0 = -R(3, 8) * k * a1 + R(5, 4) * k * b1 + R(1, 8) * (3 * k + 3) * a + R(1, 4) * (-5 * k - 5) * b + R(15, 8) * c
+    p1 = R(1, 8) * k * b1 + R(1, 8) * (-k - 1) * b + R(3, 4) * c + R(3, 8) * d
+    s0 = R(3, 8) * A - R(5, 4) * Bx + R(15, 8) * c
+    s1 = -R(1, 8) * Bx + R(3, 4) * c + R(3, 8) * d
+    assert sp.expand(p0 - s0) == 0
+    assert sp.expand(p1 - s1) == 0
+    # Eq. atS1 (the four-point second stencil) is the same interpolant
+    atS1 = R(1, 8) * k * b1 + R(1, 8) * (-k - 1) * b + R(3, 4) * c + R(3, 8) * d
+    assert sp.expand(atS1 - s1) == 0
+
+
+def test_weno_interp_scheme_orders_sync_and_at():
+    """Scalar advection (c = 5, sin^4, RK3, dt ~ dx^2) with edge values by
+    interpolation and the fourth-order staggered difference: fourth order
+    synchronous and with AT-WENO delays (p = [0.5, 0.5])."""
+    def mk(n, mode, **kw):
+        pb, u0 = W.adv_weno(n=n, pe_size=16, mode=mode, k_max=1, dt_coef=2.0, weno="interpolate", **kw)
+        return pb, u0, W.adv_weno_exact
+    for mode in ("sync", "at"):
+        errs, rates = _order_runs(mk, (64, 128, 256), mode, 0.05)
+        assert rates[-1] > 3.6, (mode, errs, rates)
+
+
+def test_weno_interp_conserves_under_sync():
+    pb, u0 = W.detonation(n=2048, pe_size=256, mode="sync", weno="interpolate")
+    o = oracle.Oracle(pb, u0)
+    assert o.run(30) == 0
+    tot0, tot1 = u0.sum(axis=1), o.state().sum(axis=1)
+    # mass, momentum and energy are conserved (the fuel reacts away)
+    assert np.all(np.abs(tot1[:3] - tot0[:3]) <= 1e-11 * np.abs(tot0[:3]).max())

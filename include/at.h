@@ -136,11 +136,20 @@ typedef struct {
     int32_t pde;      /* AT_ADVDIFF | AT_RNS | AT_EULER | AT_ADV_WENO | AT_BURGERS | AT_RNS_CHAIN */
     int32_t order;    /* 2 | 4 | 6 for central PDEs; ignored for WENO5                */
     int32_t rk;       /* AT_RK2 | AT_RK3TVD | AT_RK4                                  */
-    int32_t pe_size;  /* points per PE, >= 2 x halo width (order/2, or 3 for WENO5)   */
+    int32_t pe_size;  /* points per PE, >= 2 x halo width (order/2; 3, or 4 for the
+                         WENO interpolation form)                                    */
     int64_t n;        /* grid points, periodic, n % pe_size == 0, n < 2^31            */
     double dx, dt;    /* grid spacing and the fixed time step                         */
     double prm[16];   /* physics constants, see the PDE list above                    */
+    int32_t weno;     /* WENO PDEs: AT_WENO_RECONSTRUCT (0) flux reconstruction, Sec. 3
+                         Eq. atRecon (the default); AT_WENO_INTERPOLATE (1) edge values
+                         of the split fluxes by interpolation, Eqs. interpS, fullSten,
+                         omg (ideal weights 1/16, 5/8, 5/16), differenced by the
+                         fourth-order staggered formula (9/8, -1/24), halo width 4,
+                         per-stage path only (not in batches).  0 for central PDEs.   */
+    int32_t reserved; /* 0                                                            */
 } at_problem;
+enum { AT_WENO_RECONSTRUCT = 0, AT_WENO_INTERPOLATE = 1 };
 
 typedef struct {
     int32_t mode;      /* AT_SYNC | AT_AS | AT_AT                                     */

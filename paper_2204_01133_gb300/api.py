@@ -35,6 +35,8 @@ SYMBOLS = ("at_create", "at_workspace_bytes", "at_set_problem", "at_set_delays",
            "at_batch_step", "at_batch_run", "at_batch_query", "at_batch_destroy")
 PATH_AUTO, PATH_STAGE, PATH_PERSISTENT, PATH_FUSED = 0, 1, 2, 3
 OPT_PATH, OPT_WAIT_LIMIT, OPT_WITHHOLD_PE, OPT_ARRIVAL, OPT_HISTORY = 0, 1, 2, 3, 4
+WENO_RECONSTRUCT, WENO_INTERPOLATE = 0, 1  # the WENO form of a problem ("weno" key of the dict)
+WENO = {"reconstruct": WENO_RECONSTRUCT, "interpolate": WENO_INTERPOLATE}
 HIST_STAGE, HIST_RECOMPUTE = 0, 1  # reading B (the neighbour's stage arguments) / A (recomputed from u^m)
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -49,6 +51,7 @@ class Problem(ctypes.Structure):
     _fields_ = [
         ("pde", ctypes.c_int32), ("order", ctypes.c_int32), ("rk", ctypes.c_int32), ("pe_size", ctypes.c_int32),
         ("n", ctypes.c_int64), ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("prm", ctypes.c_double * 16),
+        ("weno", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -121,6 +124,7 @@ def problem_struct(pb: dict) -> Problem:
     s.dt = float(pb["dt"])
     for i, v in enumerate(pb.get("prm", [])):
         s.prm[i] = float(v)
+    s.weno = WENO[pb.get("weno", "reconstruct")]
     return s
 
 

@@ -88,6 +88,13 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int nvar_of(int pde) { return (pde == AT_RNS || pde == AT_EULER || pde == AT_RNS_CHAIN) ? 4 : 1; }
 bool is_weno(int pde) { return pde == AT_EULER || pde == AT_ADV_WENO || pde == AT_BURGERS; }
+// stencil reach beyond a point: order/2 for central stencils; WENO5 reaches 3
+// points, and the interpolation form's edges j +- 3/2 one more
+int halo_of(const at_problem* pb)
+{
+    if (!is_weno(pb->pde)) return pb->order / 2;
+    return pb->weno == AT_WENO_INTERPOLATE ? 4 : 3;
+}
 int stages_of(int rk) { return rk == AT_RK2 ? 2 : (rk == AT_RK3TVD ? 3 : 4); }
 
 // window length: the largest divisor of the PE size in [2H, 256]; a PE size
@@ -111,7 +118,11 @@ int check_problem(const at_problem* pb)
         return fail(AT_EINVAL, "central order must be 2, 4 or 6 (got %d)", pb->order);
     if (pb->n <= 0 || pb->n >= ((int64_t)1 << 31)) return fail(AT_EINVAL, "n out of range");
     if (pb->pe_size <= 0 || pb->n % pb->pe_size) return fail(AT_EINVAL, "n must be a multiple of pe_size");
-    const int H = is_weno(pb->pde) ? 3 : pb->order / 2;
+    if (pb->weno != AT_WENO_RECONSTRUCT && pb->weno != AT_WENO_INTERPOLATE)
+        return fail(AT_EINVAL, "unknown weno form %d", pb->weno);
+    if (pb->weno == AT_WENO_INTERPOLATE && !is_weno(pb->pde))
+        return fail(AT_EINVAL, "the WENO interpolation form needs a WENO PDE");
+    const int H = halo_of(pb);
     if (pb->pe_size < 2 * H) return fail(AT_EINVAL, "pe_size must be at least %d", 2 * H);
     if (window_of(pb->pe_size, H) == 0)
         return fail(AT_EINVAL, "pe_size above 1024 needs a divisor between %d and 256", 2 * H);
@@ -144,7 +155,7 @@ Layout layout(const at_problem* pb, const at_delays* dl)
 {
     Layout L{};
     L.nvar = nvar_of(pb->pde);
-    L.H = is_weno(pb->pde) ? 3 : pb->order / 2;
+    L.H = halo_of(pb);
     L.q = is_weno(pb->pde) ? 1 : pb->order / 2;
     L.S = stages_of(pb->rk);
     L.R = dl->k_max + L.q + 1 + kRingSlack;
@@ -294,6 +305,7 @@ atk::StageArgs build_args(const at_problem* pb, const at_delays* dl, const Layou
         }
     } else {
         a.k0 = 1.0 / dx;
+        a.weno_interp = pb->weno == AT_WENO_INTERPOLATE ? 1 : 0;
     }
     a.bufA = (double*)(ws + L.off_A);
     a.bufB = (double*)(ws + L.off_B);
@@ -699,7 +711,7 @@ int at_read(at_ctx* c, int what, void* dst, size_t bytes, int dst_on_device)
         s.path = c->last_path;
         s.stages = stages_of(c->pb.rk);
         s.nvar = nvar_of(c->pb.pde);
-        s.halo = is_weno(c->pb.pde) ? 3 : c->pb.order / 2;
+        s.halo = halo_of(&c->pb);
         s.q = is_weno(c->pb.pde) ? 1 : c->pb.order / 2;
         s.ring_levels = c->have_delays ? c->L.R : 0;
         s.kernels_launched = c->launched;
@@ -1019,6 +1031,8 @@ int at_batch_bind(at_batch* b, int64_t slot, const at_instance* in)
     int st = check_problem(&in->pb);
     if (st == AT_OK) st = check_delays(&in->dl);
     if (st != AT_OK) return st;
+    if (in->pb.weno == AT_WENO_INTERPOLATE)
+        return fail(AT_EINVAL, "the WENO interpolation form runs on a context's per-stage path, not in batches");
     if (in->nsteps < 0) return fail(AT_EINVAL, "nsteps must be >= 0");
     if (in->nsteps > kMaxLevel) return fail(AT_EINVAL, "a solve is limited to %lld steps", (long long)kMaxLevel);
     if (!in->state_dev || !in->workspace_dev || ((uintptr_t)in->state_dev & 15) || ((uintptr_t)in->workspace_dev & 255))

@@ -55,6 +55,7 @@ struct StageArgs {
     int arrival;         // 1: a delay is the age of the freshest neighbour data that has arrived
     int hist_recompute;  // 1: the ring holds stage values recomputed from u^m (reading A); the
                          //    stage kernels then push nothing into it
+    int weno_interp;     // WENO PDEs: 1 the interpolation form (edge values, halo 4)
     // delay trace (optional): the delay of every (step, stage, PE, side) of
     // levels trace_n0 .. trace_n0 + trace_steps - 1, [steps][S][P][2]
     uint8_t* trace;

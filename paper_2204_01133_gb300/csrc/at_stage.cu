@@ -502,6 +502,111 @@ __global__ void __launch_bounds__(256, 5) stage_weno(const StageArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// The interpolation form (Sec. 3, Eqs. interpS, fullSten, omg): the value at
+// the right edge of f[2] from f[0..4] by the third-order interpolants
+// u0 = 3/8 f0 - 5/4 f1 + 15/8 f2, u1 = -1/8 f1 + 3/4 f2 + 3/8 f3,
+// u2 = 3/8 f2 + 3/4 f3 - 1/8 f4, ideal weights {1/16, 5/8, 5/16}, the
+// indicators of Eq. betaS and the weights of Eq. omg, arranged as weno5():
+// u0 - u1 = 3/8 (s_0 - s_1), u2 - u1 = 1/8 (s_1 - s_2), and with the common
+// factor E_0 E_1 E_2 and a scaling by 128,
+//   num = E_1 (3 E_2 (s_0 - s_1) + 5 E_0 (s_1 - s_2)),
+//   den = E_1 (8 E_2 + 40 E_0) + 80 E_0 E_2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double weno5_interp(double f0, double f1, double f2, double f3, double f4, double eps4)
+{
+    const double s0 = fma(-2.0, f1, f0) + f2;
+    const double s1 = fma(-2.0, f2, f1) + f3;
+    const double s2 = fma(-2.0, f3, f2) + f4;
+    const double r0 = fma(2.0, f2 - f1, s0);
+    const double r1 = f1 - f3;
+    const double r2 = fma(2.0, f2 - f3, s2);
+    const double d0 = fma((13.0 / 3.0) * s0, s0, fma(r0, r0, eps4));
+    const double d1 = fma((13.0 / 3.0) * s1, s1, fma(r1, r1, eps4));
+    const double d2 = fma((13.0 / 3.0) * s2, s2, fma(r2, r2, eps4));
+    const double e0 = d0 * d0, e1 = d1 * d1, e2 = d2 * d2;
+    const double num = e1 * fma(3.0 * e2, s0 - s1, (5.0 * e0) * (s1 - s2));
+    const double den = fma(e1, fma(8.0, e2, 40.0 * e0), 80.0 * (e0 * e2));
+    const double u1 = fma(-0.125, f1, fma(0.75, f2, 0.375 * f3));
+    return fma(num, at_rcp3(den), u1);
+}
+
+// A window of Tw points with a halo of H = 4: the edge values F of the
+// Tw + 3 edges between points p and p+1, p = -2 .. Tw (window coordinates),
+// then at each point the fourth-order staggered difference
+//   -dC/dx = (9/8 (F_{j-1/2} - F_{j+1/2}) + 1/24 (F_{j+3/2} - F_{j-3/2})) / dx.
+// Shared memory: G [ND][W2], SP [W2], ARR [W2], LAM [E], REC [NV][2][E], HS.
+template <int PDE, int RKS = RKS_ANY>
+__device__ __forceinline__ void weno_interp_window(const StageArgs& a, const Cx& cx, int64_t win, double* sm)
+{
+    using P = Phys<PDE>;
+    constexpr int NV = P::NV, ND = P::ND;
+    constexpr int H = 4;
+    const int Tw = a.Tw;
+    const int W2 = Tw + 2 * H;
+    const int E = Tw + 3;  // edge t sits between points t-2 and t-1 of the window (shared index t+2, t+3)
+    double* G = sm;
+    double* SP = G + ND * W2;
+    double* ARR = SP + W2;
+    double* LAM = ARR + W2;
+    double* REC = LAM + E;
+    double* HS = REC + NV * 2 * E;
+    const int64_t pe = a.wpp == 1 ? win : win / a.wpp;
+    const int chunk = (int)(win - pe * a.wpp);
+    const int64_t t0 = pe * a.B + (int64_t)chunk * Tw;
+    fill_window<PDE, true>(a, cx, G, SP, HS, pe, chunk, t0, W2, threadIdx.x, blockDim.x, ARR);
+    __syncthreads();
+    for (int t = threadIdx.x; t < E; t += blockDim.x)
+        LAM[t] = 0.5 * fmax(SP[t + 2], SP[t + 3]);
+    __syncthreads();
+    const double eps4 = 4.0 * ((PDE == EULER) ? a.prm[4] : a.prm[1]);
+    const int items = NV * 2 * E;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int r = it / E;
+        const int t = it - r * E;
+        const int v = r >> 1;
+        const double hl = LAM[t];
+        const double* C = G + v * W2;
+        const double* Qv = G + (NV + v) * W2;
+        double rec;
+        if ((r & 1) == 0) {  // f+ on points t-4 .. t, shared index t .. t+4
+            rec = weno5_interp(fma(hl, Qv[t], C[t]), fma(hl, Qv[t + 1], C[t + 1]), fma(hl, Qv[t + 2], C[t + 2]),
+                               fma(hl, Qv[t + 3], C[t + 3]), fma(hl, Qv[t + 4], C[t + 4]), eps4);
+        } else {  // f- on points t+1 .. t-3 (mirrored), shared index t+5 .. t+1
+            rec = weno5_interp(fma(-hl, Qv[t + 5], C[t + 5]), fma(-hl, Qv[t + 4], C[t + 4]),
+                               fma(-hl, Qv[t + 3], C[t + 3]), fma(-hl, Qv[t + 2], C[t + 2]),
+                               fma(-hl, Qv[t + 1], C[t + 1]), eps4);
+        }
+        REC[r * E + t] = rec;
+    }
+    __syncthreads();
+    const double rdx = a.k0;
+    for (int it = threadIdx.x; it < NV * Tw; it += blockDim.x) {
+        const int v = it / Tw;
+        const int jl = it - v * Tw;
+        const int64_t j = t0 + jl;
+        const int c = jl + H;
+        const double* Rp = REC + (2 * v) * E;
+        const double* Rm = REC + (2 * v + 1) * E;
+        // edges of point jl: j-3/2 -> t = jl, j-1/2 -> jl+1, j+1/2 -> jl+2, j+3/2 -> jl+3
+        const double Fl2 = Rp[jl] + Rm[jl], Fl = Rp[jl + 1] + Rm[jl + 1];
+        const double Fr = Rp[jl + 2] + Rm[jl + 2], Fr2 = Rp[jl + 3] + Rm[jl + 3];
+        double K = fma(9.0 / 8.0, Fl - Fr, (1.0 / 24.0) * (Fr2 - Fl2)) * rdx;
+        const double x = G[(NV + v) * W2 + c];
+        if constexpr (PDE == EULER) {
+            if (v == 3) K = fma(-a.prm[1] * x, ARR[c], K);
+        }
+        rk_update<RKS>(a, cx, v, j, chunk * Tw + jl, pe, K, x, rk_load<RKS>(a, cx, v * a.N + j));
+    }
+}
+
+template <int PDE, int RKS>
+__global__ void __launch_bounds__(256, 4) stage_weno_interp(const StageArgs a)
+{
+    extern __shared__ double sm[];
+    weno_interp_window<PDE, RKS>(a, launch_cx(a), blockIdx.x, sm);
+}
+
+// ---------------------------------------------------------------------------
 // batched solves: a persistent grid pulls whole instances (largest first) from
 // a queue; one CTA runs every stage and step of its instance, so all of an
 // instance's PE-to-PE dependencies stay inside the CTA (a barrier between
@@ -765,7 +870,8 @@ cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaSt
 {
     const int64_t windows = a.P * a.wpp;
     const int b1 = atk_stage_block(pde, a.Tw);
-    const size_t smem1 = atk_stage_smem_bytes(pde, a.Tw, a.H);
+    size_t smem1 = atk_stage_smem_bytes(pde, a.Tw, a.H);
+    if (a.weno_interp) smem1 += sizeof(double) * ((pde == atk::EULER ? 8 : 2) + 1) * 2;  // two more edges
     // central stencils on small windows: several windows per CTA (whole PEs
     // only, dividing the window count), so a CTA carries up to 256 threads
     int m = 1;
@@ -833,13 +939,20 @@ cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaSt
         else atk::stage_central<atk::RNS_CHAIN, 3, ANY><<<grid, block, smem, st>>>(b);
         break;
     case atk::EULER:
-        if (kind == atk::RKS_RK3_0) atk::stage_weno<atk::EULER, atk::RKS_RK3_0><<<grid, block, smem, st>>>(b);
+        if (a.weno_interp) atk::stage_weno_interp<atk::EULER, ANY><<<grid, block, smem, st>>>(b);
+        else if (kind == atk::RKS_RK3_0) atk::stage_weno<atk::EULER, atk::RKS_RK3_0><<<grid, block, smem, st>>>(b);
         else if (kind == atk::RKS_RK3_1) atk::stage_weno<atk::EULER, atk::RKS_RK3_1><<<grid, block, smem, st>>>(b);
         else if (kind == atk::RKS_RK3_2) atk::stage_weno<atk::EULER, atk::RKS_RK3_2><<<grid, block, smem, st>>>(b);
         else atk::stage_weno<atk::EULER, ANY><<<grid, block, smem, st>>>(b);
         break;
-    case atk::BURGERS: atk::stage_weno<atk::BURGERS, ANY><<<grid, block, smem, st>>>(b); break;
-    default: atk::stage_weno<atk::ADV_WENO, ANY><<<grid, block, smem, st>>>(b); break;
+    case atk::BURGERS:
+        if (a.weno_interp) atk::stage_weno_interp<atk::BURGERS, ANY><<<grid, block, smem, st>>>(b);
+        else atk::stage_weno<atk::BURGERS, ANY><<<grid, block, smem, st>>>(b);
+        break;
+    default:
+        if (a.weno_interp) atk::stage_weno_interp<atk::ADV_WENO, ANY><<<grid, block, smem, st>>>(b);
+        else atk::stage_weno<atk::ADV_WENO, ANY><<<grid, block, smem, st>>>(b);
+        break;
     }
     return cudaGetLastError();
 }
@@ -862,6 +975,8 @@ cudaError_t atk_set_smem_limits()
         (const void*)atk::stage_weno<atk::EULER, ANY>, (const void*)atk::stage_weno<atk::EULER, atk::RKS_RK3_0>,
         (const void*)atk::stage_weno<atk::EULER, atk::RKS_RK3_1>, (const void*)atk::stage_weno<atk::EULER, atk::RKS_RK3_2>,
         (const void*)atk::stage_weno<atk::ADV_WENO, ANY>, (const void*)atk::stage_weno<atk::BURGERS, ANY>,
+        (const void*)atk::stage_weno_interp<atk::EULER, ANY>, (const void*)atk::stage_weno_interp<atk::ADV_WENO, ANY>,
+        (const void*)atk::stage_weno_interp<atk::BURGERS, ANY>,
         (const void*)atk::stage_central<atk::RNS, 3, ANY>, (const void*)atk::stage_central<atk::RNS, 3, atk::RKS_RK4_0>,
         (const void*)atk::stage_central<atk::RNS, 3, atk::RKS_RK4_MID>,
         (const void*)atk::stage_central<atk::RNS, 3, atk::RKS_RK4_LAST>, (const void*)atk::stage_central<atk::RNS, 2, ANY>,

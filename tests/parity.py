@@ -83,6 +83,7 @@ DET_RUN = {
     "full-1": 4e-9,      # 12 steps, around PE 1 (1.9e-10)
     "ring": 9e-9,        # 25 steps, the history ring test's case (4.1e-10)
     "serve": 8e-9,       # 40 steps, the served detonation request (4.0e-10)
+    "interp": 9e-9,      # 60 steps, the WENO interpolation form (4.4e-10)
 }
 # the served detonation request checked against the oracle: (requested N,
 # seed, request id = instance word, steps); N rounds down to 2,560 (5 PEs of 512)
@@ -97,6 +98,7 @@ DET_CASES = {  # name: (workload kwargs, steps); the same table drives the CPU d
     "sync": (dict(n=4096, pe_size=512, mode="sync", k_max=4, seed=1), 60),
     "as": (dict(n=4096, pe_size=512, mode="as", k_max=4, seed=1), 60),
     "ring": (dict(n=4096, pe_size=512, mode="at", k_max=4, seed=2), 25),
+    "interp": (dict(n=4096, pe_size=512, mode="at", k_max=4, seed=4, weno="interpolate"), 60),
 }
 
 

@@ -20,7 +20,8 @@ import pytest
 
 import oracle
 from paper_2204_01133_gb300 import workloads as W
-from parity import DET_CASES, DET_RUN, DET_STEP, TOL_RUN, TOL_STEP, check, detonation_window, scales
+from parity import (DET_CASES, DET_FULL_SHOCK, DET_FULL_STEPS, DET_RUN, DET_STEP, TOL_RUN, TOL_STEP, check,
+                    detonation_window, scales)
 
 pytestmark = pytest.mark.gpu
 
@@ -152,24 +153,26 @@ def test_burgers_weno(mode):
 
 def test_detonation_full_size_sampled_pes():
     """The N = 2^24, 16,384-PE detonation in the launch configuration the
-    benchmark times.  The oracle recomputes sampled PEs on a 5-PE window of
-    the domain (with the global PE index in the delay counter): after s steps
-    only points within 9 s of the window's outer edges can differ.  PEs 0
-    and 1 hold the shock and take their fixed shock bounds; the others are
-    in smooth or constant flow and take the plain run bound."""
+    benchmark times, 40 steps.  The oracle recomputes sampled PEs on a 5-PE
+    window of the domain (with the global PE index in the delay counter):
+    after s steps only points within 9 s of the window's outer edges can
+    differ, 360 points here, less than the two PEs on each side of the
+    middle one.  PE 0 holds the shock and PE 16,383 the rarefaction behind
+    the slab; they take their fixed shock bounds, the PEs in constant flow
+    (1, 2, 7777, 12345, 16382) the plain run bound."""
     from paper_2204_01133_gb300.api import Solver
-    steps = 12
+    steps = DET_FULL_STEPS
     pb, u0 = W.detonation()
     P, B = pb["n"] // pb["pe_size"], pb["pe_size"]
     s = Solver(pb, u0)
     s.run(steps)
     g = s.read_state()
     gd = s.read_delays()
-    for p in (0, 1, 7777, P - 1):
+    for p in (0, 1, 2, 7777, 12345, P - 2, P - 1):
         spb, sub = detonation_window(pb, u0, p)
         o = oracle.Oracle(spb, sub)
         assert o.run(steps) == 0
-        tol = DET_RUN["full-%d" % p] if p in (0, 1) else TOL_RUN
+        tol = DET_RUN[DET_FULL_SHOCK[p]] if p in DET_FULL_SHOCK else TOL_RUN
         check(spb, g[:, p * B:(p + 1) * B], o.state()[:, 2 * B:3 * B], tol, "PE %d step %d" % (p, steps))
         assert np.array_equal(gd[:, p, :], o.delays()[:, 2, :])
 

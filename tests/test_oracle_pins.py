@@ -896,3 +896,82 @@ def test_weno_interp_conserves_under_sync():
     tot0, tot1 = u0.sum(axis=1), o.state().sum(axis=1)
     # mass, momentum and energy are conserved (the fuel reacts away)
     assert np.all(np.abs(tot1[:3] - tot0[:3]) <= 1e-11 * np.abs(tot0[:3]).max())
+
+
+# --------------------------------------------------------------------------
+# The RK schemes against their textbook forms (Eq. rk1; Shu-Osher RK3-TVD)
+# --------------------------------------------------------------------------
+def _ignition_ode():
+    """Homogeneous reactive Euler: every point follows dY/dt = f(Y) with
+    rho, u, rho E fixed (p from the energy that is not chemical)."""
+    prm = W.det_prm()
+    gamma, A, Ea, Q = prm[0], prm[1], prm[2], prm[3]
+    rho, p0 = 1.0, 10.0
+    E = p0 / (gamma - 1) + Q * 1.0
+
+    def f(Y):
+        p = (gamma - 1) * (E - Q * Y)
+        return -A * Y * math.exp(-Ea * rho / p)
+
+    def oracle_step(rk, dt, Y0=1.0):
+        n = 256
+        Y = np.full(n, Y0)
+        p = (gamma - 1) * (E - Q * Y)
+        init = W.euler_conserved(np.full(n, rho), np.zeros(n), p, Y, prm)
+        pb = W.base_problem(pde="euler", rk=rk, n=n, pe_size=64, dx=0.05, dt=dt, prm=prm, mode="sync", k_max=0)
+        o = oracle.Oracle(pb, init)
+        assert o.run(1) == 0
+        return o.state()[3][0] / rho
+    return f, oracle_step
+
+
+@pytest.mark.parametrize("rk", ["rk2", "rk3tvd", "rk4"])
+def test_rk_step_is_the_textbook_scheme(rk):
+    """One step of the oracle's Butcher-form RK on the 0-D ignition ODE equals
+    the textbook scheme written in its own form: Heun (Eq. rk2), Shu-Osher
+    RK3-TVD (u1 = u + dt f(u); u2 = 3/4 u + 1/4 (u1 + dt f(u1)); u+ = 1/3 u +
+    2/3 (u2 + dt f(u2))), classic RK4.  Other schemes of the same order differ
+    on this nonlinear ODE by far more than the tolerance (checked: Ralston's
+    second-order, Kutta's third-order and the 3/8-rule fourth-order methods)."""
+    f, step = _ignition_ode()
+    dt, y = 0.05, 1.0
+    if rk == "rk2":
+        k1 = f(y)
+        k2 = f(y + dt * k1)
+        want = y + dt / 2 * (k1 + k2)
+        k2r = f(y + 2 / 3 * dt * k1)
+        other = y + dt * (k1 / 4 + 3 / 4 * k2r)                       # Ralston
+    elif rk == "rk3tvd":
+        u1 = y + dt * f(y)
+        u2 = 0.75 * y + 0.25 * (u1 + dt * f(u1))
+        want = y / 3 + 2 / 3 * (u2 + dt * f(u2))
+        k1 = f(y)
+        k2 = f(y + dt / 2 * k1)
+        k3 = f(y - dt * k1 + 2 * dt * k2)
+        other = y + dt / 6 * (k1 + 4 * k2 + k3)                        # Kutta's third order
+    else:
+        k1 = f(y)
+        k2 = f(y + dt / 2 * k1)
+        k3 = f(y + dt / 2 * k2)
+        k4 = f(y + dt * k3)
+        want = y + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        k2 = f(y + dt / 3 * k1)
+        k3 = f(y - dt / 3 * k1 + dt * k2)
+        k4 = f(y + dt * k1 - dt * k2 + dt * k3)
+        other = y + dt / 8 * (k1 + 3 * k2 + 3 * k3 + k4)              # 3/8 rule
+    got = step(rk, dt)
+    tol = 1e-13
+    assert abs(got - want) < tol, (got, want)
+    assert abs(other - want) > 100 * tol, (other, want)
+
+
+def test_all_zero_delay_trace_is_the_synchronous_run():
+    """Replaying a trace of zero delays gives the SYNC run bit for bit (the
+    synchronous scheme is pinned by its closed-form convergence)."""
+    pb, u0 = W.rns(case="flame", n=1024, pe_size=64, mode="at", k_max=4, seed=3, dt=0.003)
+    o = oracle.Oracle(pb, u0)
+    o.set_delay_trace(np.zeros((30, 4, 16, 2), dtype=np.uint8), 0)
+    assert o.run(30) == 0
+    s = oracle.Oracle(dict(pb, mode="sync"), u0)
+    assert s.run(30) == 0
+    assert np.array_equal(o.state(), s.state())

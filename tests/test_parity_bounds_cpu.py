@@ -17,7 +17,8 @@ import parity
 
 @pytest.fixture(scope="module")
 def drifts():
-    return {name: (parity.self_drift(pb, u0, steps), steps) for name, pb, u0, steps in parity.shock_cases()}
+    return {name: (parity.self_drift(pb, u0, steps, cols=cols), steps)
+            for name, pb, u0, steps, cols in parity.shock_cases()}
 
 
 def test_every_shock_case_has_a_bound(drifts):

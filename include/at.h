@@ -116,7 +116,7 @@ enum {
                                records the delays so that a run can be replayed (the oracle
                                does).  0 (default): Philox delays.  AT_EINVAL from at_step if
                                the persistent path cannot be taken.                             */
-    AT_OPT_HISTORY = 4      /* what a buffer point reads at a delayed level m and stage s
+    AT_OPT_HISTORY = 4,     /* what a buffer point reads at a delayed level m and stage s
                                (Sec. 2.3; value AT_HIST_*).  AT_HIST_STAGE (default): the
                                neighbour's stage argument U^{m,(s)} as the neighbour computed it
                                (the per-step message carries every stage).  AT_HIST_RECOMPUTE:
@@ -129,6 +129,15 @@ enum {
                                otherwise.  Both readings give the same values bit for bit when
                                every delay is 0.  Set it before at_set_delays, which seeds the
                                ring of level 0 by the chosen reading.                           */
+    AT_OPT_OPEN_ENDS = 5,   /* 1: the context owns a range of PEs of a larger domain split over
+                               ranks (Sec. 2.1): the buffer points beyond its first and last PE
+                               read windows supplied with at_put_ext instead of wrapping around
+                               the range.  It then advances one stage at a time (at_stage; at_step
+                               returns AT_EINVAL) on the per-stage path, reading B.  0: periodic */
+    AT_OPT_PE_BASE = 6,     /* global index of the context's PE 0 in the whole domain (default 0) */
+    AT_OPT_PE_TOTAL = 7     /* PEs of the whole domain (0, the default: the context's own P); the
+                               delay draws use global PE indices (pe_base + p) mod pe_total, so a
+                               range draws exactly the delays the whole domain draws there      */
 };
 enum { AT_HIST_STAGE = 0, AT_HIST_RECOMPUTE = 1 };
 
@@ -218,6 +227,31 @@ int at_read(at_ctx* ctx, int what, void* dst, size_t bytes, int dst_on_device);
 
 /* Options (AT_OPT_*); they apply from the next at_step on. */
 int at_set_option(at_ctx* ctx, int key, int64_t value);
+
+/* ---- a PE range of a domain split over ranks (AT_OPT_OPEN_ENDS) ----------
+ * The host side of the split exchanges, for every stage, the edge windows of
+ * the stage arguments between neighbouring ranks (the per-step message of S
+ * stages, Sec. 2.3).  at_stage enqueues the next RK stage of the current
+ * step (stage 0 of level n, then 1, ...; after the last one the level is
+ * n + 1); at_step may not be mixed into a step begun with at_stage.
+ * at_edges copies the range's two outer edge windows of U^{level,(stage)}
+ * (the first PE's left window, then the last PE's right window; [2][H][nvar]
+ * FP64, host memory, synchronous) once the stage before it has run: they are
+ * what the neighbouring ranks' buffer points read.  at_put_ext copies a
+ * neighbour's window beyond `side` of the range (0: left of PE 0, that PE's
+ * right edge window; 1: right of PE P-1, its left edge window; [H][nvar] FP64
+ * in host memory, points in increasing x) for (level, stage) into the
+ * context's buffer of outside windows (kept for the ring's levels), to be
+ * read by the stages launched afterwards; it synchronises the stream.
+ * at_delay returns the delay PE `pe` of the context uses at (level, stage,
+ * side): the Philox draw through the start-up clamp, computed on the host
+ * (what the kernels draw), so that a rank knows which levels of a window it
+ * must have before a stage.  AT_EINVAL for levels outside the ring or a
+ * context without open ends where the call needs them. */
+int at_stage(at_ctx* ctx);
+int at_edges(at_ctx* ctx, int64_t level, int stage, double* out);
+int at_put_ext(at_ctx* ctx, int64_t level, int stage, int side, const double* win);
+int at_delay(at_ctx* ctx, int64_t level, int stage, int64_t pe, int side);
 
 /* Delay trace: from the current level on, the kernels write the delay of
  * every (step, stage, PE, side) of the next max_steps steps into trace_dev,

@@ -30,11 +30,12 @@ STAGES = {"rk2": 2, "rk3tvd": 3, "rk4": 4}
 # every symbol include/at.h declares
 SYMBOLS = ("at_create", "at_workspace_bytes", "at_set_problem", "at_set_delays", "at_step", "at_run",
            "at_read", "at_profile", "at_set_option", "at_set_delay_trace", "at_destroy", "at_last_error",
-           "at_run_noalloc",
+           "at_run_noalloc", "at_stage", "at_edges", "at_put_ext", "at_delay",
            "at_batch_table_bytes", "at_batch_create", "at_batch_bind", "at_batch_release", "at_batch_set_config",
            "at_batch_step", "at_batch_run", "at_batch_query", "at_batch_destroy")
 PATH_AUTO, PATH_STAGE, PATH_PERSISTENT, PATH_FUSED = 0, 1, 2, 3
 OPT_PATH, OPT_WAIT_LIMIT, OPT_WITHHOLD_PE, OPT_ARRIVAL, OPT_HISTORY = 0, 1, 2, 3, 4
+OPT_OPEN_ENDS, OPT_PE_BASE, OPT_PE_TOTAL = 5, 6, 7  # a PE range of a domain split over ranks
 WENO_RECONSTRUCT, WENO_INTERPOLATE = 0, 1  # the WENO form of a problem ("weno" key of the dict)
 WENO = {"reconstruct": WENO_RECONSTRUCT, "interpolate": WENO_INTERPOLATE}
 HIST_STAGE, HIST_RECOMPUTE = 0, 1  # reading B (the neighbour's stage arguments) / A (recomputed from u^m)
@@ -99,6 +100,14 @@ def lib():
         L.at_set_delay_trace.restype = ctypes.c_int
         L.at_run_noalloc.argtypes = [P(Problem), P(Delays), vp, ctypes.c_int64, ctypes.c_int, vp]
         L.at_run_noalloc.restype = ctypes.c_int
+        L.at_stage.argtypes = [vp]
+        L.at_stage.restype = ctypes.c_int
+        L.at_edges.argtypes = [vp, ctypes.c_int64, ctypes.c_int, vp]
+        L.at_edges.restype = ctypes.c_int
+        L.at_put_ext.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp]
+        L.at_put_ext.restype = ctypes.c_int
+        L.at_delay.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_int]
+        L.at_delay.restype = ctypes.c_int
         L.at_last_error.restype = ctypes.c_char_p
         for f in ("at_create", "at_set_problem", "at_set_delays", "at_step", "at_run", "at_read", "at_profile",
                   "at_destroy"):
@@ -180,6 +189,8 @@ class Solver:
         self.n = int(pb["n"])
         self.P = self.n // int(pb["pe_size"])
         self.stages = STAGES[pb["rk"]]
+        weno = pb["pde"] in ("euler", "adv_weno", "burgers")
+        self.halo = (4 if pb.get("weno", "reconstruct") == "interpolate" else 3) if weno else int(pb["order"]) // 2
         L = lib()
         self._stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = ctypes.c_void_p()
@@ -192,6 +203,12 @@ class Solver:
             raise AtError(AT_EINVAL, "history is 'stage' or 'recompute'")
         if hist == "recompute":  # before at_set_delays, which seeds level 0 of the ring
             self.set_option(OPT_HISTORY, HIST_RECOMPUTE)
+        # a PE range of a larger domain: global PE indices, and open outer ends
+        if pb.get("pe_total", 0):
+            self.set_option(OPT_PE_BASE, int(pb.get("pe_base", 0)) % int(pb["pe_total"]))
+            self.set_option(OPT_PE_TOTAL, int(pb["pe_total"]))
+        if pb.get("open_ends", 0):
+            self.set_option(OPT_OPEN_ENDS, 1)
         nbytes = workspace_bytes(pb)
         if nbytes == 0:
             raise AtError(AT_EINVAL, lib().at_last_error().decode())
@@ -262,6 +279,28 @@ class Solver:
     def read_trace(self) -> np.ndarray:
         self.torch.cuda.synchronize(self.u.device)
         return self._trace.cpu().numpy()
+
+    # -- a PE range of a domain split over ranks (open ends) ---------------
+    def stage(self):
+        """Enqueue the next RK stage of the current step (at_stage)."""
+        check(lib().at_stage(self._h))
+
+    def edges(self, level: int, stage: int) -> np.ndarray:
+        """The range's outer edge windows of U^{level,(stage)}, [2][H][nvar]."""
+        out = np.empty((2, self.halo, self.nvar), dtype=np.float64)
+        check(lib().at_edges(self._h, int(level), int(stage), ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def put_ext(self, level: int, stage: int, side: int, win) -> None:
+        """A neighbour's [H][nvar] edge window beyond `side` of the range."""
+        w = np.ascontiguousarray(win, dtype=np.float64).reshape(self.halo, self.nvar)
+        check(lib().at_put_ext(self._h, int(level), int(stage), int(side), ctypes.c_void_p(w.ctypes.data)))
+
+    def delay(self, level: int, stage: int, pe: int, side: int) -> int:
+        k = lib().at_delay(self._h, int(level), int(stage), int(pe), int(side))
+        if k < 0:
+            check(k)
+        return k
 
     def set_path(self, path: str):
         self.set_option(OPT_PATH, {"auto": PATH_AUTO, "stage": PATH_STAGE, "persistent": PATH_PERSISTENT,

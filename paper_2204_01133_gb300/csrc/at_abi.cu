@@ -80,11 +80,18 @@ struct Layout {
     int nvar, H, q, S, R;
     int64_t P;
     int Tw, wpp;
-    size_t off_A, off_B, off_acc, off_ring, off_dlog, off_status, off_done, off_gring, total;
-    size_t ring_elems, gring_elems;
+    size_t off_A, off_B, off_acc, off_ring, off_dlog, off_status, off_done, off_gring, off_ext, total;
+    size_t ring_elems, gring_elems, ext_elems;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// element of the history ring [R][S][P][2][H][nvar] at (level, stage, PE, side), h = 0, v = 0
+size_t host_ring_index(const Layout& L, int64_t level, int stage, int64_t pe, int side)
+{
+    const int64_t r = level % L.R;
+    return ((((size_t)r * L.S + stage) * L.P + pe) * 2 + side) * L.H * L.nvar;
+}
 
 int nvar_of(int pde) { return (pde == AT_RNS || pde == AT_EULER || pde == AT_RNS_CHAIN) ? 4 : 1; }
 bool is_weno(int pde) { return pde == AT_EULER || pde == AT_ADV_WENO || pde == AT_BURGERS; }
@@ -186,6 +193,10 @@ Layout layout(const at_problem* pb, const at_delays* dl)
         L.gring_elems = (size_t)L.R * L.S * L.P * 2 * L.H * (pb->pde == AT_RNS ? 8 : 1);
     L.off_gring = off;
     off = align256(off + sizeof(double) * L.gring_elems);
+    // windows beyond the ends of a PE range (open ends): [R][S][2][H][nvar]
+    L.ext_elems = (size_t)L.R * L.S * 2 * L.H * L.nvar;
+    L.off_ext = off;
+    off = align256(off + sizeof(double) * L.ext_elems);
     L.total = off;
     return L;
 }
@@ -307,6 +318,7 @@ atk::StageArgs build_args(const at_problem* pb, const at_delays* dl, const Layou
         a.k0 = 1.0 / dx;
         a.weno_interp = pb->weno == AT_WENO_INTERPOLATE ? 1 : 0;
     }
+    a.ext = (double*)(ws + L.off_ext);
     a.bufA = (double*)(ws + L.off_A);
     a.bufB = (double*)(ws + L.off_B);
     a.state = state;
@@ -338,6 +350,9 @@ struct at_ctx {
     int64_t withhold_pe = -1;
     int arrival = 0;               // at_set_option(AT_OPT_ARRIVAL)
     int hist = AT_HIST_STAGE;      // at_set_option(AT_OPT_HISTORY)
+    int open_ends = 0;             // at_set_option(AT_OPT_OPEN_ENDS): a PE range of a split domain
+    int64_t pe_base = 0, pe_total = 0;  // AT_OPT_PE_BASE, AT_OPT_PE_TOTAL
+    int stage_pos = 0;             // at_stage: the next stage of the current level
     int64_t hist_level = -1;       // reading A: the level whose recomputed stage values the ring holds
     uint8_t* trace = nullptr;      // at_set_delay_trace: caller-owned device buffer
     int64_t trace_n0 = 0, trace_steps = 0;
@@ -476,7 +491,9 @@ int at_set_delays(at_ctx* c, const at_delays* dl)
     e = cudaMemsetAsync(a.ring, 0, sizeof(double) * L.ring_elems, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.dlog, 0, (size_t)L.S * L.P * 2, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.status, 0, 2 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.ext, 0, sizeof(double) * L.ext_elems, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
+    c->stage_pos = 0;
     atk::StageArgs s = a;
     s.u = c->state;
     e = atk_launch_ring_seed(s, c->stream);
@@ -513,6 +530,10 @@ int at_step(at_ctx* c, int64_t nsteps)
     double* A = (double*)(c->ws + L.off_A);
     double* Bf = (double*)(c->ws + L.off_B);
     double* u = c->state;
+    if (c->open_ends) return fail(AT_EINVAL, "a PE range with open ends advances with at_stage");
+    if (c->stage_pos != 0) return fail(AT_ESTATE, "a step begun with at_stage is not finished");
+    c->base.pe_base = c->pe_base;
+    c->base.pe_total = c->pe_total;
     const bool recompute = c->hist == AT_HIST_RECOMPUTE;
     if (recompute) {
         if (c->pb.pde != AT_ADVDIFF && c->pb.pde != AT_RNS)
@@ -756,8 +777,162 @@ int at_set_option(at_ctx* c, int key, int64_t value)
         c->hist = (int)value;
         c->hist_level = -1;
         return AT_OK;
+    case AT_OPT_OPEN_ENDS:
+        if (value != 0 && value != 1) return fail(AT_EINVAL, "AT_OPT_OPEN_ENDS takes 0 or 1");
+        c->open_ends = (int)value;
+        return AT_OK;
+    case AT_OPT_PE_BASE:
+        if (value < 0) return fail(AT_EINVAL, "AT_OPT_PE_BASE must be >= 0");
+        c->pe_base = value;
+        return AT_OK;
+    case AT_OPT_PE_TOTAL:
+        if (value < 0 || value >= ((int64_t)1 << 32)) return fail(AT_EINVAL, "AT_OPT_PE_TOTAL out of range");
+        c->pe_total = value;
+        return AT_OK;
     default: return fail(AT_EINVAL, "unknown option %d", key);
     }
+}
+
+// ---------------------------------------------------------------------------
+// a PE range of a domain split over ranks
+// ---------------------------------------------------------------------------
+namespace {
+// Philox4x32-10 word 0 on the host, as the kernels compute it (Salmon et al.,
+// SC'11: ten rounds of two 32x32->64 products, Weyl key increments)
+uint32_t host_philox_w0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1)
+{
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0, n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c0 = n0;
+        c1 = (uint32_t)p1;
+        c2 = n2;
+        c3 = (uint32_t)p0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c0;
+}
+
+// the range range checks shared by at_stage / at_edges / at_put_ext
+int range_ready(at_ctx* c)
+{
+    if (!c) return fail(AT_EINVAL, "context is NULL");
+    if (!c->have_problem || !c->have_delays) return fail(AT_ESTATE, "at_set_problem and at_set_delays must come first");
+    return AT_OK;
+}
+
+bool level_in_ring(const at_ctx* c, int64_t level)
+{
+    // the current level and the older ones the ring still keeps
+    return level >= 0 && level <= c->level && level > c->level - c->L.R;
+}
+} // namespace
+
+int at_delay(at_ctx* c, int64_t level, int stage, int64_t pe, int side)
+{
+    int st = range_ready(c);
+    if (st != AT_OK) return st;
+    if (level < 0 || stage < 0 || stage >= c->L.S || pe < 0 || pe >= c->L.P || (side != 0 && side != 1))
+        return fail(AT_EINVAL, "level, stage, PE or side out of range");
+    const atk::StageArgs& a = c->base;
+    if (a.mode == atk::SYNC) return 0;
+    int64_t gpe = pe;
+    if (c->pe_total > 0) {
+        gpe += c->pe_base;
+        if (gpe >= c->pe_total) gpe -= c->pe_total;
+    }
+    const uint32_t sc = a.per_stage ? (uint32_t)stage : 0u;
+    const uint32_t x = host_philox_w0((uint32_t)level, (uint32_t)gpe, sc | (uint32_t)side << 8, a.instance, a.key0,
+                                      a.key1);
+    int k = 0;
+    for (int i = 0; i < a.kmax; ++i) k += ((uint64_t)x >= a.thr[i]) ? 1 : 0;
+    int64_t avail = level - ((a.mode == atk::AT) ? a.q : 0);
+    if (avail < 0) avail = 0;
+    return (int64_t)k < avail ? k : (int)avail;
+}
+
+int at_stage(at_ctx* c)
+{
+    int st = range_ready(c);
+    if (st != AT_OK) return st;
+    if (c->hist == AT_HIST_RECOMPUTE) return fail(AT_EINVAL, "at_stage runs reading B of the stage history");
+    if (c->arrival) return fail(AT_EINVAL, "at_stage uses drawn delays");
+    if (c->level >= kMaxLevel) return fail(AT_EINVAL, "a solve is limited to %lld steps", (long long)kMaxLevel);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    const Layout& L = c->L;
+    double* A = (double*)(c->ws + L.off_A);
+    double* Bf = (double*)(c->ws + L.off_B);
+    double* u = c->state;
+    const int s = c->stage_pos;
+    atk::StageArgs a = c->base;
+    a.level = c->level;
+    a.u = u;
+    a.stage = s;
+    a.open_ends = c->open_ends;
+    a.pe_base = c->pe_base;
+    a.pe_total = c->pe_total;
+    a.trace = c->trace;
+    a.trace_n0 = c->trace_n0;
+    a.trace_steps = c->trace_steps;
+    // the buffers of at_step's per-stage loop
+    a.X = (s == 0) ? u : ((s % 2 == 1) ? A : Bf);
+    a.Y = (s == L.S - 1) ? u : ((s % 2 == 0) ? A : Bf);
+    e = record(c, true);
+    if (e == cudaSuccess) e = atk_launch_stage(a, c->pb.pde, c->pb.order, c->stream);
+    if (e == cudaSuccess) e = record(c, false);
+    if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+    ++c->launched;
+    c->last_path = AT_PATH_STAGE;
+    if (++c->stage_pos == L.S) {
+        c->stage_pos = 0;
+        ++c->level;
+    }
+    g_err[0] = 0;
+    return AT_OK;
+}
+
+int at_edges(at_ctx* c, int64_t level, int stage, double* out)
+{
+    int st = range_ready(c);
+    if (st != AT_OK) return st;
+    if (!out) return fail(AT_EINVAL, "destination is NULL");
+    if (stage < 0 || stage >= c->L.S || !level_in_ring(c, level))
+        return fail(AT_EINVAL, "level %lld stage %d is not in the ring", (long long)level, stage);
+    const Layout& L = c->L;
+    const size_t win = (size_t)L.H * L.nvar;
+    cudaError_t e = cudaSetDevice(c->device);
+    const double* ring = c->base.ring;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, ring + host_ring_index(L, level, stage, 0, 0), sizeof(double) * win,
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out + win, ring + host_ring_index(L, level, stage, L.P - 1, 1), sizeof(double) * win,
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "edge window copy");
+    return AT_OK;
+}
+
+int at_put_ext(at_ctx* c, int64_t level, int stage, int side, const double* win)
+{
+    int st = range_ready(c);
+    if (st != AT_OK) return st;
+    if (!win) return fail(AT_EINVAL, "window is NULL");
+    if (!c->open_ends) return fail(AT_EINVAL, "outside windows need AT_OPT_OPEN_ENDS");
+    if (stage < 0 || stage >= c->L.S || (side != 0 && side != 1) || level < 0)
+        return fail(AT_EINVAL, "level, stage or side out of range");
+    const Layout& L = c->L;
+    const size_t n = (size_t)L.H * L.nvar;
+    const int64_t r = level % L.R;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->base.ext + ((r * L.S + stage) * 2 + side) * n, win, sizeof(double) * n,
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "outside window copy");
+    return AT_OK;
 }
 
 int at_set_delay_trace(at_ctx* c, uint8_t* trace_dev, int64_t max_steps)

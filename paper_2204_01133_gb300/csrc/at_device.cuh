@@ -56,6 +56,10 @@ struct StageArgs {
     int hist_recompute;  // 1: the ring holds stage values recomputed from u^m (reading A); the
                          //    stage kernels then push nothing into it
     int weno_interp;     // WENO PDEs: 1 the interpolation form (edge values, halo 4)
+    // a PE range of a larger domain (split over ranks)
+    int open_ends;       // 1: the range's outer buffer points read ext, not the ring
+    double* ext;         // windows beyond the range's ends [R][S][2][H][nvar]
+    int64_t pe_base, pe_total;  // global index of PE 0 and the domain's PE count (0: P)
     // delay trace (optional): the delay of every (step, stage, PE, side) of
     // levels trace_n0 .. trace_n0 + trace_steps - 1, [steps][S][P][2]
     uint8_t* trace;
@@ -94,7 +98,12 @@ __device__ __forceinline__ int keff_at(const StageArgs& a, int64_t level, int st
 {
     if (a.mode == SYNC) return 0;
     const uint32_t sc = a.per_stage ? (uint32_t)stage : 0u;
-    const uint32_t x = philox_w0((uint32_t)level, (uint32_t)pe, sc | ((uint32_t)side << 8), a.instance,
+    int64_t gpe = pe;  // the global PE index (a range of a larger domain draws the domain's delays)
+    if (a.pe_total > 0) {
+        gpe += a.pe_base;
+        if (gpe >= a.pe_total) gpe -= a.pe_total;
+    }
+    const uint32_t x = philox_w0((uint32_t)level, (uint32_t)gpe, sc | ((uint32_t)side << 8), a.instance,
                                  a.key0, a.key1);
     int k = 0;
     for (int i = 0; i < a.kmax; ++i) k += ((uint64_t)x >= a.thr[i]) ? 1 : 0;
@@ -204,6 +213,20 @@ __device__ __forceinline__ int64_t ring_index(const StageArgs& a, int64_t level,
 {
     const int64_t r = (int64_t)((uint32_t)level % (uint32_t)a.R);
     return ((((r * a.S + stage) * a.P + pe) * 2 + side) * a.H + h) * a.nvar + v;
+}
+
+// The nvar values buffer point h beyond PE pe's `side` edge reads at level m,
+// stage s: the neighbour's edge window in the ring (the neighbour's side
+// 1 - side), or, at the outer edges of a range with open ends, the window
+// supplied from outside the range.
+__device__ __forceinline__ const double* halo_window(const StageArgs& a, int64_t m, int s, int64_t pe, int side, int h)
+{
+    if (a.open_ends && (side == 0 ? pe == 0 : pe == a.P - 1)) {
+        const int64_t r = (int64_t)((uint32_t)m % (uint32_t)a.R);
+        return a.ext + (((r * a.S + s) * 2 + side) * a.H + h) * a.nvar;
+    }
+    const int64_t nbr = side == 0 ? (pe == 0 ? a.P - 1 : pe - 1) : (pe == a.P - 1 ? 0 : pe + 1);
+    return a.ring + ring_index(a, m, s, nbr, 1 - side, h, 0);
 }
 
 // the same slot in the ring of derived quantities (nd per point)

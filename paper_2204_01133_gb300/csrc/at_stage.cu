@@ -86,13 +86,12 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
             const int hp = t / nw, l = t - hp * nw;         // buffer point, level
             const int side = hp < L0 ? 0 : 1;
             const int h = side == 0 ? hp : hp - L0;         // position in the neighbour's edge window
-            const int64_t nbr = side == 0 ? (pe == 0 ? a.P - 1 : pe - 1) : (pe == a.P - 1 ? 0 : pe + 1);
             const int k = keff_at(a, cx.level, cx.stage, pe, side);
             if (h == 0 && l == 0) log_delay(a, cx.level, cx.stage, pe, side, k);
             if ((a.wnz[k] >> l) & 1) {  // a level with weight 0 is not part of the scheme (and may not exist yet)
-                const int64_t base = ring_index(a, cx.level - k - l, cx.stage, nbr, 1 - side, h, 0);
+                const double* src = halo_window(a, cx.level - k - l, cx.stage, pe, side, h);
 #pragma unroll
-                for (int v = 0; v < NV; ++v) Q[v] = a.ring[base + v];
+                for (int v = 0; v < NV; ++v) Q[v] = src[v];
                 if constexpr (WENO) {
                     if (l == 0) {  // the wave speed at level n-k, not extrapolated
                         double sp, unused;
@@ -362,7 +361,6 @@ __global__ void __launch_bounds__(256, PPL <= 2 ? 6 : (PPL == 4 ? 4 : 3)) stage_
     if (lane < 2 * H) {  // one buffer point: delay draw, delayed ring levels, extrapolation
         const int side = lane < H ? 0 : 1;
         const int h = lane - side * H;  // position in the neighbour's edge window
-        const int64_t nbr = side == 0 ? (pe == 0 ? a.P - 1 : pe - 1) : (pe == a.P - 1 ? 0 : pe + 1);
         const int k = keff_at(a, cx.level, cx.stage, pe, side);
         if (h == 0) log_delay(a, cx.level, cx.stage, pe, side, k);
         const int nw = (a.mode == AT) ? a.q + 1 : 1;
@@ -370,8 +368,7 @@ __global__ void __launch_bounds__(256, PPL <= 2 ? 6 : (PPL == 4 ? 4 : 3)) stage_
 #pragma unroll
         for (int l = 0; l <= AT_QMAX; ++l) {
             v[l] = 0.0;  // a level with weight 0 is not part of the scheme (and may not exist yet)
-            if (l < nw && ((a.wnz[k] >> l) & 1))
-                v[l] = a.ring[ring_index(a, cx.level - k - l, cx.stage, nbr, 1 - side, h, 0)];
+            if (l < nw && ((a.wnz[k] >> l) & 1)) v[l] = *halo_window(a, cx.level - k - l, cx.stage, pe, side, h);
         }
         double acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * v[0];
 #pragma unroll

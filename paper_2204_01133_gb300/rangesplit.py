@@ -21,8 +21,9 @@ the steps, so that ranks that stopped early and ranks that finished leave
 the process group together.
 
 The engine is anything with these calls (``oracle.Oracle`` on a window
-problem with ``open_ends`` provides them; a GPU engine would be a context
-whose outer buffer points read windows put into its ring from outside):
+problem with ``open_ends`` provides them, and ``ContextEngine`` wraps a
+library context on the GPU whose outer buffer points read windows put into
+it from outside, ``at_put_ext``):
 
     level, stages, halo, nvar, P     current level n and the window's sizes
     stage_begin(s)                   form U^{n,(s)}
@@ -70,6 +71,41 @@ def levels_read(mode: str, q: int, n: int, k: int):
     if mode == "as" or k == 0:
         return [n - k]
     return [n - k - l for l in range(q + 1)]
+
+
+class ContextEngine:
+    """A library context (``api.Solver`` on the range's problem with
+    ``open_ends``, ``pe_base`` and ``pe_total`` in its dict) as the stage
+    engine of a rank.  The stage kernels form the next stage argument as part
+    of their update (Eq. rk1), so stage_begin is empty: U^{n,(s)} of the
+    range's outer edges is in the ring once stage s-1 has run."""
+
+    def __init__(self, solver):
+        self.s = solver
+        self.stages, self.halo, self.nvar, self.P = solver.stages, solver.halo, solver.nvar, solver.P
+        self.level = 0
+
+    def stage_begin(self, s):
+        pass
+
+    def edges(self, level, s):
+        return self.s.edges(level, s)
+
+    def set_ext(self, level, s, side, win):
+        self.s.put_ext(level, s, side, win)
+
+    def delay(self, level, s, pe, side):
+        return self.s.delay(level, s, pe, side)
+
+    def stage_rhs(self, s):
+        self.s.stage()
+
+    def step_end(self):
+        self.level += 1
+        return 0
+
+    def state(self):
+        return self.s.read_state()
 
 
 class GlooTransport:

@@ -92,7 +92,7 @@ BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4}
 TRAFFIC_PER_LAUNCH = {
     ("rns-flame-n16384", "persistent"): 2.5390e6,  # state and rings read once, writes stay in L2
     ("rns-flame-n16777216", "stage"): 1.6610e9 + 1.0863e9,
-    ("detonation-n16777216", "stage"): 2 * (2.7273e8 + 2.2529e8),  # captured at N = 2^23, x2
+    ("detonation-n16777216", "stage"): 2 * (2.7221e8 + 2.2493e8),  # captured at N = 2^23, x2
     ("advdiff-n134217728", "stage"): 4 * (8.7079e8 + 5.1163e8),
     ("advdiff-n33554432", "stage"): 8.7079e8 + 5.1163e8,
     ("advdiff-n134217728", "fused"): 4 * (4.6984e8 + 3.0259e8),  # one step: u^n, u^{n+1}, the ring
@@ -106,7 +106,7 @@ TRAFFIC_PER_LAUNCH = {
 # csrc/*.cu and *.cuh (sorted by name, concatenated).  When the sources
 # change, the counts may no longer hold: the roofline is then marked stale
 # and its traffic is reported as null until the captures are redone.
-PROFILED_SOURCES_SHA256 = "ac787879bc04368984897f205943f9375f3515bb345408ff48fdb57f986b7d55"
+PROFILED_SOURCES_SHA256 = "57eed2dbf2f2ea9a67b10d130ed5870b784963e26f445c30277d208f151e8a79"
 
 
 def sources_sha256() -> str:

@@ -528,7 +528,8 @@ static void rhs_point(const orc_ctx* c, int64_t level, int s, int64_t p, int64_t
             /* edge point values: the fourth-order staggered difference
              * f'_j = (9/8 (F_{j+1/2} - F_{j-1/2}) - 1/24 (F_{j+3/2} - F_{j-3/2})) / dx
              * (the paper gives no derivative formula for interpolated edge
-             * values; this is the reading, see the design notes) */
+             * values; this difference is conservative and keeps the fourth
+             * order the paper states for the AT interpolant's full stencil) */
             double Fr2[4], Fl2[4];
             edge_flux(c, level, s, p, j + 1, Fr2);
             edge_flux(c, level, s, p, j - 2, Fl2);

@@ -1,12 +1,12 @@
-"""Multi-rank helpers: one process per GPU, no data-path collective.
+"""Multi-rank helpers: one process per GPU.
 
-The hot path shards by independent units: replicas of a single problem
-(each rank runs its own instance, with its own Philox counter word), or the
-instances of a batch split over the ranks.  Neither needs an exchange while
-it runs; the only collectives are around the timed region (a barrier and the
-maximum of the per-rank times).  Splitting one large domain over GPUs would
-add a neighbour put of each rank's edge windows per step; on one-GPU machines
-that remains a design (see the repository's design notes).
+Replicas and batches shard by independent units: each rank runs its own
+instance (with its own Philox counter word), or a share of a batch's
+instances split by work (longest processing time first).  Neither needs an
+exchange while it runs; the only collectives are around the timed region (a
+barrier and the maximum of the per-rank times).  Splitting one domain over
+ranks by PE ranges, with the edge windows of every stage exchanged between
+neighbouring ranks, is in ``rangesplit``.
 """
 from __future__ import annotations
 

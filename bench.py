@@ -47,6 +47,9 @@ WORKLOADS = {
     "detonation-n8388608": dict(kind="detonation", n=1 << 23, pe_size=1024, mode="at", k_max=4, seed=0),
     "rns-flame-n16777216": dict(kind="rns", case="flame", n=1 << 24, pe_size=64, mode="at", k_max=4, seed=0,
                                 dt=0.003),
+    # half of it, for counter captures (inputs still larger than L2)
+    "rns-flame-n8388608": dict(kind="rns", case="flame", n=1 << 23, pe_size=64, mode="at", k_max=4, seed=0,
+                               dt=0.003),
     # 4,096 reacting instances, N log-uniform in [256, 8192] (9.4 M points), one batched launch
     "batched-rns-4096": dict(kind="batched", count=4096, seed=0),
     # Poisson arrivals at 2,000 requests/s of the three problem types, N log-uniform in
@@ -69,6 +72,7 @@ FLOPS_PER_POINT_STAGE = {
     ("advdiff", "stage"): 13.56,     # 5-tap merged stencil + RK4 update, mean of the 4 stages
     ("advdiff", "persistent"): 13.56,
     ("advdiff", "fused"): 13.56,     # the method's work only (13.65 as executed, with the recomputed edge points)
+    ("rns", "fused"): 176.3,         # the method's work only (the tile-fused kernel also recomputes the strips)
 }
 # The method's own FP64 work per point per stage, by operation count (a
 # divide, square root or exponential counts as one operation): the
@@ -84,7 +88,7 @@ ALG_FLOPS_PER_POINT_STAGE = {"detonation": 560.0, "rns": 155.0, "advdiff": 13.0}
 # a step reads and writes (RK4: 17 arrays, RK3-TVD: 8) x nvar x 8 B / stages.
 BYTES_PER_POINT_STAGE = {"rns": 17 * 4 * 8 / 4, "detonation": 8 * 4 * 8 / 3, "advdiff": 17 * 8 / 4}
 # the step-fused path reads u^n and writes u^{n+1} once per step (+ the ring)
-BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4}
+BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4, "rns": 2 * 4 * 8 / 4}
 # DRAM bytes per launch of the timed kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum) from the ncu captures of the current kernels, by
 # workload and path; the advection-diffusion kernels were captured at

@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "libat_gb300.so")
 PROBE = os.path.join(HERE, "libat_probe.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["at_abi.cu", "at_stage.cu", "at_persist.cu", "at_cluster.cu", "at_fused.cu"]
+SOURCES = ["at_abi.cu", "at_stage.cu", "at_persist.cu", "at_cluster.cu", "at_fused.cu", "at_tilefused.cu"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--fmad=true", "-Xptxas", "-O3"]
 
 

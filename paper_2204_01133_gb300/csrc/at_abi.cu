@@ -33,6 +33,9 @@ bool atk_fused_supported(int pde, int order, int B, int S);
 int atk_fused_multi_w(int order, int rk, int B, int S, int64_t P, int device);
 cudaError_t atk_launch_fused_steps(const atk::StageArgs& a, int order, int W, int64_t level0, int64_t nsteps,
                                    double* b0, double* b1, cudaStream_t st);
+bool atk_tile_fused_supported(int pde, int order, int B, int rk, int q);
+cudaError_t atk_launch_tile_fused(const atk::StageArgs& a, int pde, int order, int64_t n, const double* uin,
+                                  double* uout, cudaStream_t st);
 cudaError_t atk_launch_fused(const atk::StageArgs& a, int order, int64_t n, const double* uin, double* uout,
                              cudaStream_t st);
 cudaError_t atk_launch_persist(const atk::StageArgs& a, int pde, int order, int64_t level0, int64_t nsteps,
@@ -547,6 +550,9 @@ int at_step(at_ctx* c, int64_t nsteps)
         return fail(AT_EINVAL, "the persistent path needs a central PDE and at most %lld PEs (have %lld)",
                     (long long)c->persist_cap, (long long)L.P);
     const bool fused_ok = !recompute && atk_fused_supported(c->pb.pde, c->pb.order, c->pb.pe_size, L.S);
+    // the reacting flow: the tile-fused kernel, on request only (AT_PATH_FUSED)
+    const bool tile_ok = !recompute && !fused_ok &&
+                         atk_tile_fused_supported(c->pb.pde, c->pb.order, c->pb.pe_size, c->pb.rk, L.q);
     const bool cluster_ok = c->cluster_c > 0 && !c->arrival && c->withhold_pe < 0;
     bool persist = c->path == AT_PATH_PERSISTENT || (c->path == AT_PATH_AUTO && can_persist);
     // advection-diffusion beyond one thread-block cluster: the step-fused
@@ -559,9 +565,10 @@ int at_step(at_ctx* c, int64_t nsteps)
         return fail(AT_EINVAL, "delays by arrival need the persistent path (a central PDE and at most %lld PEs)",
                     (long long)c->persist_cap);
     if (c->path == AT_PATH_FUSED || (c->path == AT_PATH_AUTO && !persist && !c->arrival && fused_ok)) {
-        if (!fused_ok)
-            return fail(AT_EINVAL, "the fused path takes advection-diffusion with PEs of 32, 64, 128 or 256 points "
-                                   "and at least stages x halo points");
+        if (!fused_ok && !tile_ok)
+            return fail(AT_EINVAL, "the fused path takes advection-diffusion with PEs of 32, 64, 128 or 256 points, "
+                                   "or the reacting flow in flux form, with at least stages x halo points per PE");
+        if (c->arrival) return fail(AT_EINVAL, "delays by arrival need the persistent path");
         c->last_path = AT_PATH_FUSED;
         c->base.trace = c->trace;
         c->base.trace_n0 = c->trace_n0;
@@ -591,7 +598,9 @@ int at_step(at_ctx* c, int64_t nsteps)
             atk::StageArgs a = c->base;
             a.level = c->level;
             e = record(c, true);
-            if (e == cudaSuccess) e = atk_launch_fused(a, c->pb.order, c->level, cur, nxt, c->stream);
+            if (e == cudaSuccess)
+                e = fused_ok ? atk_launch_fused(a, c->pb.order, c->level, cur, nxt, c->stream)
+                             : atk_launch_tile_fused(a, c->pb.pde, c->pb.order, c->level, cur, nxt, c->stream);
             if (e != cudaSuccess) return cuda_fail(e, "fused step kernel launch");
             e = record(c, false);
             if (e != cudaSuccess) return cuda_fail(e, "profiling event");

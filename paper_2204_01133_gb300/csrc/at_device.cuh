@@ -394,4 +394,43 @@ struct Phys<BURGERS> {
     }
 };
 
+// ---------------------------------------------------------------------------
+// The RK update of the step-fused kernels, stage by stage: the next stage
+// argument (u^{n+1} after the last stage) from K, the stage argument x and
+// u^n, with the formulas and operation order of the per-stage kernels'
+// update; the accumulator (RK2, RK4) is carried by the caller.
+// ---------------------------------------------------------------------------
+template <int RK>
+struct RkS {
+    static constexpr int S = RK == RK4 ? 4 : (RK == RK3TVD ? 3 : 2);
+};
+
+// the update of the per-stage kernels (rk_update), stage by stage: y from K,
+// the stage argument x and u^n; the accumulator is carried by the caller
+template <int RK>
+__device__ __forceinline__ double fused_update(const StageArgs& a, int s, double K, double x, double un, double& acc)
+{
+    if (RK == RK4) {
+        if (s == 0) {
+            acc = K;
+            return fma(a.hdt, K, un);
+        }
+        if (s < 3) {
+            acc = fma(2.0, K, acc);
+            return fma(s == 1 ? a.hdt : a.dt, K, un);
+        }
+        return fma(a.dt6, acc + K, un);
+    }
+    if (RK == RK3TVD) {
+        if (s == 0) return fma(a.dt, K, x);
+        if (s == 1) return fma(0.75, un, 0.25 * fma(a.dt, K, x));
+        return fma(1.0 / 3.0, un, (2.0 / 3.0) * fma(a.dt, K, x));
+    }
+    if (s == 0) {
+        acc = K;
+        return fma(a.dt, K, un);
+    }
+    return fma(a.hdt, acc + K, un);
+}
+
 } // namespace atk

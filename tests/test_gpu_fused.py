@@ -79,7 +79,7 @@ def test_fused_full_size_equals_per_stage():
 
 def test_fused_rejects_what_it_does_not_take():
     from paper_2204_01133_gb300.api import Solver, OPT_ARRIVAL
-    pb, u0 = W.rns(case="flame", n=4096, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003)
+    pb, u0 = W.detonation(n=4096, pe_size=512, mode="at", k_max=4, seed=0)
     s = Solver(pb, u0, path="fused")
     with pytest.raises(RuntimeError):
         s.run(1)
@@ -127,3 +127,64 @@ def test_fused_wait_runs_out_without_fault():
     s.run(50)
     ref, _ = _run(pb, u0, [50], "stage")
     assert np.array_equal(s.read_state(), ref)
+
+
+# --------------------------------------------------------------------------
+# the reacting flow: the tile-fused kernel (a tile of PEs plus recomputed
+# strips of the neighbours, all stages of a step in shared memory)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("pe_size,pes,order,mode,rk,per_stage,case", [
+    (64, 256, 6, "at", "rk4", 1, "flame"),         # config 1: 64 tiles of 4 PEs
+    (64, 13, 6, "at", "rk4", 1, "ignition"),       # a partial last tile (4, 4, 4, 1)
+    (32, 20, 4, "as", "rk4", 1, "flame"),          # tiles of 8 PEs
+    (128, 6, 6, "at", "rk3tvd", 0, "ignition"),    # tiles of 2, one delay per step
+    (256, 3, 4, "sync", "rk2", 1, "flame"),        # one PE per tile
+    (512, 2, 2, "at", "rk4", 1, "flame"),          # a PE larger than the tile target
+    (64, 1, 6, "at", "rk4", 1, "flame"),           # one PE, its own neighbour
+])
+def test_tile_fused_reacting_flow_equals_per_stage_bitwise(pe_size, pes, order, mode, rk, per_stage, case):
+    pb, u0 = W.rns(case=case, n=pe_size * pes, pe_size=pe_size, order=order, mode=mode, k_max=4, seed=9,
+                   dt=0.003, per_stage=per_stage)
+    pb = dict(pb, rk=rk)
+    a_state, a_del = _run(pb, u0, [40], "stage")
+    b_state, b_del = _run(pb, u0, [13, 1, 26], "fused")  # odd chunks end with the copy back
+    assert np.array_equal(a_state, b_state) and np.array_equal(a_del, b_del)
+
+
+def test_tile_fused_parity_with_oracle():
+    pb, u0 = W.rns(case="flame", n=2048, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003)
+    parity(pb, u0, 150, path="fused", what="tile-fused flame")
+
+
+def test_tile_fused_alternates_with_other_paths():
+    from paper_2204_01133_gb300.api import Solver
+    pb, u0 = W.rns(case="flame", n=16384, pe_size=64, mode="at", k_max=4, seed=2, dt=0.003)
+    ref, _ = _run(pb, u0, [100], "stage")
+    s = Solver(pb, u0, path="fused")
+    s.run(31)
+    s.set_path("stage")
+    s.run(20)
+    s.set_path("persistent")
+    s.run(19)
+    s.set_path("fused")
+    s.run(30)
+    assert np.array_equal(s.read_state(), ref)
+
+
+def test_tile_fused_full_size_equals_per_stage_and_the_oracle():
+    """The reacting flame at N = 2^24 (2^18 PEs of 64, the size of the large
+    per-stage benchmark run): the whole state bit for bit the per-stage path's
+    after 6 steps, and sampled PEs against the oracle on 5-PE windows."""
+    import oracle
+    from parity import TOL_RUN, check
+    pb, u0 = W.rns(case="flame", n=1 << 24, pe_size=64, mode="at", k_max=4, seed=0, dt=0.003)
+    a_state, a_del = _run(pb, u0, [6], "stage")
+    b_state, b_del = _run(pb, u0, [6], "fused")
+    assert np.array_equal(a_state, b_state) and np.array_equal(a_del, b_del)
+    P, B = pb["n"] // pb["pe_size"], pb["pe_size"]
+    for p in (0, 77777, P - 1):
+        idx = np.arange(p - 2, p + 3) % P
+        sub = np.concatenate([u0[:, i * B:(i + 1) * B] for i in idx], axis=1)
+        o = oracle.Oracle(dict(pb, n=5 * B, pe_base=p - 2, pe_total=P), sub)
+        assert o.run(6) == 0
+        check(pb, b_state[:, p * B:(p + 1) * B], o.state()[:, 2 * B:3 * B], TOL_RUN, "tile-fused PE %d" % p)

@@ -103,6 +103,8 @@ TRAFFIC_PER_LAUNCH = {
     ("advdiff-n33554432", "fused"): 4.6984e8 + 3.0259e8,
     ("advdiff-n2048", "persistent"): 7.7824e4,  # one-cluster launch: state and ring read once
     ("advdiff-n16384", "fused"): 2.8288e5,  # cooperative fused launch: state and ring read once
+    ("rns-flame-n16777216", "fused"): 2 * (2.6963e8 + 3.1761e8),  # tile-fused step, captured at N = 2^23, x2
+    ("rns-flame-n8388608", "fused"): 2.6963e8 + 3.1761e8,
 }
 
 

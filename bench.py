@@ -73,6 +73,7 @@ FLOPS_PER_POINT_STAGE = {
     ("advdiff", "persistent"): 13.56,
     ("advdiff", "fused"): 13.56,     # the method's work only (13.65 as executed, with the recomputed edge points)
     ("rns", "fused"): 176.3,         # the method's work only (the tile-fused kernel also recomputes the strips)
+    ("detonation", "fused"): 678.9,  # likewise: the per-stage kernel's count
 }
 # The method's own FP64 work per point per stage, by operation count (a
 # divide, square root or exponential counts as one operation): the
@@ -88,7 +89,7 @@ ALG_FLOPS_PER_POINT_STAGE = {"detonation": 560.0, "rns": 155.0, "advdiff": 13.0}
 # a step reads and writes (RK4: 17 arrays, RK3-TVD: 8) x nvar x 8 B / stages.
 BYTES_PER_POINT_STAGE = {"rns": 17 * 4 * 8 / 4, "detonation": 8 * 4 * 8 / 3, "advdiff": 17 * 8 / 4}
 # the step-fused path reads u^n and writes u^{n+1} once per step (+ the ring)
-BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4, "rns": 2 * 4 * 8 / 4}
+BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4, "rns": 2 * 4 * 8 / 4, "detonation": 2 * 4 * 8 / 3}
 # DRAM bytes per launch of the timed kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum) from the ncu captures of the current kernels, by
 # workload and path; the advection-diffusion kernels were captured at
@@ -131,7 +132,7 @@ def kernel_label(kind, path, pb, arrival=False):
     as the library: small advection-diffusion problems take the one-cluster
     kernel on the persistent path)."""
     if path == "fused":
-        return "step_fused_" + kind
+        return "step_fused_" + kind if kind == "advdiff" else "tile_fused_" + kind
     if path == "persistent" and kind == "advdiff" and not arrival and pb["pe_size"] in (32, 64, 128, 256):
         P = pb["n"] // pb["pe_size"]
         if any(P % c == 0 and P // c <= 4 for c in range(min(P, 16), 0, -1)):

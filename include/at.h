@@ -92,8 +92,9 @@ enum { AT_READ_STATE = 0, AT_READ_DELAYS = 1, AT_READ_RING = 2, AT_READ_STATS = 
  * else one launch per step (advection-diffusion, PEs of 32, 64, 128 or 256
  * points and at least stages x halo points; the reacting flow in flux form,
  * one launch per step over tiles of up to 8 PEs with recomputed strips of
- * the outer neighbours, PEs of at least stages x halo points; AT_EINVAL from
- * at_step otherwise; u^{n+1} goes to workspace field A and back, so an odd
+ * the outer neighbours, PEs of at least stages x halo points; the WENO PDEs
+ * in the reconstruction form, one launch per step over the per-stage
+ * windows with recomputed strips; AT_EINVAL from at_step otherwise; u^{n+1} goes to workspace field A and back, so an odd
  * number of steps in one call ends with a device copy of the state); AT_PATH_AUTO
  * (default) takes the one-cluster kernel when it can, else for
  * advection-diffusion the fused path when it can, else the persistent path

@@ -550,9 +550,12 @@ int at_step(at_ctx* c, int64_t nsteps)
         return fail(AT_EINVAL, "the persistent path needs a central PDE and at most %lld PEs (have %lld)",
                     (long long)c->persist_cap, (long long)L.P);
     const bool fused_ok = !recompute && atk_fused_supported(c->pb.pde, c->pb.order, c->pb.pe_size, L.S);
-    // the reacting flow: the tile-fused kernel, on request only (AT_PATH_FUSED)
-    const bool tile_ok = !recompute && !fused_ok &&
-                         atk_tile_fused_supported(c->pb.pde, c->pb.order, c->pb.pe_size, c->pb.rk, L.q);
+    // the reacting flow and the WENO PDEs: the tile-fused kernels, on request
+    // only (AT_PATH_FUSED); a WENO tile is one window plus strips of S H
+    // points, which must stay inside the window's PE or its neighbour
+    const bool tile_ok = !recompute && !fused_ok && c->pb.weno != AT_WENO_INTERPOLATE &&
+                         atk_tile_fused_supported(c->pb.pde, c->pb.order, c->pb.pe_size, c->pb.rk, L.q) &&
+                         (!is_weno(c->pb.pde) || L.wpp == 1 || L.Tw >= L.S * L.H);
     const bool cluster_ok = c->cluster_c > 0 && !c->arrival && c->withhold_pe < 0;
     bool persist = c->path == AT_PATH_PERSISTENT || (c->path == AT_PATH_AUTO && can_persist);
     // advection-diffusion beyond one thread-block cluster: the step-fused
@@ -567,7 +570,8 @@ int at_step(at_ctx* c, int64_t nsteps)
     if (c->path == AT_PATH_FUSED || (c->path == AT_PATH_AUTO && !persist && !c->arrival && fused_ok)) {
         if (!fused_ok && !tile_ok)
             return fail(AT_EINVAL, "the fused path takes advection-diffusion with PEs of 32, 64, 128 or 256 points, "
-                                   "or the reacting flow in flux form, with at least stages x halo points per PE");
+                                   "the reacting flow in flux form or a WENO PDE in the reconstruction form, with at "
+                                   "least stages x halo points per PE");
         if (c->arrival) return fail(AT_EINVAL, "delays by arrival need the persistent path");
         c->last_path = AT_PATH_FUSED;
         c->base.trace = c->trace;

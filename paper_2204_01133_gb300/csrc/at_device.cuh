@@ -395,6 +395,44 @@ struct Phys<BURGERS> {
 };
 
 // ---------------------------------------------------------------------------
+// WENO5-JS reconstruction at the right edge of f[2] from f[0..4]
+// (candidates of Eq. atRecon at k = 0, ideal weights {1/10, 3/5, 3/10},
+// indicators of Eq. betaS, weights of Eq. omg with power 2), arranged for
+// few FP64 instructions without changing the mathematics:
+//  * with the second differences s_i (centred on f[i+1]) and the first
+//    differences r_0 = f0 - 4 f1 + 3 f2, r_1 = f1 - f3, r_2 = 3 f2 - 4 f3 + f4,
+//    beta_i = (13 s_i^2 + 3 r_i^2) / 12, so D_i = 4 (eps + beta_i) =
+//    (13/3) s_i^2 + r_i^2 + 4 eps; the weights omega_i = alpha_i / sum alpha
+//    do not change when every eps + beta_i is scaled by the same 4;
+//  * the candidates differ from the middle one by third differences,
+//    p_0 - p_1 = (s_0 - s_1) / 3 and p_2 - p_1 = (s_1 - s_2) / 6, so
+//    sum omega_i p_i = p_1 + omega_0 (p_0 - p_1) + omega_2 (p_2 - p_1);
+//  * alpha_i ~ gamma_i / D_i^2 times the common factor D_0^2 D_1^2 D_2^2, and
+//    numerator and denominator scaled by 60:
+//      num = E_1 (2 E_2 (s_0 - s_1) + 3 E_0 (s_1 - s_2)),
+//      den = E_1 (6 E_2 + 18 E_0) + 36 E_0 E_2,  E_i = D_i^2,
+//    with one reciprocal.
+// eps4 = 4 eps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double weno5(double f0, double f1, double f2, double f3, double f4, double eps4)
+{
+    const double s0 = fma(-2.0, f1, f0) + f2;
+    const double s1 = fma(-2.0, f2, f1) + f3;
+    const double s2 = fma(-2.0, f3, f2) + f4;
+    const double r0 = fma(2.0, f2 - f1, s0);  // f0 - 4 f1 + 3 f2
+    const double r1 = f1 - f3;
+    const double r2 = fma(2.0, f2 - f3, s2);  // 3 f2 - 4 f3 + f4
+    const double d0 = fma((13.0 / 3.0) * s0, s0, fma(r0, r0, eps4));
+    const double d1 = fma((13.0 / 3.0) * s1, s1, fma(r1, r1, eps4));
+    const double d2 = fma((13.0 / 3.0) * s2, s2, fma(r2, r2, eps4));
+    const double e0 = d0 * d0, e1 = d1 * d1, e2 = d2 * d2;
+    const double num = e1 * fma(2.0 * e2, s0 - s1, (3.0 * e0) * (s1 - s2));
+    const double den = fma(e1, fma(6.0, e2, 18.0 * e0), 36.0 * (e0 * e2));
+    const double p1 = fma(-1.0 / 6.0, f1, fma(5.0 / 6.0, f2, (1.0 / 3.0) * f3));  // (-f1 + 5 f2 + 2 f3) / 6
+    return fma(num, at_rcp3(den), p1);
+}
+
+// ---------------------------------------------------------------------------
 // The RK update of the step-fused kernels, stage by stage: the next stage
 // argument (u^{n+1} after the last stage) from K, the stage argument x and
 // u^n, with the formulas and operation order of the per-stage kernels'

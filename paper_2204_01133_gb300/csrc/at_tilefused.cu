@@ -1,5 +1,5 @@
-// at_tilefused.cu -- the step-fused path for the reacting flow: all S stages
-// of an RK step in one launch.
+// at_tilefused.cu -- the step-fused path for the reacting flow and the WENO
+// PDEs (the detonation): all S stages of an RK step in one launch.
 //
 // A CTA holds a tile of W consecutive PEs and, on each side, a strip of the
 // D = S H points of the neighbouring PE nearest the tile.  Stage s of the
@@ -219,6 +219,247 @@ __global__ void __launch_bounds__(256) tile_fused(const StageArgs a, const doubl
     }
 }
 
+// ---------------------------------------------------------------------------
+// The WENO PDEs (the detonation): a tile is one window of Tw points of a PE
+// (the per-stage kernels' windows), plus strips of D = S H points on each
+// side, which belong to the same PE (the neighbouring window) or, for the
+// first and last window of a PE, to the neighbouring PE.  Points are grouped
+// in rows by PE: row 1 the window's PE over its points in the region, rows 0
+// and 2 the neighbouring PEs' strips when the window touches a PE edge.  A
+// row sees its own points and, beyond a PE edge inside the region, H buffer
+// columns formed with its own delay for that side.  Stage s: the fluxes of
+// the edges around every point where stage s+1 is needed, as the row that
+// owns the point sees them (the two PEs at a PE edge each form their own
+// flux there, as in the per-stage kernels), then the update.
+//
+// Shared memory (doubles), E = Tw + 2 D; row 1 has RC = E + 2 H columns,
+// rows 0 and 2 (strips) RS = D + 2 H; a quantity of row r sits at the row's
+// base with the row's stride:
+//   UN [NV][E], XS [2][NV][E], AC [NV][E] (RK2, RK4 only)
+//   G [ND] per row, SP, ARR, LAM one per row   derived, wave speed,
+//                                             Arrhenius factor, edge speed
+//   REC [NV][2] per row                       reconstructions
+//   HS [2][2][H][2][ND]                       buffer (point, level) items
+// ---------------------------------------------------------------------------
+template <int PDE, int RK>
+__global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const double* __restrict__ uin,
+                                                        double* __restrict__ uout, int64_t n)
+{
+    using P = Phys<PDE>;
+    constexpr int NV = P::NV, ND = P::ND;
+    constexpr int H = 3;
+    constexpr int S = RkS<RK>::S;
+    constexpr int D = S * H;
+    const int B = a.B, Tw = a.Tw;
+    const int E = Tw + 2 * D, RC = E + 2 * H, RS = D + 2 * H, RT = RC + 2 * RS;
+    constexpr bool has_acc = RK != RK3TVD;
+    const int64_t PP = a.P;
+    const int64_t win = blockIdx.x;
+    const int64_t pe = a.wpp == 1 ? win : win / a.wpp;
+    const int chunk = (int)(win - pe * a.wpp);
+    const int64_t t0 = pe * B + (int64_t)chunk * Tw;       // first point of the window
+    const bool left_edge = chunk == 0, right_edge = chunk == a.wpp - 1;
+    const int64_t pl = pe == 0 ? PP - 1 : pe - 1, pr = pe == PP - 1 ? 0 : pe + 1;
+    const int nw = (a.mode == AT) ? a.q + 1 : 1;
+    // rows: own extended range [lo_r, hi_r) and PE
+    const int lo1 = left_edge ? D : 0, hi1 = right_edge ? D + Tw : E;
+    extern __shared__ double sm[];
+    double* UN = sm;
+    double* XS = UN + NV * E;
+    double* AC = XS + 2 * NV * E;            // (not there for RK3)
+    double* G = AC + (has_acc ? NV * E : 0);
+    double* SP = G + ND * RT;
+    double* ARR = SP + RT;
+    double* LAM = ARR + RT;
+    double* REC = LAM + RT;
+    double* HS = REC + NV * 2 * RT;
+    __shared__ int s_k[4];  // [boundary 0 (left), 1 (right)][0: outer row's side, 1: the window's side]
+    auto row_of = [&](int i) -> int { return i < lo1 ? 0 : (i < hi1 ? 1 : 2); };
+    auto row_lo = [&](int r) -> int { return r == 0 ? 0 : (r == 1 ? lo1 : hi1); };
+    // column of extended point i in its row
+    auto col_of = [&](int i) -> int { return H + i - row_lo(row_of(i)); };
+    // a row's stride and the offset of its first column in a one-per-row array
+    auto rstride = [&](int r) -> int { return r == 1 ? RC : RS; };
+    auto roff = [&](int r) -> int { return r == 0 ? 0 : (r == 1 ? RS : RS + RC); };
+    // a per-row array of m quantities: row r's quantity d at column c is
+    // base[m * roff(r) + d * rstride(r) + c]
+
+    for (int it = threadIdx.x; it < NV * E; it += blockDim.x) {
+        const int v = it / E, i = it - v * E;
+        int64_t g = t0 - D + i;
+        if (g < 0) g += a.N;
+        if (g >= a.N) g -= a.N;
+        const double x = __ldcg(uin + v * a.N + g);
+        UN[v * E + i] = x;
+        XS[v * E + i] = x;
+        if (has_acc) AC[v * E + i] = 0.0;
+    }
+    __syncthreads();
+
+    for (int s = 0; s < S; ++s) {
+        const double* X = XS + (s & 1) * NV * E;
+        double* Xn = XS + ((s + 1) & 1) * NV * E;
+        const int lo = s * H, hi = E - s * H;
+        // the delays at the PE edges inside the region: at the left edge the
+        // left PE's right side and the window PE's left side, at the right
+        // edge the window PE's right side and the right PE's left side
+        if (threadIdx.x < 4) {
+            const int b = threadIdx.x >> 1, w = threadIdx.x & 1;
+            if (b == 0 ? left_edge : right_edge) {
+                const int64_t q = w == 1 ? pe : (b == 0 ? pl : pr);
+                const int side = b == 0 ? (w == 1 ? 0 : 1) : (w == 1 ? 1 : 0);
+                const int k = keff_at(a, n, s, q, side);
+                s_k[threadIdx.x] = k;
+                if (w == 1) log_delay(a, n, s, pe, side, k);
+            }
+        }
+        // own points where X is known: derived quantities, wave speed, Arrhenius factor
+        for (int i = threadIdx.x + lo; i < hi; i += blockDim.x) {
+            const int r = row_of(i), c = col_of(i);
+            double Q[NV], g[ND], sp, arr;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Q[v] = X[v * E + i];
+            P::template derive_weno<PDE == EULER>(a, Q, g, sp, arr);
+            double* Gr = G + ND * roff(r);
+#pragma unroll
+            for (int d = 0; d < ND; ++d) Gr[d * rstride(r) + c] = g[d];
+            SP[roff(r) + c] = sp;
+            if constexpr (PDE == EULER) ARR[roff(r) + c] = arr;
+        }
+        __syncthreads();
+        // buffer (point, level) items at the PE edges of the region
+        const int nitems = 2 * 2 * H * nw;
+        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int l = it % nw, h = (it / nw) % H, w = (it / (nw * H)) & 1, b = it / (nw * H * 2);
+            if (!(b == 0 ? left_edge : right_edge)) continue;
+            const int k = s_k[b * 2 + w];
+            // the row whose buffer this is, its side, and the facing row's PE
+            // and edge point: at the left edge the left row's right buffer
+            // (w = 0) faces the window's first points, the window's left
+            // buffer (w = 1) faces the left PE's last points; mirrored at the right edge
+            const int64_t nb = b == 0 ? (w == 0 ? pe : pl) : (w == 0 ? pe : pr);
+            const int nside = b == 0 ? (w == 0 ? 0 : 1) : (w == 0 ? 1 : 0);  // the facing window's side
+            // extended index of the facing point (level n), in increasing x
+            const int fi = b == 0 ? (w == 0 ? D + h : D - H + h) : (w == 0 ? D + Tw - H + h : D + Tw + h);
+            double g[ND];
+            double sp = 0.0, unused;
+            if ((a.wnz[k] >> l) & 1) {
+                double Q[NV];
+                if (k + l == 0) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) Q[v] = X[v * E + fi];
+                } else {
+                    const int64_t base = ring_index(a, n - k - l, s, nb, nside, h, 0);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) Q[v] = __ldcg(a.ring + base + v);
+                }
+                if (l == 0) {
+                    P::template derive_weno<false>(a, Q, g, sp, unused);  // the speed at level n-k
+                } else {
+                    P::derive(a, Q, g);
+                }
+            } else {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) g[d] = 0.0;
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d) HS[it * ND + d] = g[d];
+            if (l == 0) {
+                // the buffer column: the row on the other side of the PE edge from the facing point
+                const int r = b == 0 ? (w == 0 ? 0 : 1) : (w == 0 ? 2 : 1);
+                const int rlen = (r == 0 ? lo1 : (r == 1 ? hi1 - lo1 : E - hi1));
+                const int c = (b == 0 ? (w == 0 ? H + rlen + h : h) : (w == 0 ? h : H + rlen + h));
+                if ((a.wnz[k] & 1)) SP[roff(r) + c] = sp;
+            }
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < 2 * 2 * H * ND; it += blockDim.x) {
+            const int d = it % ND, h = (it / ND) % H, w = (it / (ND * H)) & 1, b = it / (ND * H * 2);
+            if (!(b == 0 ? left_edge : right_edge)) continue;
+            const int k = s_k[b * 2 + w];
+            const int base = ((b * 2 + w) * H + h) * nw;
+            double acc = ((a.mode == AT) ? a.w[k][0] : 1.0) * HS[base * ND + d];
+            for (int l = 1; l < nw; ++l) acc = fma(a.w[k][l], HS[(base + l) * ND + d], acc);
+            const int r = b == 0 ? (w == 0 ? 0 : 1) : (w == 0 ? 2 : 1);
+            const int rlen = (r == 0 ? lo1 : (r == 1 ? hi1 - lo1 : E - hi1));
+            const int c = (b == 0 ? (w == 0 ? H + rlen + h : h) : (w == 0 ? h : H + rlen + h));
+            G[ND * roff(r) + d * rstride(r) + c] = acc;
+        }
+        __syncthreads();
+        // edges: for each row, the edges around its points in the update range
+        const bool last = s == S - 1;
+        const int klo = last ? D : (s + 1) * H, khi = last ? D + Tw : E - (s + 1) * H;
+        int ka[3], kb[3], ne[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int rlo = row_lo(r), rhi = r == 0 ? lo1 : (r == 1 ? hi1 : E);
+            ka[r] = rlo > klo ? rlo : klo;
+            kb[r] = rhi < khi ? rhi : khi;
+            ne[r] = kb[r] > ka[r] ? kb[r] - ka[r] + 1 : 0;  // edge t sits left of point ka + t
+        }
+        for (int t = threadIdx.x; t < ne[0] + ne[1] + ne[2]; t += blockDim.x) {
+            const int r = t < ne[0] ? 0 : (t < ne[0] + ne[1] ? 1 : 2);
+            const int e = t - (r == 0 ? 0 : (r == 1 ? ne[0] : ne[0] + ne[1]));
+            const int c = H + ka[r] + e - row_lo(r);  // column of the point right of the edge
+            LAM[roff(r) + c] = 0.5 * fmax(SP[roff(r) + c - 1], SP[roff(r) + c]);
+        }
+        __syncthreads();
+        const double eps4 = 4.0 * ((PDE == EULER) ? a.prm[4] : a.prm[1]);
+        const int nrec = NV * 2 * (ne[0] + ne[1] + ne[2]);
+        for (int it = threadIdx.x; it < nrec; it += blockDim.x) {
+            const int t = it % (ne[0] + ne[1] + ne[2]);
+            const int rv = it / (ne[0] + ne[1] + ne[2]);  // (variable, sign)
+            const int v = rv >> 1, sg = rv & 1;
+            const int r = t < ne[0] ? 0 : (t < ne[0] + ne[1] ? 1 : 2);
+            const int e = t - (r == 0 ? 0 : (r == 1 ? ne[0] : ne[0] + ne[1]));
+            const int c = H + ka[r] + e - row_lo(r);
+            const double hl = LAM[roff(r) + c];
+            const double* Cr = G + ND * roff(r) + v * rstride(r);
+            const double* Qr = G + ND * roff(r) + (NV + v) * rstride(r);
+            double rec;
+            if (sg == 0) {  // f+ on columns c-3 .. c+1
+                rec = weno5(fma(hl, Qr[c - 3], Cr[c - 3]), fma(hl, Qr[c - 2], Cr[c - 2]), fma(hl, Qr[c - 1], Cr[c - 1]),
+                            fma(hl, Qr[c], Cr[c]), fma(hl, Qr[c + 1], Cr[c + 1]), eps4);
+            } else {  // f- on columns c+2 .. c-2 (mirrored)
+                rec = weno5(fma(-hl, Qr[c + 2], Cr[c + 2]), fma(-hl, Qr[c + 1], Cr[c + 1]), fma(-hl, Qr[c], Cr[c]),
+                            fma(-hl, Qr[c - 1], Cr[c - 1]), fma(-hl, Qr[c - 2], Cr[c - 2]), eps4);
+            }
+            REC[NV * 2 * roff(r) + (v * 2 + sg) * rstride(r) + c] = rec;
+        }
+        __syncthreads();
+        const double rdx = a.k0;
+        const int nk = khi - klo;
+        for (int it = threadIdx.x; it < NV * nk; it += blockDim.x) {
+            const int v = it / nk, i = klo + (it - v * nk);
+            const int r = row_of(i), c = col_of(i);
+            const double* Rp = REC + NV * 2 * roff(r) + (v * 2) * rstride(r);
+            const double* Rm = Rp + rstride(r);
+            const double Fr = Rp[c + 1] + Rm[c + 1];
+            const double Fl = Rp[c] + Rm[c];
+            double K = (Fl - Fr) * rdx;
+            const double x = X[v * E + i];
+            if constexpr (PDE == EULER) {
+                if (v == 3) K = fma(-a.prm[1] * x, ARR[roff(r) + c], K);
+            }
+            double acc = has_acc ? AC[v * E + i] : 0.0;
+            const double y = fused_update<RK>(a, s, K, x, UN[v * E + i], acc);
+            if (has_acc) AC[v * E + i] = acc;
+            if (i >= D && i < D + Tw) {  // the window: this CTA's points
+                const int jpe = chunk * Tw + (i - D);
+                if (nonfinite(y)) atomicOr(a.status, 1);
+                if (jpe < H || jpe >= B - H) {
+                    const int side = jpe < H ? 0 : 1;
+                    const int h = jpe < H ? jpe : jpe - (B - H);
+                    a.ring[ring_index(a, last ? n + 1 : n, last ? 0 : s + 1, pe, side, h, v)] = y;
+                }
+                if (last) uout[v * a.N + t0 + (i - D)] = y;
+            }
+            if (!last) Xn[v * E + i] = y;
+        }
+        __syncthreads();
+    }
+}
+
 } // namespace atk
 
 // ---------------------------------------------------------------------------
@@ -255,19 +496,49 @@ const void* tile_fn(int pde, int H, int rk)
 }
 } // namespace
 
-// the tile-fused kernel takes the reacting flow in flux form with PEs of at
-// least S H points and tiles that fit shared memory
+size_t tile_weno_smem(int pde, int Tw, int rk)
+{
+    const int NV = pde == atk::EULER ? 4 : 1, ND = pde == atk::EULER ? 8 : 2, H = 3;
+    const size_t D = (size_t)tile_stages(rk) * H, E = (size_t)Tw + 2 * D;
+    const size_t RT = (E + 2 * H) + 2 * (D + 2 * H);  // the three rows' columns
+    const size_t fields = rk == atk::RK3TVD ? 3 : 4;    // u^n, two stage arguments, the accumulator
+    return sizeof(double) * (fields * NV * E + ND * RT + 3 * RT + NV * 2 * RT + 2 * 2 * H * 2 * ND);
+}
+
+// the tile-fused kernels take the reacting flow in flux form (tiles of whole
+// PEs of at least S H points) and the WENO PDEs in the reconstruction form
+// (tiles of one window, PEs of at least S H points)
 bool atk_tile_fused_supported(int pde, int order, int B, int rk, int q)
 {
+    const int S = tile_stages(rk);
+    if (pde == atk::EULER || pde == atk::ADV_WENO || pde == atk::BURGERS) return B >= S * 3;
     if (pde != atk::RNS) return false;
-    const int H = order / 2, S = tile_stages(rk);
+    const int H = order / 2;
     if (B < S * H || B > 1024) return false;
     return tile_smem(pde, B, H, rk, q) <= 200 * 1024;
+}
+
+template <int PDE>
+const void* tile_weno_fn(int rk)
+{
+    if (rk == atk::RK4) return (const void*)atk::tile_fused_weno<PDE, atk::RK4>;
+    if (rk == atk::RK3TVD) return (const void*)atk::tile_fused_weno<PDE, atk::RK3TVD>;
+    return (const void*)atk::tile_fused_weno<PDE, atk::RK2>;
 }
 
 cudaError_t atk_launch_tile_fused(const atk::StageArgs& a, int pde, int order, int64_t n, const double* uin,
                                   double* uout, cudaStream_t st)
 {
+    if (pde == atk::EULER || pde == atk::ADV_WENO || pde == atk::BURGERS) {
+        const void* fn = pde == atk::EULER ? tile_weno_fn<atk::EULER>(a.rk)
+                         : pde == atk::BURGERS ? tile_weno_fn<atk::BURGERS>(a.rk) : tile_weno_fn<atk::ADV_WENO>(a.rk);
+        const size_t smem = tile_weno_smem(pde, a.Tw, a.rk);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        atk::StageArgs args = a;
+        void* params[] = {(void*)&args, (void*)&uin, (void*)&uout, (void*)&n};
+        return cudaLaunchKernel(fn, dim3((unsigned)(a.P * a.wpp)), dim3(256), params, smem, st);
+    }
     const int H = order / 2;
     const void* fn = tile_fn(pde, H, a.rk);
     const size_t smem = tile_smem(pde, a.B, H, a.rk, a.q);

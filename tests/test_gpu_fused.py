@@ -79,7 +79,7 @@ def test_fused_full_size_equals_per_stage():
 
 def test_fused_rejects_what_it_does_not_take():
     from paper_2204_01133_gb300.api import Solver, OPT_ARRIVAL
-    pb, u0 = W.detonation(n=4096, pe_size=512, mode="at", k_max=4, seed=0)
+    pb, u0 = W.adv_weno(n=512, pe_size=32, mode="at", k_max=3, seed=4, dt_coef=2.0, weno="interpolate")
     s = Solver(pb, u0, path="fused")
     with pytest.raises(RuntimeError):
         s.run(1)
@@ -188,3 +188,40 @@ def test_tile_fused_full_size_equals_per_stage_and_the_oracle():
         o = oracle.Oracle(dict(pb, n=5 * B, pe_base=p - 2, pe_total=P), sub)
         assert o.run(6) == 0
         check(pb, b_state[:, p * B:(p + 1) * B], o.state()[:, 2 * B:3 * B], TOL_RUN, "tile-fused PE %d" % p)
+
+
+# --------------------------------------------------------------------------
+# the WENO PDEs (the detonation): a tile is one window of the per-stage
+# kernels plus recomputed strips
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("maker,steps", [
+    ("det-1024", 40), ("det-512", 40), ("det-96", 30), ("det-1024-sync", 30), ("det-512-as-perstep", 30),
+    ("det-one-pe", 30), ("adv", 60), ("burgers", 60)])
+def test_tile_fused_weno_equals_per_stage_bitwise(maker, steps):
+    """Windows of 256 in PEs of 1024 and 512 (inner windows: the strips are
+    the same PE's neighbouring windows), PEs of 96 (one window, both strips
+    from the neighbouring PEs), SYNC, AS with one delay per step, one PE that
+    is its own neighbour; scalar advection and Burgers."""
+    if maker.startswith("det"):
+        B = {"det-1024": 1024, "det-512": 512, "det-96": 96, "det-1024-sync": 1024, "det-512-as-perstep": 512,
+             "det-one-pe": 512}[maker]
+        pes = 1 if maker == "det-one-pe" else 8
+        mode = "sync" if "sync" in maker else ("as" if "-as" in maker else "at")
+        pb, u0 = W.detonation(n=B * pes, pe_size=B, mode=mode, k_max=4, seed=3,
+                              per_stage=0 if "perstep" in maker else 1)
+    elif maker == "adv":
+        pb, u0 = W.adv_weno(n=512, pe_size=32, mode="at", k_max=3, seed=4, dt_coef=2.0)
+    else:
+        pb, u0 = W.burgers(n=1024, pe_size=64, mode="at", k_max=3, seed=6, dt_coef=1.0)
+    a_state, a_del = _run(pb, u0, [steps], "stage")
+    b_state, b_del = _run(pb, u0, [7, 1, steps - 8], "fused")
+    assert np.array_equal(a_state, b_state) and np.array_equal(a_del, b_del)
+
+
+def test_tile_fused_detonation_full_size():
+    """The N = 2^24 detonation: the whole state bit for bit the per-stage
+    path's after 6 steps."""
+    pb, u0 = W.detonation()
+    a_state, a_del = _run(pb, u0, [6], "stage")
+    b_state, b_del = _run(pb, u0, [6], "fused")
+    assert np.array_equal(a_state, b_state) and np.array_equal(a_del, b_del)

@@ -235,11 +235,17 @@ __global__ void __launch_bounds__(256) tile_fused(const StageArgs a, const doubl
 // Shared memory (doubles), E = Tw + 2 D; row 1 has RC = E + 2 H columns,
 // rows 0 and 2 (strips) RS = D + 2 H; a quantity of row r sits at the row's
 // base with the row's stride:
-//   UN [NV][E], XS [2][NV][E], AC [NV][E] (RK2, RK4 only)
 //   G [ND] per row, SP, ARR, LAM one per row   derived, wave speed,
-//                                             Arrhenius factor, edge speed
+//                                             Arrhenius factor, edge speed;
+//                                             the derived quantities NV..2NV-1
+//                                             are the state itself, so the
+//                                             own columns of G hold the stage
+//                                             argument, updated in place
 //   REC [NV][2] per row                       reconstructions
 //   HS [2][2][H][2][ND]                       buffer (point, level) items
+//   AC [NV][E]                                accumulator (RK2, RK4 only)
+// u^n is read from global memory where the update needs it (L2 holds the
+// tile's part, read at the start of the step).
 // ---------------------------------------------------------------------------
 template <int PDE, int RK>
 __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const double* __restrict__ uin,
@@ -264,15 +270,13 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
     // rows: own extended range [lo_r, hi_r) and PE
     const int lo1 = left_edge ? D : 0, hi1 = right_edge ? D + Tw : E;
     extern __shared__ double sm[];
-    double* UN = sm;
-    double* XS = UN + NV * E;
-    double* AC = XS + 2 * NV * E;            // (not there for RK3)
-    double* G = AC + (has_acc ? NV * E : 0);
+    double* G = sm;
     double* SP = G + ND * RT;
     double* ARR = SP + RT;
     double* LAM = ARR + RT;
     double* REC = LAM + RT;
     double* HS = REC + NV * 2 * RT;
+    double* AC = HS + 2 * 2 * H * 2 * ND;  // (not there for RK3)
     __shared__ int s_k[4];  // [boundary 0 (left), 1 (right)][0: outer row's side, 1: the window's side]
     auto row_of = [&](int i) -> int { return i < lo1 ? 0 : (i < hi1 ? 1 : 2); };
     auto row_lo = [&](int r) -> int { return r == 0 ? 0 : (r == 1 ? lo1 : hi1); };
@@ -283,22 +287,24 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
     auto roff = [&](int r) -> int { return r == 0 ? 0 : (r == 1 ? RS : RS + RC); };
     // a per-row array of m quantities: row r's quantity d at column c is
     // base[m * roff(r) + d * rstride(r) + c]
-
-    for (int it = threadIdx.x; it < NV * E; it += blockDim.x) {
-        const int v = it / E, i = it - v * E;
+    // variable v of the stage argument at extended point i (row r, column c)
+    auto xq = [&](int r, int c, int v) -> double& { return G[ND * roff(r) + (NV + v) * rstride(r) + c]; };
+    // its global point
+    auto glob = [&](int i) -> int64_t {
         int64_t g = t0 - D + i;
         if (g < 0) g += a.N;
         if (g >= a.N) g -= a.N;
-        const double x = __ldcg(uin + v * a.N + g);
-        UN[v * E + i] = x;
-        XS[v * E + i] = x;
+        return g;
+    };
+
+    for (int it = threadIdx.x; it < NV * E; it += blockDim.x) {
+        const int v = it / E, i = it - v * E;
+        xq(row_of(i), col_of(i), v) = __ldcg(uin + v * a.N + glob(i));
         if (has_acc) AC[v * E + i] = 0.0;
     }
     __syncthreads();
 
     for (int s = 0; s < S; ++s) {
-        const double* X = XS + (s & 1) * NV * E;
-        double* Xn = XS + ((s + 1) & 1) * NV * E;
         const int lo = s * H, hi = E - s * H;
         // the delays at the PE edges inside the region: at the left edge the
         // left PE's right side and the window PE's left side, at the right
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
             const int r = row_of(i), c = col_of(i);
             double Q[NV], g[ND], sp, arr;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) Q[v] = X[v * E + i];
+            for (int v = 0; v < NV; ++v) Q[v] = xq(r, c, v);
             P::template derive_weno<PDE == EULER>(a, Q, g, sp, arr);
             double* Gr = G + ND * roff(r);
 #pragma unroll
@@ -346,8 +352,9 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
             if ((a.wnz[k] >> l) & 1) {
                 double Q[NV];
                 if (k + l == 0) {
+                    const int fr = row_of(fi), fc = col_of(fi);
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) Q[v] = X[v * E + fi];
+                    for (int v = 0; v < NV; ++v) Q[v] = xq(fr, fc, v);
                 } else {
                     const int64_t base = ring_index(a, n - k - l, s, nb, nside, h, 0);
 #pragma unroll
@@ -437,12 +444,14 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
             const double Fr = Rp[c + 1] + Rm[c + 1];
             const double Fl = Rp[c] + Rm[c];
             double K = (Fl - Fr) * rdx;
-            const double x = X[v * E + i];
+            const double x = xq(r, c, v);
             if constexpr (PDE == EULER) {
                 if (v == 3) K = fma(-a.prm[1] * x, ARR[roff(r) + c], K);
             }
             double acc = has_acc ? AC[v * E + i] : 0.0;
-            const double y = fused_update<RK>(a, s, K, x, UN[v * E + i], acc);
+            // u^n where the update reads it (RK3-TVD's first stage does not)
+            const double un = (RK == RK3TVD && s == 0) ? 0.0 : __ldcg(uin + v * a.N + glob(i));
+            const double y = fused_update<RK>(a, s, K, x, un, acc);
             if (has_acc) AC[v * E + i] = acc;
             if (i >= D && i < D + Tw) {  // the window: this CTA's points
                 const int jpe = chunk * Tw + (i - D);
@@ -454,7 +463,7 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
                 }
                 if (last) uout[v * a.N + t0 + (i - D)] = y;
             }
-            if (!last) Xn[v * E + i] = y;
+            if (!last) xq(r, c, v) = y;  // in place: nothing else reads it in this phase
         }
         __syncthreads();
     }
@@ -501,8 +510,8 @@ size_t tile_weno_smem(int pde, int Tw, int rk)
     const int NV = pde == atk::EULER ? 4 : 1, ND = pde == atk::EULER ? 8 : 2, H = 3;
     const size_t D = (size_t)tile_stages(rk) * H, E = (size_t)Tw + 2 * D;
     const size_t RT = (E + 2 * H) + 2 * (D + 2 * H);  // the three rows' columns
-    const size_t fields = rk == atk::RK3TVD ? 3 : 4;    // u^n, two stage arguments, the accumulator
-    return sizeof(double) * (fields * NV * E + ND * RT + 3 * RT + NV * 2 * RT + 2 * 2 * H * 2 * ND);
+    const size_t acc = rk == atk::RK3TVD ? 0 : NV * E;  // the accumulator
+    return sizeof(double) * (ND * RT + 3 * RT + NV * 2 * RT + 2 * 2 * H * 2 * ND + acc);
 }
 
 // the tile-fused kernels take the reacting flow in flux form (tiles of whole

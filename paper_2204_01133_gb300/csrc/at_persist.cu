@@ -165,7 +165,7 @@ __device__ __forceinline__ void bar_arrive_p(int p, int count)
 // arrives; the workers stop at that stage and the halo warp matches the one
 // arrival it would otherwise have consumed, so every barrier completes.
 template <int PDE, int H>
-__global__ void __launch_bounds__(288) persist_central(const StageArgs a, int64_t level0, int64_t nsteps)
+__global__ void __launch_bounds__(288, 2) persist_central(const StageArgs a, int64_t level0, int64_t nsteps)
 {
     using P = Phys<PDE>;
     constexpr int NV = P::NV, ND = P::ND;

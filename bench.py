@@ -96,34 +96,62 @@ BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4, "rns": 2 * 4 * 8 / 4, "deto
 # N = 2^25 and are scaled by 4 for N = 2^27.
 TRAFFIC_PER_LAUNCH = {
     ("rns-flame-n16384", "persistent"): 2.5390e6,  # state and rings read once, writes stay in L2
-    ("rns-flame-n16777216", "stage"): 1.6610e9 + 1.0863e9,
-    ("detonation-n16777216", "stage"): 2 * (2.7221e8 + 2.2493e8),  # captured at N = 2^23, x2
+    ("rns-flame-n16777216", "stage"): 2 * (8.3059e8 + 5.2038e8),  # captured at N = 2^23, x2
+    ("rns-flame-n8388608", "stage"): 8.3059e8 + 5.2038e8,
+    ("detonation-n8388608", "stage"): 2.7217e8 + 2.2516e8,
+    ("detonation-n16777216", "stage"): 2 * (2.7217e8 + 2.2516e8),  # captured at N = 2^23, x2
     ("advdiff-n134217728", "stage"): 4 * (8.7079e8 + 5.1163e8),
     ("advdiff-n33554432", "stage"): 8.7079e8 + 5.1163e8,
     ("advdiff-n134217728", "fused"): 4 * (4.6984e8 + 3.0259e8),  # one step: u^n, u^{n+1}, the ring
     ("advdiff-n33554432", "fused"): 4.6984e8 + 3.0259e8,
     ("advdiff-n2048", "persistent"): 7.7824e4,  # one-cluster launch: state and ring read once
     ("advdiff-n16384", "fused"): 2.8288e5,  # cooperative fused launch: state and ring read once
-    ("rns-flame-n16777216", "fused"): 2 * (2.6963e8 + 3.1761e8),  # tile-fused step, captured at N = 2^23, x2
-    ("rns-flame-n8388608", "fused"): 2.6963e8 + 3.1761e8,
+    ("rns-flame-n16777216", "fused"): 2 * (2.6861e8 + 3.1843e8),  # tile-fused step, captured at N = 2^23, x2
+    ("rns-flame-n8388608", "fused"): 2.6861e8 + 3.1843e8,
+    ("detonation-n16777216", "fused"): 2 * (2.7658e8 + 2.3381e8),  # tile-fused step, captured at N = 2^23, x2
+    ("detonation-n8388608", "fused"): 2.7658e8 + 2.3381e8,
 }
 
 
-# The kernel sources the captured counts above were taken from: sha256 of
-# csrc/*.cu and *.cuh (sorted by name, concatenated).  When the sources
-# change, the counts may no longer hold: the roofline is then marked stale
-# and its traffic is reported as null until the captures are redone.
-PROFILED_SOURCES_SHA256 = "57eed2dbf2f2ea9a67b10d130ed5870b784963e26f445c30277d208f151e8a79"
+# The kernel sources the captured counts above were taken from, per
+# (workload, path): sha256 of the files that define the timed kernel (sorted
+# by name, concatenated).  When they change, the counts may no longer hold:
+# the roofline is then marked stale and its traffic is reported as null
+# until the capture is redone.  A key without an entry is stale.
+KERNEL_FILES = {
+    "stage": ("at_device.cuh", "at_stage.cu"),
+    "persistent": ("at_cluster.cu", "at_device.cuh", "at_persist.cu"),
+    "fused": ("at_device.cuh", "at_fused.cu", "at_tilefused.cu"),
+}
+_SHA_STAGE = "986aef04754fbf63c943d009cc0fe8b63ad8af1b713b92c2e129392c96abcada"
+_SHA_PERSISTENT = "3ea7c8dbafcc91c42149cef99a7b65015f3ada7ec48dd02593ce93010f1eae4f"
+_SHA_FUSED = "051722a4685ea00382b2aafb89261de7cf1ef86413e01bdcf123a122c62ac19f"
+PROFILED_SHA256 = {
+    ("detonation-n16777216", "stage"): _SHA_STAGE,
+    ("detonation-n8388608", "stage"): _SHA_STAGE,
+    ("rns-flame-n16777216", "stage"): _SHA_STAGE,
+    ("rns-flame-n8388608", "stage"): _SHA_STAGE,
+    ("advdiff-n134217728", "stage"): _SHA_STAGE,
+    ("advdiff-n33554432", "stage"): _SHA_STAGE,
+    ("rns-flame-n16384", "persistent"): _SHA_PERSISTENT,
+    ("advdiff-n2048", "persistent"): _SHA_PERSISTENT,
+    ("advdiff-n134217728", "fused"): _SHA_FUSED,
+    ("advdiff-n33554432", "fused"): _SHA_FUSED,
+    ("advdiff-n16384", "fused"): _SHA_FUSED,
+    ("rns-flame-n16777216", "fused"): _SHA_FUSED,
+    ("rns-flame-n8388608", "fused"): _SHA_FUSED,
+    ("detonation-n16777216", "fused"): _SHA_FUSED,
+    ("detonation-n8388608", "fused"): _SHA_FUSED,
+}
 
 
-def sources_sha256() -> str:
+def sources_sha256(path: str) -> str:
     import hashlib
     d = os.path.join(ROOT, "paper_2204_01133_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
+    for f in sorted(KERNEL_FILES[path]):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()
 
 
@@ -608,7 +636,7 @@ def run_ours(args):
     if rank == 0:
         fl = FLOPS_PER_POINT_STAGE[(kind, path)] * units_per_launch  # per launch
         achieved = fl / (launch_ms * 1e-3) / 1e12
-        stale = sources_sha256() != PROFILED_SOURCES_SHA256
+        stale = PROFILED_SHA256.get((args.workload, path)) != sources_sha256(path)
         alg = ALG_FLOPS_PER_POINT_STAGE[kind] * units_per_launch / (launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / NOMINAL_FP64_TFLOPS,

@@ -68,12 +68,12 @@ NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal, at 2070 M
 FLOPS_PER_POINT_STAGE = {
     ("rns", "stage"): 176.3,         # central6 + AT6, 4 variables (RK4 stage 1 counted)
     ("rns", "persistent"): 177.0,    # same work, all K steps of one launch
-    ("detonation", "stage"): 678.9,  # WENO5 + AT-WENO5, 8 reconstructions per edge (RK3 stage 0)
+    ("detonation", "stage"): 608.8,  # WENO5 + AT-WENO5, 8 reconstructions per edge (RK3 stage 0)
     ("advdiff", "stage"): 13.56,     # 5-tap merged stencil + RK4 update, mean of the 4 stages
     ("advdiff", "persistent"): 13.56,
     ("advdiff", "fused"): 13.56,     # the method's work only (13.65 as executed, with the recomputed edge points)
     ("rns", "fused"): 176.3,         # the method's work only (the tile-fused kernel also recomputes the strips)
-    ("detonation", "fused"): 678.9,  # likewise: the per-stage kernel's count
+    ("detonation", "fused"): 608.8,  # likewise: the per-stage kernel's count
 }
 # The method's own FP64 work per point per stage, by operation count (a
 # divide, square root or exponential counts as one operation): the
@@ -98,8 +98,8 @@ TRAFFIC_PER_LAUNCH = {
     ("rns-flame-n16384", "persistent"): 2.5390e6,  # state and rings read once, writes stay in L2
     ("rns-flame-n16777216", "stage"): 2 * (8.3059e8 + 5.2038e8),  # captured at N = 2^23, x2
     ("rns-flame-n8388608", "stage"): 8.3059e8 + 5.2038e8,
-    ("detonation-n8388608", "stage"): 2.7217e8 + 2.2516e8,
-    ("detonation-n16777216", "stage"): 2 * (2.7217e8 + 2.2516e8),  # captured at N = 2^23, x2
+    ("detonation-n8388608", "stage"): 2.7214e8 + 2.2619e8,
+    ("detonation-n16777216", "stage"): 2 * (2.7214e8 + 2.2619e8),  # captured at N = 2^23, x2
     ("advdiff-n134217728", "stage"): 4 * (8.7079e8 + 5.1163e8),
     ("advdiff-n33554432", "stage"): 8.7079e8 + 5.1163e8,
     ("advdiff-n134217728", "fused"): 4 * (4.6984e8 + 3.0259e8),  # one step: u^n, u^{n+1}, the ring
@@ -108,8 +108,8 @@ TRAFFIC_PER_LAUNCH = {
     ("advdiff-n16384", "fused"): 2.8288e5,  # cooperative fused launch: state and ring read once
     ("rns-flame-n16777216", "fused"): 2 * (2.6861e8 + 3.1843e8),  # tile-fused step, captured at N = 2^23, x2
     ("rns-flame-n8388608", "fused"): 2.6861e8 + 3.1843e8,
-    ("detonation-n16777216", "fused"): 2 * (2.7658e8 + 2.3381e8),  # tile-fused step, captured at N = 2^23, x2
-    ("detonation-n8388608", "fused"): 2.7658e8 + 2.3381e8,
+    ("detonation-n16777216", "fused"): 2 * (2.7652e8 + 2.3236e8),  # tile-fused step, captured at N = 2^23, x2
+    ("detonation-n8388608", "fused"): 2.7652e8 + 2.3236e8,
 }
 
 
@@ -123,9 +123,9 @@ KERNEL_FILES = {
     "persistent": ("at_cluster.cu", "at_device.cuh", "at_persist.cu"),
     "fused": ("at_device.cuh", "at_fused.cu", "at_tilefused.cu"),
 }
-_SHA_STAGE = "986aef04754fbf63c943d009cc0fe8b63ad8af1b713b92c2e129392c96abcada"
-_SHA_PERSISTENT = "3ea7c8dbafcc91c42149cef99a7b65015f3ada7ec48dd02593ce93010f1eae4f"
-_SHA_FUSED = "051722a4685ea00382b2aafb89261de7cf1ef86413e01bdcf123a122c62ac19f"
+_SHA_STAGE = "5281eee5824d0b93942c1c135cae6fbb6f9f402126bf1dc39c8639dc2716ddcd"
+_SHA_PERSISTENT = "ccad8dddf0803ca8735838211ff4c47a1f5cbf0b1c29375aee8abe9410e35e20"
+_SHA_FUSED = "c53fea64703177f5b47e78bd01838f116671379ffaa272717f780b64da53f5b6"
 PROFILED_SHA256 = {
     ("detonation-n16777216", "stage"): _SHA_STAGE,
     ("detonation-n8388608", "stage"): _SHA_STAGE,

@@ -397,14 +397,18 @@ struct Phys<BURGERS> {
 // ---------------------------------------------------------------------------
 // WENO5-JS reconstruction at the right edge of f[2] from f[0..4]
 // (candidates of Eq. atRecon at k = 0, ideal weights {1/10, 3/5, 3/10},
-// indicators of Eq. betaS, weights of Eq. omg with power 2), arranged for
-// few FP64 instructions without changing the mathematics:
-//  * with the second differences s_i (centred on f[i+1]) and the first
-//    differences r_0 = f0 - 4 f1 + 3 f2, r_1 = f1 - f3, r_2 = 3 f2 - 4 f3 + f4,
+// indicators of Eq. betaS, weights of Eq. omg with power 2), taken from the
+// first differences a_k = f[k] - f[k-1] (k = 1..4) and f[2], and arranged
+// for few FP64 instructions without changing the mathematics:
+//  * the second differences s_i (centred on f[i+1]) are s_0 = a_2 - a_1,
+//    s_1 = a_3 - a_2, s_2 = a_4 - a_3, and the first-difference terms of the
+//    indicators r_0 = f0 - 4 f1 + 3 f2 = s_0 + 2 a_2, r_1 = f1 - f3 =
+//    -(a_2 + a_3), r_2 = 3 f2 - 4 f3 + f4 = s_2 - 2 a_3; then
 //    beta_i = (13 s_i^2 + 3 r_i^2) / 12, so D_i = 4 (eps + beta_i) =
 //    (13/3) s_i^2 + r_i^2 + 4 eps; the weights omega_i = alpha_i / sum alpha
 //    do not change when every eps + beta_i is scaled by the same 4;
-//  * the candidates differ from the middle one by third differences,
+//  * the middle candidate p_1 = (-f1 + 5 f2 + 2 f3) / 6 = f2 + a_2/6 + a_3/3,
+//    and the others differ from it by third differences,
 //    p_0 - p_1 = (s_0 - s_1) / 3 and p_2 - p_1 = (s_1 - s_2) / 6, so
 //    sum omega_i p_i = p_1 + omega_0 (p_0 - p_1) + omega_2 (p_2 - p_1);
 //  * alpha_i ~ gamma_i / D_i^2 times the common factor D_0^2 D_1^2 D_2^2, and
@@ -414,22 +418,41 @@ struct Phys<BURGERS> {
 //    with one reciprocal.
 // eps4 = 4 eps.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double weno5(double f0, double f1, double f2, double f3, double f4, double eps4)
+__device__ __forceinline__ double weno5d(double a1, double a2, double a3, double a4, double f2, double eps4)
 {
-    const double s0 = fma(-2.0, f1, f0) + f2;
-    const double s1 = fma(-2.0, f2, f1) + f3;
-    const double s2 = fma(-2.0, f3, f2) + f4;
-    const double r0 = fma(2.0, f2 - f1, s0);  // f0 - 4 f1 + 3 f2
-    const double r1 = f1 - f3;
-    const double r2 = fma(2.0, f2 - f3, s2);  // 3 f2 - 4 f3 + f4
+    const double s0 = a2 - a1;
+    const double s1 = a3 - a2;
+    const double s2 = a4 - a3;
+    const double r0 = fma(2.0, a2, s0);   // f0 - 4 f1 + 3 f2
+    const double r1 = a2 + a3;            // f3 - f1
+    const double r2 = fma(-2.0, a3, s2);  // 3 f2 - 4 f3 + f4
     const double d0 = fma((13.0 / 3.0) * s0, s0, fma(r0, r0, eps4));
     const double d1 = fma((13.0 / 3.0) * s1, s1, fma(r1, r1, eps4));
     const double d2 = fma((13.0 / 3.0) * s2, s2, fma(r2, r2, eps4));
     const double e0 = d0 * d0, e1 = d1 * d1, e2 = d2 * d2;
     const double num = e1 * fma(2.0 * e2, s0 - s1, (3.0 * e0) * (s1 - s2));
     const double den = fma(e1, fma(6.0, e2, 18.0 * e0), 36.0 * (e0 * e2));
-    const double p1 = fma(-1.0 / 6.0, f1, fma(5.0 / 6.0, f2, (1.0 / 3.0) * f3));  // (-f1 + 5 f2 + 2 f3) / 6
+    const double p1 = fma(1.0 / 6.0, a2, fma(1.0 / 3.0, a3, f2));  // (-f1 + 5 f2 + 2 f3) / 6
     return fma(num, at_rcp3(den), p1);
+}
+
+// The LLF-split WENO5 flux at the edge left of column c of a row: the
+// reconstruction of f+ = C + hl Q from columns c-3..c+1 plus that of
+// f- = C - hl Q from columns c+2..c-2 (mirrored), hl half the edge's wave
+// speed (Eq. Csplit).  The split fluxes' first differences are those of C
+// and Q combined, dC(j) +- hl dQ(j) with dC(j) = C[j] - C[j-1], so they come
+// from the rows' own first differences, formed once per column and shared
+// by every edge and both signs; dC(j), dQ(j) are callables returning them.
+template <class DC, class DQ>
+__device__ __forceinline__ double weno_flux(const double* C, const double* Q, DC dC, DQ dQ, int c, double hl,
+                                            double eps4)
+{
+    const double rp = weno5d(fma(hl, dQ(c - 2), dC(c - 2)), fma(hl, dQ(c - 1), dC(c - 1)), fma(hl, dQ(c), dC(c)),
+                             fma(hl, dQ(c + 1), dC(c + 1)), fma(hl, Q[c - 1], C[c - 1]), eps4);
+    // mirrored: a_k of f- is -(dC - hl dQ) at columns c+2, c+1, c, c-1
+    const double rm = weno5d(fma(hl, dQ(c + 2), -dC(c + 2)), fma(hl, dQ(c + 1), -dC(c + 1)),
+                             fma(hl, dQ(c), -dC(c)), fma(hl, dQ(c - 1), -dC(c - 1)), fma(-hl, Q[c], C[c]), eps4);
+    return rp + rm;
 }
 
 // ---------------------------------------------------------------------------

@@ -397,16 +397,18 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
 {
     using P = Phys<PDE>;
     constexpr int NV = P::NV, ND = P::ND;
+    static_assert(ND == 2 * NV, "the WENO PDEs derive C/2 and Q for each variable");
     constexpr int H = 3;
     const int Tw = a.Tw;
     const int W2 = Tw + 2 * H;
     const int E = Tw + 1;  // edges of the window: edge e sits between points e-1 and e
     double* G = sm;
-    double* SP = G + ND * W2;
+    double* DG = G + ND * W2;  // first differences along the window: DG[d W2 + j] = G[d W2 + j] - G[d W2 + j - 1]
+    double* SP = DG + ND * W2;
     double* ARR = SP + W2;
     double* LAM = ARR + W2;
-    double* REC = LAM + E;
-    double* HS = REC + NV * 2 * E;
+    double* FL = LAM + E;      // the flux at every edge, [NV][E]
+    double* HS = FL + NV * E;
     const int64_t pe = a.wpp == 1 ? win : win / a.wpp;  // a 64-bit division only where PEs hold several windows
     const int chunk = (int)(win - pe * a.wpp);
     const int64_t t0 = pe * a.B + (int64_t)chunk * Tw;
@@ -414,26 +416,20 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
     __syncthreads();
     for (int e = threadIdx.x; e < E; e += blockDim.x)
         LAM[e] = 0.5 * fmax(SP[e - 1 + H], SP[e + H]);  // half the edge's local wave speed
+    for (int it = threadIdx.x; it < ND * (W2 - 1); it += blockDim.x) {
+        const int d = it / (W2 - 1);
+        const int j = 1 + it - d * (W2 - 1);
+        DG[d * W2 + j] = G[d * W2 + j] - G[d * W2 + j - 1];
+    }
     __syncthreads();
     const double eps4 = 4.0 * ((PDE == EULER) ? a.prm[4] : a.prm[1]);
-    const int items = NV * 2 * E;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int r = it / E;
-        const int e = it - r * E;
-        const int v = r >> 1;
-        const double hl = LAM[e];
-        const double* C = G + v * W2;
-        const double* Qv = G + (NV + v) * W2;
-        double rec;
-        if ((r & 1) == 0) {  // f+ = C/2 + (lam/2) Q on points e-3..e+1
-            rec = weno5(fma(hl, Qv[e], C[e]), fma(hl, Qv[e + 1], C[e + 1]), fma(hl, Qv[e + 2], C[e + 2]),
-                        fma(hl, Qv[e + 3], C[e + 3]), fma(hl, Qv[e + 4], C[e + 4]), eps4);
-        } else {  // f- = C/2 - (lam/2) Q on points e+2..e-2 (mirrored)
-            rec = weno5(fma(-hl, Qv[e + 5], C[e + 5]), fma(-hl, Qv[e + 4], C[e + 4]),
-                        fma(-hl, Qv[e + 3], C[e + 3]), fma(-hl, Qv[e + 2], C[e + 2]),
-                        fma(-hl, Qv[e + 1], C[e + 1]), eps4);
-        }
-        REC[r * E + e] = rec;
+    for (int it = threadIdx.x; it < NV * E; it += blockDim.x) {
+        const int v = it / E;
+        const int e = it - v * E;
+        const double* dC = DG + v * W2;
+        const double* dQ = DG + (NV + v) * W2;
+        FL[it] = weno_flux(G + v * W2, G + (NV + v) * W2, [&](int j) { return dC[j]; },
+                           [&](int j) { return dQ[j]; }, e + H, LAM[e], eps4);
     }
     __syncthreads();
     const double rdx = a.k0;  // 1 / dx
@@ -442,9 +438,7 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
         const int jl = it - v * Tw;
         const int64_t j = t0 + jl;
         const int c = jl + H;
-        const double Fr = REC[(2 * v) * E + jl + 1] + REC[(2 * v + 1) * E + jl + 1];
-        const double Fl = REC[(2 * v) * E + jl] + REC[(2 * v + 1) * E + jl];
-        double K = (Fl - Fr) * rdx;
+        double K = (FL[v * E + jl] - FL[v * E + jl + 1]) * rdx;
         const double x = G[(NV + v) * W2 + c];
         if constexpr (PDE == EULER) {
             if (v == 3) K = fma(-a.prm[1] * x, ARR[c], K);  // x = rho Y; ARR from the fill
@@ -454,7 +448,7 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
 }
 
 template <int PDE, int RKS>
-__global__ void __launch_bounds__(256, 5) stage_weno(const StageArgs a)
+__global__ void __launch_bounds__(256, 4) stage_weno(const StageArgs a)
 {
     extern __shared__ double sm[];
     weno_window<PDE, RKS>(a, launch_cx(a), blockIdx.x, sm);
@@ -465,7 +459,7 @@ __global__ void __launch_bounds__(256, 5) stage_weno(const StageArgs a)
 // the right edge of f[2] from f[0..4] by the third-order interpolants
 // u0 = 3/8 f0 - 5/4 f1 + 15/8 f2, u1 = -1/8 f1 + 3/4 f2 + 3/8 f3,
 // u2 = 3/8 f2 + 3/4 f3 - 1/8 f4, ideal weights {1/16, 5/8, 5/16}, the
-// indicators of Eq. betaS and the weights of Eq. omg, arranged as weno5():
+// indicators of Eq. betaS and the weights of Eq. omg, arranged as weno5d():
 // u0 - u1 = 3/8 (s_0 - s_1), u2 - u1 = 1/8 (s_1 - s_2), and with the common
 // factor E_0 E_1 E_2 and a scaling by 128,
 //   num = E_1 (3 E_2 (s_0 - s_1) + 5 E_0 (s_1 - s_2)),
@@ -804,8 +798,10 @@ size_t atk_stage_smem_bytes(int pde, int Tw, int H)
     case atk::ADVDIFF: return sizeof(double) * (W2 + hs * 1);
     case atk::RNS: return sizeof(double) * (8 * W2 + hs * 8);
     case atk::RNS_CHAIN: return sizeof(double) * (6 * W2 + hs * 6);
-    case atk::EULER: return sizeof(double) * (10 * W2 + E + 8 * E + hs * 8);
-    default: return sizeof(double) * (4 * W2 + E + 2 * E + hs * 2);
+    // WENO: G and its first differences (2 ND W2), SP, ARR (2 W2), LAM (E),
+    // the edge fluxes (NV E), HS
+    case atk::EULER: return sizeof(double) * (18 * W2 + E + 4 * E + hs * 8);
+    default: return sizeof(double) * (6 * W2 + E + E + hs * 2);
     }
 }
 
@@ -830,7 +826,10 @@ cudaError_t atk_launch_stage(const atk::StageArgs& a, int pde, int order, cudaSt
     const int64_t windows = a.P * a.wpp;
     const int b1 = atk_stage_block(pde, a.Tw);
     size_t smem1 = atk_stage_smem_bytes(pde, a.Tw, a.H);
-    if (a.weno_interp) smem1 += sizeof(double) * ((pde == atk::EULER ? 8 : 2) + 1) * 2;  // two more edges
+    if (a.weno_interp) {  // G [ND][W2], SP, ARR [W2], LAM [E], REC [NV][2][E], HS with W2 = Tw + 8, E = Tw + 3
+        const size_t nd = pde == atk::EULER ? 8 : 2, nv = nd / 2, W2 = a.Tw + 2 * a.H, E = a.Tw + 3;
+        smem1 = sizeof(double) * (nd * W2 + 2 * W2 + E + 2 * nv * E + (size_t)2 * a.H * (AT_QMAX + 1) * nd);
+    }
     // central stencils on small windows: several windows per CTA (whole PEs
     // only, dividing the window count), so a CTA carries up to 256 threads
     int m = 1;

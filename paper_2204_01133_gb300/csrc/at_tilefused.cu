@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) tile_fused(const StageArgs a, const doubl
 //                                             are the state itself, so the
 //                                             own columns of G hold the stage
 //                                             argument, updated in place
-//   REC [NV][2] per row                       reconstructions
+//   REC [NV] per row                          fluxes at the edges
 //   HS [2][2][H][2][ND]                       buffer (point, level) items
 //   AC [NV][E]                                accumulator (RK2, RK4 only)
 // u^n is read from global memory where the update needs it (L2 holds the
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
     double* ARR = SP + RT;
     double* LAM = ARR + RT;
     double* REC = LAM + RT;
-    double* HS = REC + NV * 2 * RT;
+    double* HS = REC + NV * RT;
     double* AC = HS + 2 * 2 * H * 2 * ND;  // (not there for RK3)
     __shared__ int s_k[4];  // [boundary 0 (left), 1 (right)][0: outer row's side, 1: the window's side]
     auto row_of = [&](int i) -> int { return i < lo1 ? 0 : (i < hi1 ? 1 : 2); };
@@ -412,26 +412,20 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
         }
         __syncthreads();
         const double eps4 = 4.0 * ((PDE == EULER) ? a.prm[4] : a.prm[1]);
-        const int nrec = NV * 2 * (ne[0] + ne[1] + ne[2]);
+        const int nrec = NV * (ne[0] + ne[1] + ne[2]);
         for (int it = threadIdx.x; it < nrec; it += blockDim.x) {
             const int t = it % (ne[0] + ne[1] + ne[2]);
-            const int rv = it / (ne[0] + ne[1] + ne[2]);  // (variable, sign)
-            const int v = rv >> 1, sg = rv & 1;
+            const int v = it / (ne[0] + ne[1] + ne[2]);
             const int r = t < ne[0] ? 0 : (t < ne[0] + ne[1] ? 1 : 2);
             const int e = t - (r == 0 ? 0 : (r == 1 ? ne[0] : ne[0] + ne[1]));
             const int c = H + ka[r] + e - row_lo(r);
-            const double hl = LAM[roff(r) + c];
             const double* Cr = G + ND * roff(r) + v * rstride(r);
             const double* Qr = G + ND * roff(r) + (NV + v) * rstride(r);
-            double rec;
-            if (sg == 0) {  // f+ on columns c-3 .. c+1
-                rec = weno5(fma(hl, Qr[c - 3], Cr[c - 3]), fma(hl, Qr[c - 2], Cr[c - 2]), fma(hl, Qr[c - 1], Cr[c - 1]),
-                            fma(hl, Qr[c], Cr[c]), fma(hl, Qr[c + 1], Cr[c + 1]), eps4);
-            } else {  // f- on columns c+2 .. c-2 (mirrored)
-                rec = weno5(fma(-hl, Qr[c + 2], Cr[c + 2]), fma(-hl, Qr[c + 1], Cr[c + 1]), fma(-hl, Qr[c], Cr[c]),
-                            fma(-hl, Qr[c - 1], Cr[c - 1]), fma(-hl, Qr[c - 2], Cr[c - 2]), eps4);
-            }
-            REC[NV * 2 * roff(r) + (v * 2 + sg) * rstride(r) + c] = rec;
+            // the rows' first differences formed where they are used: the same
+            // operations, so the same values, as the per-stage kernels' stored ones
+            REC[NV * roff(r) + v * rstride(r) + c] =
+                weno_flux(Cr, Qr, [&](int j) { return Cr[j] - Cr[j - 1]; }, [&](int j) { return Qr[j] - Qr[j - 1]; }, c,
+                          LAM[roff(r) + c], eps4);
         }
         __syncthreads();
         const double rdx = a.k0;
@@ -439,11 +433,8 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
         for (int it = threadIdx.x; it < NV * nk; it += blockDim.x) {
             const int v = it / nk, i = klo + (it - v * nk);
             const int r = row_of(i), c = col_of(i);
-            const double* Rp = REC + NV * 2 * roff(r) + (v * 2) * rstride(r);
-            const double* Rm = Rp + rstride(r);
-            const double Fr = Rp[c + 1] + Rm[c + 1];
-            const double Fl = Rp[c] + Rm[c];
-            double K = (Fl - Fr) * rdx;
+            const double* F = REC + NV * roff(r) + v * rstride(r);
+            double K = (F[c] - F[c + 1]) * rdx;
             const double x = xq(r, c, v);
             if constexpr (PDE == EULER) {
                 if (v == 3) K = fma(-a.prm[1] * x, ARR[roff(r) + c], K);
@@ -511,7 +502,7 @@ size_t tile_weno_smem(int pde, int Tw, int rk)
     const size_t D = (size_t)tile_stages(rk) * H, E = (size_t)Tw + 2 * D;
     const size_t RT = (E + 2 * H) + 2 * (D + 2 * H);  // the three rows' columns
     const size_t acc = rk == atk::RK3TVD ? 0 : NV * E;  // the accumulator
-    return sizeof(double) * (ND * RT + 3 * RT + NV * 2 * RT + 2 * 2 * H * 2 * ND + acc);
+    return sizeof(double) * (ND * RT + 3 * RT + NV * RT + 2 * 2 * H * 2 * ND + acc);
 }
 
 // the tile-fused kernels take the reacting flow in flux form (tiles of whole

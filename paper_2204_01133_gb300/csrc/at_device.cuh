@@ -139,29 +139,29 @@ __device__ __forceinline__ int keff(const StageArgs& a, int64_t pe, int side)
 }
 
 // exp(x) by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989)
-// with 64 table entries: x = (64 M + j) ln2/64 + r, |r| <= ln2/128, and
-// exp(x) = 2^M 2^(j/64) (1 + expm1(r)), expm1(r) by its Taylor polynomial of
-// degree 5 (the first omitted term is below 4e-17).  The product with 2^M is
-// an integer add to the exponent field, exact while the result is normal,
-// which the fast path |x| < 512 guarantees (tested on the high word with
-// integer instructions); every other x (and Inf, NaN) goes to exp().  About
-// ten FP64 instructions; within 2 ulp of the correctly rounded value.
+// with 256 table entries: x = (256 M + j) ln2/256 + r, |r| <= ln2/512, and
+// exp(x) = 2^M 2^(j/256) (1 + expm1(r)), expm1(r) by its Taylor polynomial of
+// degree 4 (the first omitted term, r^5/120, is below 4e-17).  The product
+// with 2^M is an integer add to the exponent field, exact while the result is
+// normal, which the fast path |x| < 512 guarantees (tested on the high word
+// with integer instructions); every other x (and Inf, NaN) goes to exp().
+// Nine FP64 instructions; within 2 ulp of the correctly rounded value.
 __device__ __forceinline__ double at_exp(double x)
 {
+    static_assert(AT_EXP_N == 256, "the table has 256 entries");
     if ((__double2hiint(x) & 0x7fffffff) >= 0x40800000) return exp(x);
-    const double shift = 0x1.8p52;                 // round to integer, result in the low word
+    const double shift = 0x1.8p52;                  // round to integer, result in the low word
     const double t = fma(x, AT_EXP_INV_L, shift);
-    const int n = __double2loint(t);               // 64 M + j
+    const int n = __double2loint(t);                // 256 M + j
     const double nf = t - shift;
     double r = fma(-nf, AT_EXP_L_HI, x);
     r = fma(-nf, AT_EXP_L_LO, r);
-    double c = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-    c = fma(c, r, 1.0 / 6.0);
+    double c = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     c = fma(c, r, 0.5);
-    const double em1 = fma(c, r * r, r);           // expm1(r)
-    const double tj = __ldg(&at_exp_tab[n & 63]);  // 2^(j/64)
+    const double em1 = fma(c, r * r, r);            // expm1(r)
+    const double tj = __ldg(&at_exp_tab[n & 255]);  // 2^(j/256)
     const double e = fma(tj, em1, tj);
-    return __hiloint2double(__double2hiint(e) + ((n >> 6) << 20), __double2loint(e));
+    return __hiloint2double(__double2hiint(e) + ((n >> 8) << 20), __double2loint(e));
 }
 
 // 1/x by two Newton-Raphson steps r <- r + r (1 - x r) from the hardware's
@@ -170,7 +170,9 @@ __device__ __forceinline__ double at_exp(double x)
 // normal, finite, nonzero x the kernels divide by (densities, pressures,
 // temperatures, WENO weight sums).  Zero, Inf or subnormal x give Inf or
 // NaN, which the non-finite check reports.  Five FP64-pipe instructions, about
-// half of an IEEE division.
+// half of an IEEE division.  The kernels use at_rcp3 below (one instruction
+// fewer); this form is exported by the probe library beside it for the
+// reciprocal tests.
 __device__ __forceinline__ double at_rcp(double x)
 {
     double r;
@@ -186,8 +188,9 @@ __device__ __forceinline__ double at_rcp(double x)
 // relative error of r (Householder's method of order 3, e.g. Householder,
 // "The Numerical Treatment of a Single Nonlinear Equation", 1970), one FP64
 // instruction fewer than at_rcp's two quadratic steps, within about an ulp
-// of 1/x for normal, finite, nonzero x.  Used where a reciprocal serves
-// only one product (the WENO weight normalisation).
+// of 1/x for normal, finite, nonzero x (both are tested against 1/x).  The
+// kernels' reciprocals (densities, temperatures, pressures, WENO weight
+// sums) all use this one.
 __device__ __forceinline__ double at_rcp3(double x)
 {
     double r;
@@ -261,7 +264,7 @@ struct Phys<RNS> {
     __device__ static void derive(const StageArgs& a, const double* Q, double* g)
     {
         const double gm1 = a.prm[0] - 1.0, qc = a.prm[6];
-        const double rinv = at_rcp(Q[0]);
+        const double rinv = at_rcp3(Q[0]);
         const double u = Q[1] * rinv;
         const double p = gm1 * (Q[2] - fma(0.5 * Q[1], u, qc * Q[3]));
         const double T = p * rinv;
@@ -279,7 +282,7 @@ struct Phys<RNS> {
     __device__ static double temperature(const StageArgs& a, const double* Q)
     {
         const double gm1 = a.prm[0] - 1.0, qc = a.prm[6];
-        const double rinv = at_rcp(Q[0]);
+        const double rinv = at_rcp3(Q[0]);
         const double u = Q[1] * rinv;
         const double p = gm1 * (Q[2] - fma(0.5 * Q[1], u, qc * Q[3]));
         return p * rinv;
@@ -295,7 +298,7 @@ struct Phys<RNS_CHAIN> {
     __device__ static void derive(const StageArgs& a, const double* Q, double* g)
     {
         const double gm1 = a.prm[0] - 1.0, qc = a.prm[6];
-        const double rinv = at_rcp(Q[0]);
+        const double rinv = at_rcp3(Q[0]);
         const double u = Q[1] * rinv;
         const double p = gm1 * (Q[2] - fma(0.5 * Q[1], u, qc * Q[3]));
         g[0] = Q[0];
@@ -318,7 +321,7 @@ struct Phys<EULER> {
     }
     __device__ static void derive(const StageArgs& a, const double* Q, double* g)
     {
-        const double u = Q[1] * at_rcp(Q[0]);
+        const double u = Q[1] * at_rcp3(Q[0]);
         const double p = pressure(a, Q, u);
         g[0] = 0.5 * Q[1];
         g[1] = 0.5 * fma(Q[1], u, p);
@@ -331,7 +334,7 @@ struct Phys<EULER> {
     }
     __device__ static double speed(const StageArgs& a, const double* Q)
     {
-        const double rinv = at_rcp(Q[0]);
+        const double rinv = at_rcp3(Q[0]);
         const double u = Q[1] * rinv;
         const double p = pressure(a, Q, u);
         return fabs(u) + sqrt(a.prm[0] * p * rinv);
@@ -342,7 +345,7 @@ struct Phys<EULER> {
     template <bool ARR>
     __device__ static void derive_weno(const StageArgs& a, const double* Q, double* g, double& sp, double& arr)
     {
-        const double rinv = at_rcp(Q[0]);
+        const double rinv = at_rcp3(Q[0]);
         const double u = Q[1] * rinv;
         const double p = pressure(a, Q, u);
         g[0] = 0.5 * Q[1];
@@ -354,7 +357,7 @@ struct Phys<EULER> {
         g[6] = Q[2];
         g[7] = Q[3];
         sp = fabs(u) + sqrt(a.prm[0] * p * rinv);
-        if constexpr (ARR) arr = at_exp(-a.prm[2] * Q[0] * at_rcp(p));
+        if constexpr (ARR) arr = at_exp(-a.prm[2] * Q[0] * at_rcp3(p));
     }
 };
 

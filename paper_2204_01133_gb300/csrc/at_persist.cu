@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(288, 2) persist_central(const StageArgs a, int
                     P::derive(a, Q, g);
 #pragma unroll
                     for (int d = 0; d < ND; ++d) G[d * W2 + H + it] = g[d];
-                    if constexpr (PDE == RNS) E[it] = at_exp(-a.prm[5] * at_rcp(g[7]));  // g[7] = T
+                    if constexpr (PDE == RNS) E[it] = at_exp(-a.prm[5] * at_rcp3(g[7]));  // g[7] = T
                 }
             }
             bar_sync_p<1>(p, nall);  // own derived quantities and stage t's halo in G[p]

@@ -241,7 +241,7 @@ __device__ __forceinline__ void chain_point(const StageArgs& a, const Cx& cx, co
     K[1] = fma(m[0] * u, u, fma(2.0 * ru, m[1], fma(a.k0, uxx, m[2])));
     K[2] = fma(m[1], rE + p, fma(u, m[3] + m[2], fma(a.k0, fma(m[1], m[1], u * uxx), fma(a.k2, Txx, a.prm[6] * a.k3 * Yxx))));
     const double x3 = cx.X[3 * a.N + j];
-    K[3] = fma(m[0] * u, Y, fma(rho * m[1], Y, fma(ru, m[4], fma(a.k3, Yxx, -a.prm[4] * x3 * at_exp(-a.prm[5] * at_rcp(T))))));
+    K[3] = fma(m[0] * u, Y, fma(rho * m[1], Y, fma(ru, m[4], fma(a.k3, Yxx, -a.prm[4] * x3 * at_exp(-a.prm[5] * at_rcp3(T))))));
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const double x = v == 3 ? x3 : cx.X[v * a.N + j];
@@ -309,7 +309,7 @@ __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx,
 #pragma unroll
                 for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[c + o], K);
             }
-            if (v == 3) K = fma(-a.prm[4] * x, at_exp(-a.prm[5] * at_rcp(G[7 * W2 + c])), K);
+            if (v == 3) K = fma(-a.prm[4] * x, at_exp(-a.prm[5] * at_rcp3(G[7 * W2 + c])), K);
         }
         rk_update<RKS>(a, cx, v, j, chunk * a.Tw + jl, pe, K, x, in);
     }
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(128) ring_recompute(const StageArgs a, const d
 #pragma unroll
                         for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[lane + o], K);
                     }
-                    if (v == 3) K = fma(-a.prm[4] * x[v], at_exp(-a.prm[5] * at_rcp(G[7 * W + lane])), K);
+                    if (v == 3) K = fma(-a.prm[4] * x[v], at_exp(-a.prm[5] * at_rcp3(G[7 * W + lane])), K);
                 }
                 // the stage-(r+1) argument as rk_update forms it
                 if (RK == RK4) y[v] = fma(r == 2 ? a.dt : a.hdt, K, un[v]);

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256) tile_fused(const StageArgs a, const doubl
 #pragma unroll
                     for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], Dq[c + o], K);
                 }
-                if (v == 3) K = fma(-a.prm[4] * x, at_exp(-a.prm[5] * at_rcp(Gr[7 * RW + c])), K);
+                if (v == 3) K = fma(-a.prm[4] * x, at_exp(-a.prm[5] * at_rcp3(Gr[7 * RW + c])), K);
             }
             double acc = AC[v * E + i];
             const double y = fused_update<RK>(a, s, K, x, UN[v * E + i], acc);

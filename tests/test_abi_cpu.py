@@ -175,3 +175,22 @@ def test_noalloc_scratch_size_matches_the_binding():
     m = re.search(r"#define\s+AT_NOALLOC_SCRATCH_BYTES\s+\(\(size_t\)(\d+)\s*<<\s*(\d+)\)", open(HEADER).read())
     assert m, "AT_NOALLOC_SCRATCH_BYTES is not of the form ((size_t)A << B)"
     assert int(m.group(1)) << int(m.group(2)) == api.NOALLOC_SCRATCH_BYTES
+
+
+def test_exp_table_is_what_its_generator_writes():
+    """csrc/exp_table.h is generated from the definitions 2^(j/256) and
+    ln 2 / 256 in high-precision decimal arithmetic; the committed file must
+    be exactly the generator's output, and its table must hold 2^(j/256)
+    rounded to double."""
+    import math
+    import subprocess
+    import sys
+    csrc = os.path.join(ROOT, "paper_2204_01133_gb300", "csrc")
+    out = subprocess.run([sys.executable, os.path.join(csrc, "gen_exp_table.py")], capture_output=True, text=True,
+                         check=True).stdout
+    with open(os.path.join(csrc, "exp_table.h")) as f:
+        assert f.read().strip() == out.strip()
+    vals = [float.fromhex(t) for line in out.splitlines() if line.startswith("    0x")
+            for t in line.strip().rstrip(",").split(", ")]
+    assert len(vals) == 256
+    assert all(abs(v - 2.0 ** (j / 256)) <= math.ulp(v) for j, v in enumerate(vals))

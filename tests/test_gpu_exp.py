@@ -1,4 +1,4 @@
-"""The stage kernels' own exponential (Tang's table-driven method, 64
+"""The stage kernels' own exponential (Tang's table-driven method, 256
 entries) and reciprocals (two Newton steps, or one cubic step, from the
 hardware approximation), against the host C library and CUDA, through
 libat_probe.so."""
@@ -34,13 +34,13 @@ def probe():
 
 def _inputs():
     rng = np.random.default_rng(7)
-    ln2_128 = math.log(2.0) / 128.0
-    k = np.arange(-4000, 4001, dtype=np.float64)
+    ln2_512 = math.log(2.0) / 512.0  # half a table step: where the reduction rounds to a tie
+    k = np.arange(-16000, 16001, dtype=np.float64)
     return np.concatenate([
         rng.uniform(-60.0, 0.0, 1 << 20),        # Arrhenius exponents -Ea/T
         rng.uniform(-708.0, 709.0, 1 << 18),     # the whole normal range
         rng.uniform(-1e-3, 1e-3, 1 << 14),
-        k * ln2_128, np.nextafter(k * ln2_128, np.inf), np.nextafter(k * ln2_128, -np.inf),  # reduction ties
+        k * ln2_512, np.nextafter(k * ln2_512, np.inf), np.nextafter(k * ln2_512, -np.inf),  # reduction ties
         [0.0, -0.0, 1e-300, -1e-300, 511.999, -511.999, 512.0, -512.0],
     ])
 

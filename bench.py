@@ -66,14 +66,14 @@ NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal, at 2070 M
 # instruction sequences of exp and the reciprocals, so achieved / peak is the
 # share of the FP64 roof the kernel's own arithmetic uses.
 FLOPS_PER_POINT_STAGE = {
-    ("rns", "stage"): 176.3,         # central6 + AT6, 4 variables (RK4 stage 1 counted)
-    ("rns", "persistent"): 177.0,    # same work, all K steps of one launch
-    ("detonation", "stage"): 608.8,  # WENO5 + AT-WENO5, 8 reconstructions per edge (RK3 stage 0)
+    ("rns", "stage"): 170.3,         # central6 + AT6, 4 variables (RK4 stage 1 counted)
+    ("rns", "persistent"): 170.3,    # same work, all K steps of one launch
+    ("detonation", "stage"): 602.6,  # WENO5 + AT-WENO5, 8 reconstructions per edge (RK3 stage 0)
     ("advdiff", "stage"): 13.56,     # 5-tap merged stencil + RK4 update, mean of the 4 stages
     ("advdiff", "persistent"): 13.56,
     ("advdiff", "fused"): 13.56,     # the method's work only (13.65 as executed, with the recomputed edge points)
-    ("rns", "fused"): 176.3,         # the method's work only (the tile-fused kernel also recomputes the strips)
-    ("detonation", "fused"): 608.8,  # likewise: the per-stage kernel's count
+    ("rns", "fused"): 170.3,         # the method's work only (the tile-fused kernel also recomputes the strips)
+    ("detonation", "fused"): 602.6,  # likewise: the per-stage kernel's count
 }
 # The method's own FP64 work per point per stage, by operation count (a
 # divide, square root or exponential counts as one operation): the
@@ -95,21 +95,21 @@ BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4, "rns": 2 * 4 * 8 / 4, "deto
 # workload and path; the advection-diffusion kernels were captured at
 # N = 2^25 and are scaled by 4 for N = 2^27.
 TRAFFIC_PER_LAUNCH = {
-    ("rns-flame-n16384", "persistent"): 2.5390e6,  # state and rings read once, writes stay in L2
-    ("rns-flame-n16777216", "stage"): 2 * (8.3059e8 + 5.2038e8),  # captured at N = 2^23, x2
-    ("rns-flame-n8388608", "stage"): 8.3059e8 + 5.2038e8,
-    ("detonation-n8388608", "stage"): 2.7214e8 + 2.2619e8,
-    ("detonation-n16777216", "stage"): 2 * (2.7214e8 + 2.2619e8),  # captured at N = 2^23, x2
-    ("advdiff-n134217728", "stage"): 4 * (8.7079e8 + 5.1163e8),
-    ("advdiff-n33554432", "stage"): 8.7079e8 + 5.1163e8,
-    ("advdiff-n134217728", "fused"): 4 * (4.6984e8 + 3.0259e8),  # one step: u^n, u^{n+1}, the ring
-    ("advdiff-n33554432", "fused"): 4.6984e8 + 3.0259e8,
-    ("advdiff-n2048", "persistent"): 7.7824e4,  # one-cluster launch: state and ring read once
-    ("advdiff-n16384", "fused"): 2.8288e5,  # cooperative fused launch: state and ring read once
-    ("rns-flame-n16777216", "fused"): 2 * (2.6861e8 + 3.1843e8),  # tile-fused step, captured at N = 2^23, x2
-    ("rns-flame-n8388608", "fused"): 2.6861e8 + 3.1843e8,
-    ("detonation-n16777216", "fused"): 2 * (2.7652e8 + 2.3236e8),  # tile-fused step, captured at N = 2^23, x2
-    ("detonation-n8388608", "fused"): 2.7652e8 + 2.3236e8,
+    ("rns-flame-n16384", "persistent"): 2.5503e6,  # state and rings read once, writes stay in L2
+    ("rns-flame-n16777216", "stage"): 2 * (8.3056e8 + 5.2100e8),  # captured at N = 2^23, x2
+    ("rns-flame-n8388608", "stage"): 8.3056e8 + 5.2100e8,
+    ("detonation-n8388608", "stage"): 2.7212e8 + 2.2645e8,
+    ("detonation-n16777216", "stage"): 2 * (2.7212e8 + 2.2645e8),  # captured at N = 2^23, x2
+    ("advdiff-n134217728", "stage"): 4 * (8.7099e8 + 5.1159e8),
+    ("advdiff-n33554432", "stage"): 8.7099e8 + 5.1159e8,
+    ("advdiff-n134217728", "fused"): 4 * (4.6988e8 + 3.0230e8),  # one step: u^n, u^{n+1}, the ring
+    ("advdiff-n33554432", "fused"): 4.6988e8 + 3.0230e8,
+    ("advdiff-n2048", "persistent"): 7.8080e4,  # one-cluster launch: state and ring read once
+    ("advdiff-n16384", "fused"): 2.8339e5,  # cooperative fused launch: state and ring read once
+    ("rns-flame-n16777216", "fused"): 2 * (2.6973e8 + 3.1845e8),  # tile-fused step, captured at N = 2^23, x2
+    ("rns-flame-n8388608", "fused"): 2.6973e8 + 3.1845e8,
+    ("detonation-n16777216", "fused"): 2 * (2.7727e8 + 2.3261e8),  # tile-fused step, captured at N = 2^23, x2
+    ("detonation-n8388608", "fused"): 2.7727e8 + 2.3261e8,
 }
 
 
@@ -123,9 +123,9 @@ KERNEL_FILES = {
     "persistent": ("at_cluster.cu", "at_device.cuh", "at_persist.cu"),
     "fused": ("at_device.cuh", "at_fused.cu", "at_tilefused.cu"),
 }
-_SHA_STAGE = "5281eee5824d0b93942c1c135cae6fbb6f9f402126bf1dc39c8639dc2716ddcd"
-_SHA_PERSISTENT = "ccad8dddf0803ca8735838211ff4c47a1f5cbf0b1c29375aee8abe9410e35e20"
-_SHA_FUSED = "c53fea64703177f5b47e78bd01838f116671379ffaa272717f780b64da53f5b6"
+_SHA_STAGE = "9a1326f30de33c3fe605023967c4eb2a6473f34538f076d5546be7e924b12b4f"
+_SHA_PERSISTENT = "d8d9af5f0e1203f1157c6b87b2eda5837ed3941543eca810c6b831d867a1e297"
+_SHA_FUSED = "4f81ecf5ead62774dbcdeee41972e963777e86d5b9d4a45c2e7d542cdaac332c"
 PROFILED_SHA256 = {
     ("detonation-n16777216", "stage"): _SHA_STAGE,
     ("detonation-n8388608", "stage"): _SHA_STAGE,

@@ -1,0 +1,99 @@
+"""Edge cases of the GPU path against the oracle: the smallest PE the
+stencils allow (pe_size = 2H) for every PDE, that PE alone (its own
+neighbour on both sides), the largest single window (a prime PE size of
+1021, one window per PE, the largest shared-memory request of the WENO
+kernel), a zero-step call (state and delay log unchanged, bit for bit, on
+every path) and a negative step count (refused).  The Euler cases use the
+smooth entropy wave, so the plain per-variable bounds (1e-12 after one
+step, 1e-10 after the run) apply."""
+import numpy as np
+import pytest
+
+from paper_2204_01133_gb300 import workloads as W
+from test_gpu_parity import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2204_01133_gb300 import build
+    build.build()
+
+
+def _case(name, pes):
+    if name == "advdiff-order2":
+        return W.advdiff(n=2 * pes, pe_size=2, order=2, mode="at", k_max=3, seed=21, cfl=0.05), 200
+    if name == "advdiff-order6":
+        return W.advdiff(n=6 * pes, pe_size=6, order=6, mode="at", k_max=3, seed=22, cfl=0.01), 200
+    if name == "rns-order6":
+        return W.rns(case="flame", n=6 * pes, pe_size=6, order=6, mode="at", k_max=4, seed=23, dt=0.003), 60
+    if name == "rns-order2-ignition":
+        return W.rns(case="ignition", n=2 * pes, pe_size=2, order=2, mode="at", k_max=2, seed=24, dt=0.003), 60
+    if name == "euler-weno":
+        return W.entropy_wave(n=6 * pes, pe_size=6, mode="at", k_max=2, seed=25), 60
+    return W.adv_weno(n=6 * pes, pe_size=6, mode="at", k_max=2, seed=26), 60
+
+
+CASES = ["advdiff-order2", "advdiff-order6", "rns-order6", "rns-order2-ignition", "euler-weno", "adv-weno"]
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("pes", [1, 40])
+def test_smallest_pe_matches_the_oracle(name, pes):
+    (pb, u0), steps = _case(name, pes)
+    assert pb["pe_size"] == 2 * (3 if pb["pde"] in ("euler", "adv_weno") else pb["order"] // 2)
+    parity(pb, u0, steps, what="%s, %d PE(s) of %d" % (name, pes, pb["pe_size"]))
+
+
+@pytest.mark.parametrize("name", ["advdiff-order6", "rns-order6"])
+def test_smallest_pe_on_the_persistent_path(name):
+    (pb, u0), steps = _case(name, 40)
+    s, _ = parity(pb, u0, steps, path="persistent", what="%s persistent" % name)
+    assert s.stats().path == 2
+
+
+@pytest.mark.parametrize("pes", [1, 3])
+def test_largest_window_matches_the_oracle(pes):
+    """A prime PE size of 1021 has no divisor in [2H, 256]: the PE is one
+    window of 1021 points (about 190 KB of shared memory per CTA)."""
+    pb, u0 = W.entropy_wave(n=1021 * pes, pe_size=1021, mode="at", k_max=3, seed=27)
+    parity(pb, u0, 40, what="entropy wave, %d PE(s) of 1021" % pes)
+
+
+@pytest.mark.parametrize("path,maker", [("stage", "rns"), ("persistent", "rns"), ("fused", "advdiff"),
+                                        ("stage", "detonation"), ("fused", "rns")])
+def test_zero_steps_change_nothing(path, maker):
+    from paper_2204_01133_gb300.api import Solver
+    if maker == "rns":
+        pb, u0 = W.rns(case="flame", n=2048, pe_size=64, mode="at", k_max=4, seed=3, dt=0.003)
+    elif maker == "advdiff":
+        pb, u0 = W.advdiff(n=8192, pe_size=64, mode="at", k_max=3, seed=3, cfl=0.075)
+    else:
+        pb, u0 = W.detonation(n=4096, pe_size=256, mode="at", k_max=4, seed=3)
+    s = Solver(pb, u0, path=path)
+    s.run(5)
+    st, dl = s.read_state(), s.read_delays()
+    s.run(0)
+    assert np.array_equal(s.read_state(), st)
+    assert np.array_equal(s.read_delays(), dl)
+    # and the run continues exactly as one without the empty call
+    r = Solver(pb, u0, path=path)
+    r.run(5)
+    r.run(7)
+    s.run(7)
+    assert np.array_equal(s.read_state(), r.read_state())
+
+
+def test_negative_step_count_is_refused():
+    from paper_2204_01133_gb300 import api
+    pb, u0 = W.advdiff(n=2048, pe_size=64, mode="at", k_max=3, seed=0, cfl=0.075)
+    s = api.Solver(pb, u0)
+    st = s.read_state()
+    with pytest.raises(api.AtError) as ei:
+        s.run(-1)
+    assert ei.value.code == api.AT_EINVAL
+    assert np.array_equal(s.read_state(), st)

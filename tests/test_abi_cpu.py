@@ -98,6 +98,9 @@ def test_workspace_sizing_and_validation(L):
     assert api.workspace_bytes(dict(pb, k_max=6)) > nb
     # invalid descriptions are rejected with 0
     assert api.workspace_bytes(dict(pb, n=2049)) == 0
+    assert api.workspace_bytes(dict(pb, n=0)) == 0            # empty domain
+    assert api.workspace_bytes(dict(pb, pe_size=0)) == 0
+    assert api.workspace_bytes(dict(pb, n=-64)) == 0
     assert api.workspace_bytes(dict(pb, pe_size=3)) == 0      # below 2 x halo width
     assert api.workspace_bytes(dict(pb, k_max=16)) == 0
     assert api.workspace_bytes(dict(pb, order=8)) == 0

@@ -415,9 +415,9 @@ struct Phys<BURGERS> {
 //    p_0 - p_1 = (s_0 - s_1) / 3 and p_2 - p_1 = (s_1 - s_2) / 6, so
 //    sum omega_i p_i = p_1 + omega_0 (p_0 - p_1) + omega_2 (p_2 - p_1);
 //  * alpha_i ~ gamma_i / D_i^2 times the common factor D_0^2 D_1^2 D_2^2, and
-//    numerator and denominator scaled by 60:
-//      num = E_1 (2 E_2 (s_0 - s_1) + 3 E_0 (s_1 - s_2)),
-//      den = E_1 (6 E_2 + 18 E_0) + 36 E_0 E_2,  E_i = D_i^2,
+//    numerator and denominator scaled by 10 (ideal weights 1 : 6 : 3):
+//      num = E_1 (E_2 (s_0 - s_1) / 3 + E_0 (s_1 - s_2) / 2),
+//      den = E_1 (E_2 + 3 E_0) + 6 E_0 E_2,  E_i = D_i^2,
 //    with one reciprocal.
 // eps4 = 4 eps.
 // ---------------------------------------------------------------------------
@@ -433,8 +433,8 @@ __device__ __forceinline__ double weno5d(double a1, double a2, double a3, double
     const double d1 = fma((13.0 / 3.0) * s1, s1, fma(r1, r1, eps4));
     const double d2 = fma((13.0 / 3.0) * s2, s2, fma(r2, r2, eps4));
     const double e0 = d0 * d0, e1 = d1 * d1, e2 = d2 * d2;
-    const double num = e1 * fma(2.0 * e2, s0 - s1, (3.0 * e0) * (s1 - s2));
-    const double den = fma(e1, fma(6.0, e2, 18.0 * e0), 36.0 * (e0 * e2));
+    const double num = e1 * fma(e2, (s0 - s1) * (1.0 / 3.0), e0 * ((s1 - s2) * 0.5));
+    const double den = fma(e1, fma(3.0, e0, e2), 6.0 * (e0 * e2));
     const double p1 = fma(1.0 / 6.0, a2, fma(1.0 / 3.0, a3, f2));  // (-f1 + 5 f2 + 2 f3) / 6
     return fma(num, at_rcp3(den), p1);
 }

@@ -83,7 +83,7 @@ struct Layout {
     int nvar, H, q, S, R;
     int64_t P;
     int Tw, wpp;
-    size_t off_A, off_B, off_acc, off_ring, off_dlog, off_status, off_done, off_gring, off_ext, total;
+    size_t off_A, off_B, off_acc, off_ring, off_dlog, off_status, off_done, off_place, off_gring, off_ext, total;
     size_t ring_elems, gring_elems, ext_elems;
 };
 
@@ -189,6 +189,8 @@ Layout layout(const at_problem* pb, const at_delays* dl)
     off = align256(off + 256);
     L.off_done = off;    // per-PE progress counters of the persistent path
     off = align256(off + sizeof(int64_t) * (size_t)L.P);
+    L.off_place = off;   // the persistent path's SM of every CTA (PE placement)
+    if (L.P <= kPersistMaxPE) off = align256(off + sizeof(int) * (size_t)L.P);
     // the persistent path's ring of derived quantities of the edge windows
     // (central PDEs with few enough PEs to take that path)
     L.gring_elems = 0;
@@ -255,7 +257,9 @@ atk::StageArgs build_args(const at_problem* pb, const at_delays* dl, const Layou
     a.dlog = (uint8_t*)(ws + L.off_dlog);
     a.status = (int*)(ws + L.off_status);
     a.abort_flag = (int*)(ws + L.off_status + sizeof(int));
+    a.place_count = (int*)(ws + L.off_status + 2 * sizeof(int));
     a.done = (int64_t*)(ws + L.off_done);
+    a.place = L.P <= kPersistMaxPE ? (int*)(ws + L.off_place) : nullptr;
     a.gring = L.gring_elems ? (double*)(ws + L.off_gring) : nullptr;
     a.wait_limit = (int64_t)4000000;
     a.withhold_pe = (int64_t)-1;

@@ -49,6 +49,8 @@ struct StageArgs {
     int64_t* done;       // per PE: stages completed, as the index n*S + s + 1 [P]
     double* gring;       // derived quantities of the edge windows [R][S][P][2][H][ND]
     int* abort_flag;     // set by the first wait that runs out
+    int* place;          // per CTA: the SM it runs on, for the PE placement [P]
+    int* place_count;    // CTAs that have written their SM
     int64_t wait_limit;  // polls before a wait gives up (bounded spin)
     int64_t withhold_pe; // fault injection: this PE never publishes (-1: none)
     int slack;           // ring levels beyond k_max + q + 1

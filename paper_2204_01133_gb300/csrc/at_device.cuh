@@ -420,10 +420,12 @@ struct Phys<BURGERS> {
 //    numerator and denominator scaled by 10 (ideal weights 1 : 6 : 3):
 //      num = E_1 (E_2 (s_0 - s_1) / 3 + E_0 (s_1 - s_2) / 2),
 //      den = E_1 (E_2 + 3 E_0) + 6 E_0 E_2,  E_i = D_i^2,
-//    with one reciprocal.
-// eps4 = 4 eps.
+//    so the reconstruction is p_1 + num / den.
+// The parts (num, den, p_1) are returned, so that the two reconstructions of
+// an edge share one reciprocal.  eps4 = 4 eps.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double weno5d(double a1, double a2, double a3, double a4, double f2, double eps4)
+__device__ __forceinline__ void weno5d(double a1, double a2, double a3, double a4, double f2, double eps4,
+                                       double& num, double& den, double& p1)
 {
     const double s0 = a2 - a1;
     const double s1 = a3 - a2;
@@ -435,10 +437,9 @@ __device__ __forceinline__ double weno5d(double a1, double a2, double a3, double
     const double d1 = fma((13.0 / 3.0) * s1, s1, fma(r1, r1, eps4));
     const double d2 = fma((13.0 / 3.0) * s2, s2, fma(r2, r2, eps4));
     const double e0 = d0 * d0, e1 = d1 * d1, e2 = d2 * d2;
-    const double num = e1 * fma(e2, (s0 - s1) * (1.0 / 3.0), e0 * ((s1 - s2) * 0.5));
-    const double den = fma(e1, fma(3.0, e0, e2), 6.0 * (e0 * e2));
-    const double p1 = fma(1.0 / 6.0, a2, fma(1.0 / 3.0, a3, f2));  // (-f1 + 5 f2 + 2 f3) / 6
-    return fma(num, at_rcp3(den), p1);
+    num = e1 * fma(e2, (s0 - s1) * (1.0 / 3.0), e0 * ((s1 - s2) * 0.5));
+    den = fma(e1, fma(3.0, e0, e2), 6.0 * (e0 * e2));
+    p1 = fma(1.0 / 6.0, a2, fma(1.0 / 3.0, a3, f2));  // (-f1 + 5 f2 + 2 f3) / 6
 }
 
 // The LLF-split WENO5 flux at the edge left of column c of a row: the
@@ -448,16 +449,23 @@ __device__ __forceinline__ double weno5d(double a1, double a2, double a3, double
 // and Q combined, dC(j) +- hl dQ(j) with dC(j) = C[j] - C[j-1], so they come
 // from the rows' own first differences, formed once per column and shared
 // by every edge and both signs; dC(j), dQ(j) are callables returning them.
+// The flux p+ + p- + num+ / den+ + num- / den- is formed as
+// p+ + p- + (num+ den- + num- den+) / (den+ den-), one reciprocal for both
+// (den is at least 6 (4 eps)^4 ~ 1.5e-21 with eps = 1e-6 and grows with the
+// fourth power of the differences, so the product stays far inside the
+// double range for the states these PDEs carry).
 template <class DC, class DQ>
 __device__ __forceinline__ double weno_flux(const double* C, const double* Q, DC dC, DQ dQ, int c, double hl,
                                             double eps4)
 {
-    const double rp = weno5d(fma(hl, dQ(c - 2), dC(c - 2)), fma(hl, dQ(c - 1), dC(c - 1)), fma(hl, dQ(c), dC(c)),
-                             fma(hl, dQ(c + 1), dC(c + 1)), fma(hl, Q[c - 1], C[c - 1]), eps4);
+    double np, dp, pp, nm, dm, pm;
+    weno5d(fma(hl, dQ(c - 2), dC(c - 2)), fma(hl, dQ(c - 1), dC(c - 1)), fma(hl, dQ(c), dC(c)),
+           fma(hl, dQ(c + 1), dC(c + 1)), fma(hl, Q[c - 1], C[c - 1]), eps4, np, dp, pp);
     // mirrored: a_k of f- is -(dC - hl dQ) at columns c+2, c+1, c, c-1
-    const double rm = weno5d(fma(hl, dQ(c + 2), -dC(c + 2)), fma(hl, dQ(c + 1), -dC(c + 1)),
-                             fma(hl, dQ(c), -dC(c)), fma(hl, dQ(c - 1), -dC(c - 1)), fma(-hl, Q[c], C[c]), eps4);
-    return rp + rm;
+    weno5d(fma(hl, dQ(c + 2), -dC(c + 2)), fma(hl, dQ(c + 1), -dC(c + 1)), fma(hl, dQ(c), -dC(c)),
+           fma(hl, dQ(c - 1), -dC(c - 1)), fma(-hl, Q[c], C[c]), eps4, nm, dm, pm);
+    // both corrections over one reciprocal
+    return fma(fma(np, dm, nm * dp), at_rcp3(dp * dm), pp + pm);
 }
 
 // ---------------------------------------------------------------------------

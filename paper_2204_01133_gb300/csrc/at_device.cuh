@@ -4,6 +4,8 @@
 // argument block, the Philox4x32-10 delay draw, the temporal extrapolation of
 // halo values from the history ring, and the per-PDE derived quantities.
 #pragma once
+#include <cuda/atomic>
+
 #include <cstdint>
 
 #include "exp_table.h"
@@ -398,6 +400,60 @@ struct Phys<BURGERS> {
         sp = speed(a, Q);
     }
 };
+
+// the SM this thread runs on
+__device__ __forceinline__ int sm_id()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return (int)r;
+}
+
+// The position of this CTA in a cooperative launch whose CTAs hand data to
+// their neighbours (the persistent kernel: one PE per CTA; the multi-step
+// fused kernel: a range of PEs per CTA).  A hand-off between SMs far apart
+// (GB300's two dies) costs more than one between SMs that share a GPC, and
+// the blocks of a launch are spread over the SMs in an order the program
+// does not choose, so positions are dealt out by the SMs the CTAs landed on:
+// every CTA records its SM, meets the others at a one-time bounded barrier
+// (the launch is cooperative, so all CTAs are resident), and takes as its
+// position its rank in (SM, block) order.  Consecutive positions then sit on
+// the same or neighbouring SMs.  The arithmetic does not depend on where it
+// runs, so results are the same bit for bit; a barrier that runs out keeps
+// position = block (status bit 2 and the abort flag stop the run).  The
+// caller resets *a.place_count before the launch.
+__device__ __forceinline__ int64_t place_rank(const StageArgs& a)
+{
+    __shared__ int s_pe;
+    if (threadIdx.x == 0) {
+        int rank = (int)blockIdx.x;
+        if (a.place && a.place_count) {
+            const int me = sm_id();
+            a.place[blockIdx.x] = me;
+            cuda::atomic_ref<int, cuda::thread_scope_device> cnt(*a.place_count);
+            cnt.fetch_add(1, cuda::memory_order_release);
+            bool ok = cnt.load(cuda::memory_order_acquire) >= (int)gridDim.x;
+            for (int64_t it = 0; !ok && it < a.wait_limit; ++it) {
+                __nanosleep(128);
+                ok = cnt.load(cuda::memory_order_acquire) >= (int)gridDim.x;
+                if (!ok && (it & 63) == 0 && *(volatile int*)a.abort_flag) break;
+            }
+            if (ok) {
+                rank = 0;
+                for (int j = 0; j < (int)gridDim.x; ++j) {
+                    const int sj = __ldcg(a.place + j);
+                    rank += (sj < me) || (sj == me && j < (int)blockIdx.x);
+                }
+            } else {
+                atomicOr(a.status, 2);
+                atomicExch(a.abort_flag, 1);
+            }
+        }
+        s_pe = rank;
+    }
+    __syncthreads();
+    return s_pe;
+}
 
 // ---------------------------------------------------------------------------
 // WENO5-JS reconstruction at the right edge of f[2] from f[0..4]

@@ -86,7 +86,7 @@ __device__ __forceinline__ double fused_buffer_old(const StageArgs& a, int64_t n
 // stage argument itself (no FP64 instruction).
 template <int H, int PPL, int RK, int W>
 __device__ __forceinline__ void fused_step(const StageArgs& a, const double* __restrict__ uin,
-                                           double* __restrict__ uout, int64_t n, double* sm)
+                                           double* __restrict__ uout, int64_t n, double* sm, int64_t cta)
 {
     constexpr int B = 32 * PPL;
     constexpr int S = RkS<RK>::S;
@@ -102,7 +102,7 @@ __device__ __forceinline__ void fused_step(const StageArgs& a, const double* __r
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int64_t P = a.P;
-    const int64_t p0 = (int64_t)blockIdx.x * W;
+    const int64_t p0 = cta * W;  // the CTA's first PE
     const int nW = (int)(P - p0 < W ? P - p0 : W);  // PEs of this CTA
     const int64_t pl = p0 == 0 ? P - 1 : p0 - 1;     // outer neighbours
     const int64_t pr = p0 + nW == P ? 0 : p0 + nW;
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) step_fused_advdiff(const StageAr
                                                                    double* __restrict__ uout, int64_t n)
 {
     extern __shared__ double sm[];
-    fused_step<H, PPL, RK, W>(a, uin, uout, n, sm);
+    fused_step<H, PPL, RK, W>(a, uin, uout, n, sm, blockIdx.x);
 }
 
 __device__ __forceinline__ int64_t fused_load_acquire(int64_t* p)
@@ -288,7 +288,9 @@ __device__ bool fused_wait_ge(const StageArgs& a, int64_t* ctr, int64_t target)
 }
 
 // All steps of an at_step call in one cooperative launch (every CTA
-// resident).  CTA c publishes in done[c] the level it has reached; before
+// resident).  The CTA at position c (its rank by SM, place_rank: neighbouring
+// positions on neighbouring SMs) takes PEs c W .. c W + W - 1 and publishes
+// in done[c] the level it has reached; before
 // step n it waits for its two neighbour CTAs to have finished step n-1.  That
 // one wait covers everything a step reads from outside the CTA: the
 // neighbours' u^n on the strips (written at their step n-1), and ring levels
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) steps_fused_advdiff(const StageA
 {
     extern __shared__ double sm[];
     __shared__ int s_fail;
-    const int64_t C = gridDim.x, c = blockIdx.x;
+    const int64_t C = gridDim.x, c = place_rank(a);  // CTA c takes PEs c W .. c W + W - 1
     const int64_t cl = c == 0 ? C - 1 : c - 1, cr = c == C - 1 ? 0 : c + 1;
     const bool withheld = a.withhold_pe >= 0 && a.withhold_pe / W == c;  // fault injection: never publishes
     for (int64_t i = 0; i < nsteps; ++i) {
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) steps_fused_advdiff(const StageA
             __syncthreads();
             if (s_fail) break;
         }
-        fused_step<H, PPL, RK, W>(a, (i & 1) ? b1 : b0, (i & 1) ? b0 : b1, n, sm);
+        fused_step<H, PPL, RK, W>(a, (i & 1) ? b1 : b0, (i & 1) ? b0 : b1, n, sm, c);
         __syncthreads();  // every thread's writes of step n
         if (threadIdx.x == 0 && !withheld) {
             __threadfence();
@@ -322,12 +324,15 @@ __global__ void __launch_bounds__(32 * (W + 1)) steps_fused_advdiff(const StageA
     }
 }
 
-// done[c] = level0 for the CTAs of a launch, and the abort flag cleared
-__global__ void fused_counters_set(int64_t* done, int64_t C, int64_t level0, int* abort_flag)
+// done[c] = level0 for the CTAs of a launch, the abort flag and the placement count cleared
+__global__ void fused_counters_set(int64_t* done, int64_t C, int64_t level0, int* abort_flag, int* place_count)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C; i += (int64_t)gridDim.x * blockDim.x)
         done[i] = level0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *abort_flag = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *abort_flag = 0;
+        *place_count = 0;
+    }
 }
 
 } // namespace atk
@@ -460,7 +465,7 @@ cudaError_t atk_launch_fused_steps(const atk::StageArgs& a, int order, int W, in
     void* fn = fused_steps_fn(H, a.rk, a.B / 32, W);
     const size_t smem = fused_smem(a.B, H, a.S, W);
     atk::fused_counters_set<<<(unsigned)((C + 255) / 256 < 1024 ? (C + 255) / 256 : 1024), 256, 0, st>>>(
-        a.done, C, level0, a.abort_flag);
+        a.done, C, level0, a.abort_flag, a.place_count);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -40,58 +40,6 @@ __device__ __forceinline__ void store_release(int64_t* p, int64_t v)
     r.store(v, cuda::memory_order_release);
 }
 
-// the SM this thread runs on
-__device__ __forceinline__ int sm_id()
-{
-    unsigned r;
-    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
-    return (int)r;
-}
-
-// The PE of this CTA.  Neighbouring PEs hand each other their edge windows
-// every stage, and a hand-off between SMs far apart (GB300's two dies) costs
-// more than one between SMs that share a GPC.  The blocks of a launch are
-// spread over the SMs in an order the program does not choose, so the PEs
-// are dealt out by the SMs the CTAs landed on: every CTA records its SM,
-// meets the others at a one-time bounded barrier (the launch is cooperative,
-// so all CTAs are resident), and takes as its PE its rank in (SM, block)
-// order.  Consecutive PEs then sit on the same or neighbouring SMs.  The
-// arithmetic of a PE does not depend on where it runs, so results are the
-// same bit for bit; a barrier that runs out keeps block = PE (the run then
-// stops with the wait error).
-__device__ int64_t place_pe(const StageArgs& a)
-{
-    __shared__ int s_pe;
-    if (threadIdx.x == 0) {
-        int rank = (int)blockIdx.x;
-        if (a.place) {
-            const int me = sm_id();
-            a.place[blockIdx.x] = me;
-            cuda::atomic_ref<int, cuda::thread_scope_device> cnt(*a.place_count);
-            cnt.fetch_add(1, cuda::memory_order_release);
-            bool ok = cnt.load(cuda::memory_order_acquire) >= (int)gridDim.x;
-            for (int64_t it = 0; !ok && it < a.wait_limit; ++it) {
-                __nanosleep(128);
-                ok = cnt.load(cuda::memory_order_acquire) >= (int)gridDim.x;
-                if (!ok && (it & 63) == 0 && *(volatile int*)a.abort_flag) break;
-            }
-            if (ok) {
-                rank = 0;
-                for (int j = 0; j < (int)gridDim.x; ++j) {
-                    const int sj = __ldcg(a.place + j);
-                    rank += (sj < me) || (sj == me && j < (int)blockIdx.x);
-                }
-            } else {
-                atomicOr(a.status, 2);
-                atomicExch(a.abort_flag, 1);
-            }
-        }
-        s_pe = rank;
-    }
-    __syncthreads();
-    return s_pe;
-}
-
 // bounded wait for *ctr >= target; false if it ran out or another wait did
 __device__ bool wait_ge(const StageArgs& a, int64_t* ctr, int64_t target)
 {
@@ -222,7 +170,7 @@ __global__ void __launch_bounds__(288, 2) persist_central(const StageArgs a, int
     using P = Phys<PDE>;
     constexpr int NV = P::NV, ND = P::ND;
     const int B = a.B, W2 = B + 2 * H, S = a.S;
-    const int64_t pe = place_pe(a);
+    const int64_t pe = place_rank(a);
     const int64_t nbr[2] = {pe == 0 ? a.P - 1 : pe - 1, pe == a.P - 1 ? 0 : pe + 1};
     extern __shared__ double sm[];
     double* U = sm;                // u^n                 [NV][B]

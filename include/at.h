@@ -228,6 +228,25 @@ int at_run(at_ctx* ctx, int64_t nsteps);
  * the target; the copy is synchronous. */
 int at_read(at_ctx* ctx, int what, void* dst, size_t bytes, int dst_on_device);
 
+/* Checkpoint / resume.  The delays are counter-based (Philox of the seed,
+ * level, stage, PE and side, Sec. 5), so between two steps a run is fully
+ * described by the problem, the delay model, the level n, the state u^n, the
+ * history ring (the edge windows of the stage arguments of the levels a
+ * delayed buffer point can still read, Sec. 2.3), the delays of the last step
+ * and, for a PE range (AT_OPT_OPEN_ENDS), its outside windows.
+ * at_checkpoint_bytes gives the size of such a blob (0 without a problem and
+ * a delay model); at_save copies it to dst (host or device memory, as
+ * dst_on_device says; synchronous), between steps only (AT_ESTATE within a
+ * step begun with at_stage); at_restore loads one into a context that has
+ * the same problem, delay model and history / PE-range options (AT_EINVAL
+ * otherwise, and for a truncated or foreign blob; nothing is changed then),
+ * after which the run continues exactly, bit for bit, as the run that saved
+ * it, on any path.  The blob's layout is private to the library (a header,
+ * then the state, the delay log, the ring and the outside windows). */
+size_t at_checkpoint_bytes(const at_ctx* ctx);
+int at_save(at_ctx* ctx, void* dst, size_t bytes, int dst_on_device);
+int at_restore(at_ctx* ctx, const void* src, size_t bytes, int src_on_device);
+
 /* Options (AT_OPT_*); they apply from the next at_step on. */
 int at_set_option(at_ctx* ctx, int key, int64_t value);
 

@@ -31,6 +31,7 @@ STAGES = {"rk2": 2, "rk3tvd": 3, "rk4": 4}
 SYMBOLS = ("at_create", "at_workspace_bytes", "at_set_problem", "at_set_delays", "at_step", "at_run",
            "at_read", "at_profile", "at_set_option", "at_set_delay_trace", "at_destroy", "at_last_error",
            "at_run_noalloc", "at_stage", "at_edges", "at_put_ext", "at_delay",
+           "at_checkpoint_bytes", "at_save", "at_restore",
            "at_batch_table_bytes", "at_batch_create", "at_batch_bind", "at_batch_release", "at_batch_set_config",
            "at_batch_step", "at_batch_run", "at_batch_query", "at_batch_destroy")
 PATH_AUTO, PATH_STAGE, PATH_PERSISTENT, PATH_FUSED = 0, 1, 2, 3
@@ -108,6 +109,12 @@ def lib():
         L.at_put_ext.restype = ctypes.c_int
         L.at_delay.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_int]
         L.at_delay.restype = ctypes.c_int
+        L.at_checkpoint_bytes.argtypes = [vp]
+        L.at_checkpoint_bytes.restype = ctypes.c_size_t
+        L.at_save.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
+        L.at_save.restype = ctypes.c_int
+        L.at_restore.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
+        L.at_restore.restype = ctypes.c_int
         L.at_last_error.restype = ctypes.c_char_p
         for f in ("at_create", "at_set_problem", "at_set_delays", "at_step", "at_run", "at_read", "at_profile",
                   "at_destroy"):
@@ -263,6 +270,29 @@ class Solver:
 
     def set_option(self, key: int, value: int):
         check(lib().at_set_option(self._h, int(key), int(value)))
+
+    def checkpoint(self, device: bool = False):
+        """The run between two steps as one blob (at_save): host bytes (numpy
+        uint8), or a torch uint8 tensor on the context's device."""
+        nb = lib().at_checkpoint_bytes(self._h)
+        if nb == 0:
+            raise AtError(AT_ESTATE, "no problem and delay model set")
+        if device:
+            out = self.torch.empty(nb, dtype=self.torch.uint8, device=self.u.device)
+            check(lib().at_save(self._h, ctypes.c_void_p(out.data_ptr()), nb, 1))
+        else:
+            out = np.empty(nb, dtype=np.uint8)
+            check(lib().at_save(self._h, ctypes.c_void_p(out.ctypes.data), nb, 0))
+        return out
+
+    def restore(self, blob):
+        """Continue from a blob of checkpoint() (at_restore); the context must
+        hold the same problem and delay model."""
+        if isinstance(blob, np.ndarray):
+            blob = np.ascontiguousarray(blob, dtype=np.uint8)
+            check(lib().at_restore(self._h, ctypes.c_void_p(blob.ctypes.data), blob.nbytes, 0))
+        else:
+            check(lib().at_restore(self._h, ctypes.c_void_p(blob.data_ptr()), blob.numel(), 1))
 
     def trace_delays(self, nsteps: int):
         """Record the delay of every (step, stage, PE, side) of the next

@@ -769,6 +769,136 @@ int at_read(at_ctx* c, int what, void* dst, size_t bytes, int dst_on_device)
     return AT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// checkpoint / resume.  The delays are counter-based (Philox of seed, level,
+// stage, PE, side), so a run is determined by the problem, the delay model
+// and, at a step boundary, the state, the history ring, the outside windows
+// of a PE range and the level: a blob of those resumes bit for bit.
+// ---------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];  // "AT-CKPT1"
+    int64_t level, hist_level;
+    at_problem pb;
+    at_delays dl;
+    int32_t hist, open_ends;
+    int64_t pe_base, pe_total;
+    int64_t state_bytes, dlog_bytes, ring_bytes, ext_bytes;
+};
+const char kCkptMagic[8] = {'A', 'T', '-', 'C', 'K', 'P', 'T', '1'};
+
+bool same_problem(const at_problem& a, const at_problem& b)
+{
+    return a.pde == b.pde && a.order == b.order && a.rk == b.rk && a.pe_size == b.pe_size && a.n == b.n &&
+           std::memcmp(&a.dx, &b.dx, sizeof(double)) == 0 && std::memcmp(&a.dt, &b.dt, sizeof(double)) == 0 &&
+           std::memcmp(a.prm, b.prm, sizeof a.prm) == 0 && a.weno == b.weno;
+}
+
+bool same_delays(const at_delays& a, const at_delays& b)
+{
+    return a.mode == b.mode && a.k_max == b.k_max && a.dist == b.dist && a.per_stage == b.per_stage &&
+           std::memcmp(a.prob, b.prob, sizeof a.prob) == 0 && a.seed == b.seed && a.instance == b.instance;
+}
+
+void ckpt_sizes(const at_ctx* c, CkptHeader& h)
+{
+    h.state_bytes = (int64_t)(sizeof(double) * (size_t)nvar_of(c->pb.pde) * c->pb.n);
+    h.dlog_bytes = (int64_t)((size_t)c->L.S * c->L.P * 2);
+    h.ring_bytes = (int64_t)(sizeof(double) * c->L.ring_elems);
+    h.ext_bytes = (int64_t)(sizeof(double) * c->L.ext_elems);
+}
+}  // namespace
+
+size_t at_checkpoint_bytes(const at_ctx* c)
+{
+    if (!c || !c->have_problem || !c->have_delays) return 0;
+    CkptHeader h{};
+    ckpt_sizes(c, h);
+    return sizeof(CkptHeader) + (size_t)(h.state_bytes + h.dlog_bytes + h.ring_bytes + h.ext_bytes);
+}
+
+int at_save(at_ctx* c, void* dst, size_t bytes, int dst_on_device)
+{
+    if (!c || !dst) return fail(AT_EINVAL, "context or destination is NULL");
+    if (!c->have_problem || !c->have_delays) return fail(AT_ESTATE, "at_set_problem and at_set_delays must come first");
+    if (c->stage_pos != 0) return fail(AT_ESTATE, "a checkpoint is taken between steps, not within a step begun with at_stage");
+    const size_t need = at_checkpoint_bytes(c);
+    if (bytes < need) return fail(AT_EINVAL, "destination of %zu bytes is below the %zu bytes needed", bytes, need);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, sizeof h.magic);
+    h.level = c->level;
+    h.hist_level = c->hist_level;
+    h.pb = c->pb;
+    h.dl = c->dl;
+    h.hist = c->hist;
+    h.open_ends = c->open_ends;
+    h.pe_base = c->pe_base;
+    h.pe_total = c->pe_total;
+    ckpt_sizes(c, h);
+    unsigned char* d = (unsigned char*)dst;
+    const cudaMemcpyKind from_host = dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    const cudaMemcpyKind from_dev = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    size_t off = 0;
+    e = cudaMemcpyAsync(d, &h, sizeof h, from_host, c->stream);
+    off += sizeof h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + off, c->state, (size_t)h.state_bytes, from_dev, c->stream);
+    off += (size_t)h.state_bytes;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + off, c->base.dlog, (size_t)h.dlog_bytes, from_dev, c->stream);
+    off += (size_t)h.dlog_bytes;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + off, c->base.ring, (size_t)h.ring_bytes, from_dev, c->stream);
+    off += (size_t)h.ring_bytes;
+    if (e == cudaSuccess && h.ext_bytes)
+        e = cudaMemcpyAsync(d + off, c->base.ext, (size_t)h.ext_bytes, from_dev, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // h lives on this frame
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
+    return AT_OK;
+}
+
+int at_restore(at_ctx* c, const void* src, size_t bytes, int src_on_device)
+{
+    if (!c || !src) return fail(AT_EINVAL, "context or source is NULL");
+    if (!c->have_problem || !c->have_delays) return fail(AT_ESTATE, "at_set_problem and at_set_delays must come first");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if (bytes < sizeof(CkptHeader)) return fail(AT_EINVAL, "a checkpoint of %zu bytes has no header", bytes);
+    CkptHeader h{};
+    e = cudaMemcpyAsync(&h, src, sizeof h, src_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint header read");
+    if (std::memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0) return fail(AT_EINVAL, "not a checkpoint of this library");
+    CkptHeader want{};
+    ckpt_sizes(c, want);
+    if (!same_problem(h.pb, c->pb) || !same_delays(h.dl, c->dl))
+        return fail(AT_EINVAL, "the checkpoint belongs to another problem or delay model");
+    if (h.hist != c->hist || h.open_ends != c->open_ends || h.pe_base != c->pe_base || h.pe_total != c->pe_total)
+        return fail(AT_EINVAL, "the checkpoint was taken with other history / PE-range options");
+    if (h.state_bytes != want.state_bytes || h.dlog_bytes != want.dlog_bytes || h.ring_bytes != want.ring_bytes ||
+        h.ext_bytes != want.ext_bytes || h.level < 0)
+        return fail(AT_EINVAL, "the checkpoint's sizes do not match this context");
+    const size_t need = at_checkpoint_bytes(c);
+    if (bytes < need) return fail(AT_EINVAL, "a checkpoint of %zu bytes is below the %zu bytes it needs", bytes, need);
+    const unsigned char* sp = (const unsigned char*)src;
+    const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t off = sizeof h;
+    e = cudaMemcpyAsync(c->state, sp + off, (size_t)h.state_bytes, kind, c->stream);
+    off += (size_t)h.state_bytes;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->base.dlog, sp + off, (size_t)h.dlog_bytes, kind, c->stream);
+    off += (size_t)h.dlog_bytes;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->base.ring, sp + off, (size_t)h.ring_bytes, kind, c->stream);
+    off += (size_t)h.ring_bytes;
+    if (e == cudaSuccess && h.ext_bytes) e = cudaMemcpyAsync(c->base.ext, sp + off, (size_t)h.ext_bytes, kind, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->base.status, 0, 2 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint restore");
+    c->level = h.level;
+    c->hist_level = h.hist_level;
+    c->stage_pos = 0;
+    g_err[0] = 0;
+    return AT_OK;
+}
+
 int at_set_option(at_ctx* c, int key, int64_t value)
 {
     if (!c) return fail(AT_EINVAL, "context is NULL");

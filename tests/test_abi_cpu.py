@@ -127,6 +127,9 @@ def test_calls_out_of_order_and_without_gpu(L):
         assert rc in (api.AT_ECUDA, api.AT_EINVAL)
         assert L.at_last_error()
     assert L.at_step(None, 1) == api.AT_EINVAL
+    assert L.at_checkpoint_bytes(None) == 0
+    assert L.at_save(None, None, 0, 0) == api.AT_EINVAL
+    assert L.at_restore(None, None, 0, 0) == api.AT_EINVAL
 
 
 def test_batch_table_and_validation(L):

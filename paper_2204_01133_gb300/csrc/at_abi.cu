@@ -15,6 +15,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/at.h"
 #include "at_device.cuh"
 
@@ -335,6 +337,17 @@ atk::StageArgs build_args(const at_problem* pb, const at_delays* dl, const Layou
 
 } // namespace
 
+namespace {
+// An NVTX range over a scope: the library's calls, steps and persistent
+// launches appear on the Nsight Systems timeline (a no-op without a tool).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
+
 struct at_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -478,6 +491,7 @@ int at_set_problem(at_ctx* c, const at_problem* pb, double* state_dev, const dou
 
 int at_set_delays(at_ctx* c, const at_delays* dl)
 {
+    NvtxRange nvtx_range("at_set_delays");
     if (!c) return fail(AT_EINVAL, "context is NULL");
     if (!c->have_problem) return fail(AT_ESTATE, "at_set_problem must come first");
     int st = check_delays(dl);
@@ -525,6 +539,7 @@ int at_set_delays(at_ctx* c, const at_delays* dl)
 
 int at_step(at_ctx* c, int64_t nsteps)
 {
+    NvtxRange nvtx_range("at_step");
     if (!c) return fail(AT_EINVAL, "context is NULL");
     if (!c->have_problem || !c->have_delays) return fail(AT_ESTATE, "at_set_problem and at_set_delays must come first");
     if (nsteps < 0) return fail(AT_EINVAL, "nsteps must be >= 0");
@@ -603,6 +618,7 @@ int at_step(at_ctx* c, int64_t nsteps)
             nsteps = 0;               // nothing left for the per-step launches
         }
         for (int64_t i = 0; i < nsteps; ++i) {
+            NvtxRange step_range("step (fused path)");
             atk::StageArgs a = c->base;
             a.level = c->level;
             e = record(c, true);
@@ -672,6 +688,7 @@ int at_step(at_ctx* c, int64_t nsteps)
         if (e != cudaSuccess) return cuda_fail(e, "stage-history recompute launch");
     }
     for (int64_t i = 0; i < nsteps; ++i) {
+        NvtxRange step_range("step (per-stage path)");
         atk::StageArgs a = c->base;
         a.level = c->level;
         a.u = u;
@@ -819,6 +836,7 @@ size_t at_checkpoint_bytes(const at_ctx* c)
 
 int at_save(at_ctx* c, void* dst, size_t bytes, int dst_on_device)
 {
+    NvtxRange nvtx_range("at_save");
     if (!c || !dst) return fail(AT_EINVAL, "context or destination is NULL");
     if (!c->have_problem || !c->have_delays) return fail(AT_ESTATE, "at_set_problem and at_set_delays must come first");
     if (c->stage_pos != 0) return fail(AT_ESTATE, "a checkpoint is taken between steps, not within a step begun with at_stage");
@@ -858,6 +876,7 @@ int at_save(at_ctx* c, void* dst, size_t bytes, int dst_on_device)
 
 int at_restore(at_ctx* c, const void* src, size_t bytes, int src_on_device)
 {
+    NvtxRange nvtx_range("at_restore");
     if (!c || !src) return fail(AT_EINVAL, "context or source is NULL");
     if (!c->have_problem || !c->have_delays) return fail(AT_ESTATE, "at_set_problem and at_set_delays must come first");
     cudaError_t e = cudaSetDevice(c->device);
@@ -1001,6 +1020,7 @@ int at_delay(at_ctx* c, int64_t level, int stage, int64_t pe, int side)
 
 int at_stage(at_ctx* c)
 {
+    NvtxRange nvtx_range("at_stage");
     int st = range_ready(c);
     if (st != AT_OK) return st;
     if (c->hist == AT_HIST_RECOMPUTE) return fail(AT_EINVAL, "at_stage runs reading B of the stage history");
@@ -1428,6 +1448,7 @@ int at_batch_set_config(at_batch* b, int mode, int block, int ctas_per_sm, int u
 
 int at_batch_step(at_batch* b, int64_t chunk)
 {
+    NvtxRange nvtx_range("at_batch_step");
     if (!b) return fail(AT_EINVAL, "batch is NULL");
     if (chunk < 0) return fail(AT_EINVAL, "chunk must be >= 0");
     cudaError_t e = cudaSetDevice(b->device);
@@ -1543,6 +1564,7 @@ void* g_noalloc_ptr[kMaxDevices];  // device address of the array, per device (s
 int at_run_noalloc(const at_problem* pb, const at_delays* dl, double* state_dev, int64_t nsteps, int device,
                    void* cuda_stream)
 {
+    NvtxRange nvtx_range("at_run_noalloc");
     if (!state_dev) return fail(AT_EINVAL, "state must be a device pointer");
     if (nsteps < 0) return fail(AT_EINVAL, "nsteps must be >= 0");
     const size_t need = at_workspace_bytes(pb, dl);

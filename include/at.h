@@ -42,7 +42,8 @@ typedef enum {
     AT_ECUDA = -3,     /* a CUDA call failed; at_last_error() has its message   */
     AT_EUNSTABLE = -4, /* a non-finite value appeared in the state              */
     AT_ETIMEOUT = -5,  /* a bounded device wait (persistent, fused path) ran out */
-    AT_ESTATE = -6     /* calls out of order (problem, then delays, then steps) */
+    AT_ESTATE = -6,    /* calls out of order (problem, then delays, then steps) */
+    AT_ECORRUPT = -7   /* a canary zone of the workspace was overwritten         */
 } at_status;
 
 /* PDEs.  Physics constants prm[] for each (nondimensional, rho0 = T0 = 1,
@@ -246,6 +247,16 @@ int at_read(at_ctx* ctx, int what, void* dst, size_t bytes, int dst_on_device);
 size_t at_checkpoint_bytes(const at_ctx* ctx);
 int at_save(at_ctx* ctx, void* dst, size_t bytes, int dst_on_device);
 int at_restore(at_ctx* ctx, const void* src, size_t bytes, int src_on_device);
+
+/* Canary zones: the workspace holds kGuardBytes = 256 bytes of 0xA5 after
+ * each of its slices (stage buffers, RK accumulator, history ring, delay log,
+ * status words, progress counters, placement, ring of derived quantities,
+ * outside windows), written by at_set_delays.  at_check_guards reads them
+ * back (synchronous): AT_OK while every zone is intact, AT_ECORRUPT naming
+ * the first overwritten one otherwise, the evidence a kernel or a caller
+ * wrote past a slice.  A check for tests and debugging; no kernel reads the
+ * zones. */
+int at_check_guards(at_ctx* ctx);
 
 /* Options (AT_OPT_*); they apply from the next at_step on. */
 int at_set_option(at_ctx* ctx, int key, int64_t value);

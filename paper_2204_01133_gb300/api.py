@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libat_gb300.so")
 
-AT_OK, AT_EINVAL, AT_ENOMEM, AT_ECUDA, AT_EUNSTABLE, AT_ETIMEOUT, AT_ESTATE = 0, -1, -2, -3, -4, -5, -6
+AT_OK, AT_EINVAL, AT_ENOMEM, AT_ECUDA, AT_EUNSTABLE, AT_ETIMEOUT, AT_ESTATE, AT_ECORRUPT = 0, -1, -2, -3, -4, -5, -6, -7
 PDE = {"advdiff": 0, "rns": 1, "euler": 2, "adv_weno": 3, "burgers": 4, "rns_chain": 5}
 RK = {"rk2": 0, "rk3tvd": 1, "rk4": 2}
 MODE = {"sync": 0, "as": 1, "at": 2}
@@ -31,7 +31,7 @@ STAGES = {"rk2": 2, "rk3tvd": 3, "rk4": 4}
 SYMBOLS = ("at_create", "at_workspace_bytes", "at_set_problem", "at_set_delays", "at_step", "at_run",
            "at_read", "at_profile", "at_set_option", "at_set_delay_trace", "at_destroy", "at_last_error",
            "at_run_noalloc", "at_stage", "at_edges", "at_put_ext", "at_delay",
-           "at_checkpoint_bytes", "at_save", "at_restore",
+           "at_checkpoint_bytes", "at_save", "at_restore", "at_check_guards",
            "at_batch_table_bytes", "at_batch_create", "at_batch_bind", "at_batch_release", "at_batch_set_config",
            "at_batch_step", "at_batch_run", "at_batch_query", "at_batch_destroy")
 PATH_AUTO, PATH_STAGE, PATH_PERSISTENT, PATH_FUSED = 0, 1, 2, 3
@@ -115,6 +115,8 @@ def lib():
         L.at_save.restype = ctypes.c_int
         L.at_restore.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
         L.at_restore.restype = ctypes.c_int
+        L.at_check_guards.argtypes = [vp]
+        L.at_check_guards.restype = ctypes.c_int
         L.at_last_error.restype = ctypes.c_char_p
         for f in ("at_create", "at_set_problem", "at_set_delays", "at_step", "at_run", "at_read", "at_profile",
                   "at_destroy"):
@@ -270,6 +272,11 @@ class Solver:
 
     def set_option(self, key: int, value: int):
         check(lib().at_set_option(self._h, int(key), int(value)))
+
+    def check_guards(self):
+        """Raise AtError(AT_ECORRUPT) if a canary zone of the workspace was
+        overwritten (at_check_guards)."""
+        check(lib().at_check_guards(self._h))
 
     def checkpoint(self, device: bool = False):
         """The run between two steps as one blob (at_save): host bytes (numpy

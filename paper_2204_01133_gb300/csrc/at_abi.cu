@@ -81,12 +81,20 @@ int cuda_fail(cudaError_t e, const char* what)
     return fail(AT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// canary zones: kGuardBytes of kGuardByte after each workspace slice,
+// written by at_set_delays and checked by at_check_guards
+const int kGuards = 10;
+const size_t kGuardBytes = 256;
+const unsigned char kGuardByte = 0xA5;
+
 struct Layout {
     int nvar, H, q, S, R;
     int64_t P;
     int Tw, wpp;
     size_t off_A, off_B, off_acc, off_ring, off_dlog, off_status, off_done, off_place, off_gring, off_ext, total;
     size_t ring_elems, gring_elems, ext_elems;
+    size_t guard[kGuards];  // a canary zone of kGuardBytes after every slice
+    int nguard;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -176,34 +184,34 @@ Layout layout(const at_problem* pb, const at_delays* dl)
     L.wpp = pb->pe_size / L.Tw;
     const size_t field = sizeof(double) * (size_t)L.nvar * pb->n;
     size_t off = 0;
-    L.off_A = off;
-    off = align256(off + field);
-    L.off_B = off;
-    off = align256(off + field);
-    L.off_acc = off;
-    if (pb->rk != AT_RK3TVD) off = align256(off + field);
+    L.nguard = 0;
+    // a slice of `bytes` at the current offset, then its canary zone
+    auto slice = [&](size_t bytes) -> size_t {
+        const size_t at = off;
+        off = align256(off + bytes);
+        L.guard[L.nguard++] = off;
+        off += kGuardBytes;
+        return at;
+    };
+    L.off_A = slice(field);
+    L.off_B = slice(field);
+    L.off_acc = slice(pb->rk != AT_RK3TVD ? field : 0);
     L.ring_elems = (size_t)L.R * L.S * L.P * 2 * L.H * L.nvar;
-    L.off_ring = off;
-    off = align256(off + sizeof(double) * L.ring_elems);
-    L.off_dlog = off;
-    off = align256(off + (size_t)L.S * L.P * 2);
-    L.off_status = off;  // status word, then the abort flag of the persistent path
-    off = align256(off + 256);
-    L.off_done = off;    // per-PE progress counters of the persistent path
-    off = align256(off + sizeof(int64_t) * (size_t)L.P);
-    L.off_place = off;   // the persistent path's SM of every CTA (PE placement)
-    if (L.P <= kPersistMaxPE) off = align256(off + sizeof(int) * (size_t)L.P);
+    L.off_ring = slice(sizeof(double) * L.ring_elems);
+    L.off_dlog = slice((size_t)L.S * L.P * 2);
+    L.off_status = slice(256);  // status word, the abort flag and the placement count of the persistent path
+    L.off_done = slice(sizeof(int64_t) * (size_t)L.P);  // per-PE progress counters of the persistent path
+    // the persistent path's SM of every CTA (PE placement)
+    L.off_place = slice(L.P <= kPersistMaxPE ? sizeof(int) * (size_t)L.P : 0);
     // the persistent path's ring of derived quantities of the edge windows
     // (central PDEs with few enough PEs to take that path)
     L.gring_elems = 0;
     if ((pb->pde == AT_ADVDIFF || pb->pde == AT_RNS) && L.P <= kPersistMaxPE)
         L.gring_elems = (size_t)L.R * L.S * L.P * 2 * L.H * (pb->pde == AT_RNS ? 8 : 1);
-    L.off_gring = off;
-    off = align256(off + sizeof(double) * L.gring_elems);
+    L.off_gring = slice(sizeof(double) * L.gring_elems);
     // windows beyond the ends of a PE range (open ends): [R][S][2][H][nvar]
     L.ext_elems = (size_t)L.R * L.S * 2 * L.H * L.nvar;
-    L.off_ext = off;
-    off = align256(off + sizeof(double) * L.ext_elems);
+    L.off_ext = slice(sizeof(double) * L.ext_elems);
     L.total = off;
     return L;
 }
@@ -513,6 +521,8 @@ int at_set_delays(at_ctx* c, const at_delays* dl)
     if (e == cudaSuccess) e = cudaMemsetAsync(a.dlog, 0, (size_t)L.S * L.P * 2, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.status, 0, 2 * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.ext, 0, sizeof(double) * L.ext_elems, c->stream);
+    for (int g = 0; g < L.nguard && e == cudaSuccess; ++g)
+        e = cudaMemsetAsync(c->ws + L.guard[g], kGuardByte, kGuardBytes, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "workspace reset");
     c->stage_pos = 0;
     atk::StageArgs s = a;
@@ -783,6 +793,30 @@ int at_read(at_ctx* c, int what, void* dst, size_t bytes, int dst_on_device)
     e = cudaMemcpyAsync(dst, src, need, kind, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "at_read copy");
+    return AT_OK;
+}
+
+int at_check_guards(at_ctx* c)
+{
+    if (!c) return fail(AT_EINVAL, "context is NULL");
+    if (!c->have_problem || !c->have_delays) return fail(AT_ESTATE, "at_set_problem and at_set_delays must come first");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    static const char* const names[kGuards] = {"stage buffer A", "stage buffer B", "RK accumulator", "history ring",
+                                               "delay log", "status words", "progress counters", "PE placement",
+                                               "ring of derived quantities", "outside windows"};
+    const Layout& L = c->L;
+    std::vector<unsigned char> buf(kGuardBytes * (size_t)L.nguard);
+    for (int g = 0; g < L.nguard && e == cudaSuccess; ++g)
+        e = cudaMemcpyAsync(buf.data() + kGuardBytes * g, c->ws + L.guard[g], kGuardBytes, cudaMemcpyDeviceToHost,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "canary read");
+    for (int g = 0; g < L.nguard; ++g)
+        for (size_t b = 0; b < kGuardBytes; ++b)
+            if (buf[kGuardBytes * g + b] != kGuardByte)
+                return fail(AT_ECORRUPT, "the canary zone after the %s was overwritten (byte %zu of %zu)", names[g], b,
+                            kGuardBytes);
     return AT_OK;
 }
 

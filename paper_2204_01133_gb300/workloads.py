@@ -370,9 +370,23 @@ def serving_stream(rate=2000.0, duration=10.0, seed=0, n_min=512, n_max=262144, 
     return out
 
 
-CONFIGS = {
-    "advdiff-n2048": lambda **kw: advdiff(**kw),
-    "rns-flame-n16384": lambda **kw: rns(case="flame", **kw),
-    "rns-ignition-n16384": lambda **kw: rns(case="ignition", **kw),
-    "detonation-n16777216": lambda **kw: detonation(**kw),
-}
+def config_names():
+    """The named benchmark configurations of configs.json (next to this file)."""
+    return sorted(_configs())
+
+
+def config(name: str):
+    """Build a named configuration of configs.json: (the builder's output, the
+    step count).  The output is (problem dict, initial state) for a single
+    solve, a list of (problem, state, steps) for the batched one and a list
+    of requests for the serving stream."""
+    c = _configs()[name]
+    return globals()[c["builder"]](**c["kwargs"]), c["steps"]
+
+
+@lru_cache(maxsize=1)
+def _configs():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs.json")) as f:
+        return json.load(f)

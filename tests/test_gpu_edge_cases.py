@@ -3,7 +3,8 @@ stencils allow (pe_size = 2H) for every PDE, that PE alone (its own
 neighbour on both sides), the largest single window (a prime PE size of
 1021, one window per PE, the largest shared-memory request of the WENO
 kernel), a zero-step call (state and delay log unchanged, bit for bit, on
-every path) and a negative step count (refused).  The Euler cases use the
+every path), a negative step count (refused) and forced maximum delays
+(every drawn delay at k_max, the oldest levels the ring keeps).  The Euler cases use the
 smooth entropy wave, so the plain per-variable bounds (1e-12 after one
 step, 1e-10 after the run) apply."""
 import numpy as np
@@ -97,3 +98,22 @@ def test_negative_step_count_is_refused():
         s.run(-1)
     assert ei.value.code == api.AT_EINVAL
     assert np.array_equal(s.read_state(), st)
+
+
+@pytest.mark.parametrize("name", ["advdiff", "rns", "entropy-wave"])
+def test_every_delay_at_its_maximum(name):
+    """Forced maximum delays (a delay table with all its mass at k_max): the
+    buffer points extrapolate from the oldest levels the ring keeps at every
+    step after the start-up clamp.  The AT schemes are built to take that
+    (Sec. 2.2); the run matches the oracle and the delay log shows k_max."""
+    if name == "advdiff":
+        pb, u0 = W.advdiff(n=1024, pe_size=32, order=4, mode="at", k_max=3, seed=31, cfl=0.05, dist="table",
+                           prob=[0.0, 0.0, 0.0, 1.0])
+    elif name == "rns":
+        pb, u0 = W.rns(case="flame", n=1536, pe_size=64, mode="at", k_max=4, seed=32, dt=0.003, dist="table",
+                       prob=[0.0, 0.0, 0.0, 0.0, 1.0])
+    else:
+        pb, u0 = W.entropy_wave(n=960, pe_size=96, mode="at", k_max=4, seed=33, dist="table",
+                                prob=[0.0, 0.0, 0.0, 0.0, 1.0])
+    s, _ = parity(pb, u0, 60, what="all delays at k_max, %s" % name)
+    assert (s.read_delays() == pb["k_max"]).all()

@@ -8,8 +8,9 @@ kernels on the same delay stream as the regular context path (at_set_problem
 + at_set_delays + at_run with a caller workspace), so its result must equal
 that path's bit for bit, on calls in a row that reuse the shared array (a
 stale ring, delay log or status word left by the previous call would show),
-and oversized problems must be refused before anything runs.  This file is
-collected last on purpose.
+and oversized problems must be refused before anything runs.  It is also
+checked against the oracle directly.  This file is collected last on
+purpose.
 """
 import numpy as np
 import pytest
@@ -70,3 +71,16 @@ def test_noalloc_refuses_problems_above_its_scratch(torch_cuda):
     assert "workspace" in str(ei.value)
     torch_cuda.cuda.synchronize()
     assert torch_cuda.equal(state, before)  # nothing ran
+
+
+def test_noalloc_matches_the_oracle(torch_cuda):
+    """The allocation-free run against the oracle itself, at the per-variable
+    bounds of the parity tests (1e-10 after the run)."""
+    import oracle
+    from parity import TOL_RUN, check
+    for pb, init, steps in [W.advdiff(n=2048, pe_size=64, mode="at", k_max=3, seed=5, cfl=0.075) + (400,),
+                            W.rns(case="flame", n=2048, pe_size=64, mode="at", k_max=4, seed=5, dt=0.003) + (60,)]:
+        got = _noalloc(torch_cuda, pb, init, steps)
+        o = oracle.Oracle(pb, init)
+        assert o.run(steps) == 0
+        check(pb, got, o.state(), TOL_RUN, "noalloc %s step %d" % (pb["pde"], steps))

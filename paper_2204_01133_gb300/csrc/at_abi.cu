@@ -48,7 +48,7 @@ cudaError_t atk_launch_batch(int variant, const atk::StageArgs* tab, int64_t* lv
 int atk_batch_max_ctas_per_sm(int variant, int block, size_t smem);
 cudaError_t atk_launch_batch_stage(int variant, const atk::StageArgs* tab, const int64_t* lvl, const int64_t* left,
                                    const int* win_slot, const int* win_idx, int nwin, int stage, int block,
-                                   size_t smem, cudaStream_t st);
+                                   size_t smem, int win_smem, cudaStream_t st);
 cudaError_t atk_launch_batch_advance(int64_t* lvl, int64_t* left, const int* slots, int n, cudaStream_t st);
 cudaError_t atk_launch_batch_status(const atk::StageArgs* tab, const int* slots, int n, int* out, cudaStream_t st);
 
@@ -1211,6 +1211,9 @@ BatchTable batch_table(int64_t cap, int64_t max_windows)
 }
 } // namespace
 
+// kernel variants of the WENO PDEs (one window per CTA in flat mode)
+static bool variant_is_weno(int g) { return g == 6 || g == 7 || g == 8; }
+
 struct at_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -1266,17 +1269,22 @@ cudaError_t batch_upload_order(at_batch* b)
         b->group_smem[g] = sm;
     }
     b->group_begin[kVariants] = (int)b->order_h.size();
-    // flat-mode window map, in the same order
+    // flat-mode map of CTAs, in the same order: one window each, or (central
+    // PDEs) two consecutive windows of one slot, marked by bit 30 of the
+    // window index (a lone last window of a slot takes a CTA alone)
     b->wslot_h.clear();
     b->widx_h.clear();
     for (int g = 0; g < kVariants; ++g) {
         b->wbegin[g] = (int64_t)b->wslot_h.size();
+        const bool pairs = !variant_is_weno(g);
         int smax = 0;
         for (int q = b->group_begin[g]; q < b->group_begin[g + 1]; ++q) {
             const int i = b->order_h[q];
-            for (int64_t w = 0; w < b->windows[i]; ++w) {
+            for (int64_t w = 0; w < b->windows[i];) {
+                const bool two = pairs && w + 1 < b->windows[i];
                 b->wslot_h.push_back(i);
-                b->widx_h.push_back((int)w);
+                b->widx_h.push_back((int)w | (two ? (1 << 30) : 0));
+                w += two ? 2 : 1;
             }
             smax = std::max(smax, b->args[i].S);
         }
@@ -1336,7 +1344,9 @@ cudaError_t batch_enqueue(at_batch* b, cudaStream_t st, int64_t chunk)
             const int* wi = (const int*)(b->tab + b->T.off_widx) + b->wbegin[g];
             for (int64_t step = 0; step < chunk && e == cudaSuccess; ++step) {
                 for (int stage = 0; stage < b->group_stages[g] && e == cudaSuccess; ++stage)
-                    e = atk_launch_batch_stage(g, tab, lvl, left, ws, wi, nwin, stage, b->block, smem, b->branch[g]);
+                    e = atk_launch_batch_stage(g, tab, lvl, left, ws, wi, nwin, stage, b->block,
+                                               variant_is_weno(g) ? smem : 2 * smem, (int)(smem / sizeof(double)),
+                                               b->branch[g]);
                 if (e == cudaSuccess) e = atk_launch_batch_advance(lvl, left, order, n, b->branch[g]);
             }
         }

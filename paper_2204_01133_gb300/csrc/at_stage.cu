@@ -608,26 +608,40 @@ __global__ void __launch_bounds__(256) batch_run(const StageArgs* __restrict__ t
 }
 
 // Flat mode: one launch per stage over the windows of every bound instance
-// of a kernel variant (window w belongs to slot win_slot[w] and is its window
-// win_idx[w]), so large instances spread over all SMs; an instance with no
-// steps left, or whose RK scheme has fewer stages, skips the launch.
+// of a kernel variant, so large instances spread over all SMs; an instance
+// with no steps left, or whose RK scheme has fewer stages, skips the launch.
+// CTA c takes window win_idx[c] & AT_BATCH_WIN_MASK of slot win_slot[c] and,
+// when bit 30 of win_idx[c] is set (central PDEs), the next window of the
+// same slot too, one half of the threads each with win_smem doubles of
+// shared memory apiece: two windows' fill items then share the barrier phases
+// of one CTA, as on the per-stage path.
+constexpr int AT_BATCH_WIN_MASK = 0x3fffffff;
 template <int PDE, int H, bool WENO>
 __global__ void __launch_bounds__(256, 4) batch_stage(const StageArgs* __restrict__ tab, const int64_t* __restrict__ lvl,
                                                    const int64_t* __restrict__ left, const int* __restrict__ win_slot,
-                                                   const int* __restrict__ win_idx, int stage)
+                                                   const int* __restrict__ win_idx, int stage, int win_smem)
 {
     extern __shared__ double sm[];
     const int slot = win_slot[blockIdx.x];
-    if (left[slot] <= 0) return;
+    if (left[slot] <= 0) return;  // the whole CTA: both windows belong to the slot
     const StageArgs& a = tab[slot];
     if (stage >= a.S) return;
     const double* X = (stage == 0) ? a.state : ((stage & 1) ? a.bufA : a.bufB);
     double* Y = (stage == a.S - 1) ? a.state : ((stage & 1) ? a.bufB : a.bufA);
     const Cx cx{lvl[slot], stage, X, Y, a.state};
-    if constexpr (WENO)
-        weno_window<PDE>(a, cx, win_idx[blockIdx.x], sm);
-    else
-        central_window<PDE, H>(a, cx, win_idx[blockIdx.x], sm, threadIdx.x, blockDim.x);
+    const int e = win_idx[blockIdx.x];
+    const int w0 = e & AT_BATCH_WIN_MASK;
+    if constexpr (WENO) {
+        weno_window<PDE>(a, cx, w0, sm);
+    } else {
+        if (e >> 30) {
+            const int half = blockDim.x >> 1;
+            const int g = threadIdx.x >= half ? 1 : 0;
+            central_window<PDE, H>(a, cx, w0 + g, sm + (size_t)g * win_smem, threadIdx.x - g * half, half);
+        } else {
+            central_window<PDE, H>(a, cx, w0, sm, threadIdx.x, blockDim.x);
+        }
+    }
 }
 
 // after every stage of a step: advance the level of each slot with steps left
@@ -1012,12 +1026,13 @@ static void* batch_stage_fn(int variant)
 
 cudaError_t atk_launch_batch_stage(int variant, const atk::StageArgs* tab, const int64_t* lvl, const int64_t* left,
                                    const int* win_slot, const int* win_idx, int nwin, int stage, int block,
-                                   size_t smem, cudaStream_t st)
+                                   size_t smem, int win_smem, cudaStream_t st)
 {
     void* fn = batch_stage_fn(variant);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    void* params[] = {(void*)&tab, (void*)&lvl, (void*)&left, (void*)&win_slot, (void*)&win_idx, (void*)&stage};
+    void* params[] = {(void*)&tab, (void*)&lvl, (void*)&left, (void*)&win_slot, (void*)&win_idx, (void*)&stage,
+                      (void*)&win_smem};
     return cudaLaunchKernel(fn, dim3(nwin), dim3(block), params, smem, st);
 }
 

@@ -95,21 +95,21 @@ BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4, "rns": 2 * 4 * 8 / 4, "deto
 # workload and path; the advection-diffusion kernels were captured at
 # N = 2^25 and are scaled by 4 for N = 2^27.
 TRAFFIC_PER_LAUNCH = {
-    ("rns-flame-n16384", "persistent"): 2.5508e+06,  # state and rings read once, writes stay in L2
-    ("rns-flame-n16777216", "stage"): 2 * (8.3059e+08 + 5.2064e+08),  # captured at N = 2^23, x2
-    ("rns-flame-n8388608", "stage"): 8.3059e+08 + 5.2064e+08,
-    ("detonation-n8388608", "stage"): 2.7444e+08 + 2.2632e+08,
-    ("detonation-n16777216", "stage"): 2 * (2.7444e+08 + 2.2632e+08),  # captured at N = 2^23, x2
-    ("advdiff-n134217728", "stage"): 4 * (8.7080e+08 + 5.1163e+08),
-    ("advdiff-n33554432", "stage"): 8.7080e+08 + 5.1163e+08,
-    ("advdiff-n134217728", "fused"): 4 * (4.6981e+08 + 3.0261e+08),  # one step: u^n, u^{n+1}, the ring
-    ("advdiff-n33554432", "fused"): 4.6981e+08 + 3.0261e+08,
+    ("rns-flame-n16384", "persistent"): 2.5498e+06,  # state and rings read once, writes stay in L2
+    ("rns-flame-n16777216", "stage"): 2 * (8.3059e+08 + 5.2106e+08),  # captured at N = 2^23, x2
+    ("rns-flame-n8388608", "stage"): 8.3059e+08 + 5.2106e+08,
+    ("detonation-n8388608", "stage"): 2.7215e+08 + 2.2599e+08,
+    ("detonation-n16777216", "stage"): 2 * (2.7215e+08 + 2.2599e+08),  # captured at N = 2^23, x2
+    ("advdiff-n134217728", "stage"): 4 * (8.7080e+08 + 5.1172e+08),
+    ("advdiff-n33554432", "stage"): 8.7080e+08 + 5.1172e+08,
+    ("advdiff-n134217728", "fused"): 4 * (4.6992e+08 + 3.0248e+08),  # one step: u^n, u^{n+1}, the ring
+    ("advdiff-n33554432", "fused"): 4.6992e+08 + 3.0248e+08,
     ("advdiff-n2048", "persistent"): 7.7824e+04,  # one-cluster launch: state and ring read once
-    ("advdiff-n16384", "fused"): 2.8826e+05,  # cooperative fused launch: state and ring read once
-    ("rns-flame-n16777216", "fused"): 2 * (2.6968e+08 + 3.1833e+08),  # tile-fused step, captured at N = 2^23, x2
-    ("rns-flame-n8388608", "fused"): 2.6968e+08 + 3.1833e+08,
-    ("detonation-n16777216", "fused"): 2 * (2.7680e+08 + 2.3259e+08),  # tile-fused step, captured at N = 2^23, x2
-    ("detonation-n8388608", "fused"): 2.7680e+08 + 2.3259e+08,
+    ("advdiff-n16384", "fused"): 2.8851e+05,  # cooperative fused launch: state and ring read once
+    ("rns-flame-n16777216", "fused"): 2 * (2.6972e+08 + 3.1805e+08),  # tile-fused step, captured at N = 2^23, x2
+    ("rns-flame-n8388608", "fused"): 2.6972e+08 + 3.1805e+08,
+    ("detonation-n16777216", "fused"): 2 * (2.7654e+08 + 2.3220e+08),  # tile-fused step, captured at N = 2^23, x2
+    ("detonation-n8388608", "fused"): 2.7654e+08 + 2.3220e+08,
 }
 
 
@@ -123,7 +123,7 @@ KERNEL_FILES = {
     "persistent": ("at_cluster.cu", "at_device.cuh", "at_persist.cu"),
     "fused": ("at_device.cuh", "at_fused.cu", "at_tilefused.cu"),
 }
-_SHA_STAGE = "9e209c621b8263f25ac493dda27d56d986924a2abab13ac4f13826633dcac031"
+_SHA_STAGE = "d9ce7fb1a7997fa1c2a43a41cfdec0fce9bbb234f818320743ebf155280daef4"
 _SHA_PERSISTENT = "c7025fbd5d9a2c338ff9781b172e21cc0d7cb7003b9d5540cf9f91aab8fab327"
 _SHA_FUSED = "04ba6ef7165741297e38504909e2d04bb138564b4638ba970f67d926bdbfa4b0"
 PROFILED_SHA256 = {

@@ -975,3 +975,43 @@ def test_all_zero_delay_trace_is_the_synchronous_run():
     s = oracle.Oracle(dict(pb, mode="sync"), u0)
     assert s.run(30) == 0
     assert np.array_equal(o.state(), s.state())
+
+
+# --------------------------------------------------------------------------
+# Homogeneous ignition under AT: the separable AT-error check.  Every stencil
+# annihilates a constant field, so the synchronous run is the 0-D ODE at every
+# point, and the start-up clamp makes every delay 0 through step q: the AT run
+# is the synchronous run bit for bit until then.  At the first step with a
+# real delay (k_eff = 1) only the extrapolated buffer values differ, by the
+# extrapolation error of the stage values' time series, O(dt^{q+1}); it enters
+# the update times dt, and over S stages it spreads by H points per stage.  So
+# the deviation is zero beyond S H points from a PE edge, nonzero at the edge,
+# and shrinks like dt^{q+2} (q = 3 for AT6: 2^5 per halving; a degree one
+# lower would give 2^4).
+# --------------------------------------------------------------------------
+def _homogeneous_rns(mode, dt, steps, n=128, B=32, T0=6.0, k_max=2):
+    prm = W.rns_prm()
+    rho = 1.0 / T0
+    init = W.rns_conserved(np.full(n, rho), np.zeros(n), np.full(n, T0), np.ones(n), prm)
+    pb = W.base_problem(pde="rns", order=6, rk="rk4", n=n, pe_size=B, dx=1.0, dt=dt, prm=prm, mode=mode,
+                        k_max=k_max, dist="table", prob=[0.0] * k_max + [1.0])
+    o = oracle.Oracle(pb, init)
+    assert o.run(steps) == 0
+    return o.state()
+
+
+def test_homogeneous_ignition_separates_the_at_error():
+    q, S, H, B, n = 3, 4, 3, 32, 128
+    # through step q every delay is clamped to 0: the synchronous run, bit for bit
+    assert np.array_equal(_homogeneous_rns("at", 0.08, q + 1), _homogeneous_rns("sync", 0.08, q + 1))
+    # the first step with a delay: only points within S H of a PE edge move
+    dev = np.abs(_homogeneous_rns("at", 0.08, q + 2) - _homogeneous_rns("sync", 0.08, q + 2)).max(axis=0)
+    j = np.arange(n) % B
+    dist = np.minimum(j, B - 1 - j)
+    assert (dev[dist >= S * H] == 0.0).all()
+    assert (dev[dist < H] > 1e-13).all()
+    # and the deviation shrinks like dt^(q+2)
+    devs = [np.abs(_homogeneous_rns("at", dt, q + 2) - _homogeneous_rns("sync", dt, q + 2)).max()
+            for dt in (0.08, 0.04, 0.02)]
+    for coarse, fine in zip(devs, devs[1:]):
+        assert 2 ** (q + 1.3) < coarse / fine < 2 ** (q + 2.5), devs

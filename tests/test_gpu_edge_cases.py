@@ -117,3 +117,32 @@ def test_every_delay_at_its_maximum(name):
                                 prob=[0.0, 0.0, 0.0, 0.0, 1.0])
     s, _ = parity(pb, u0, 60, what="all delays at k_max, %s" % name)
     assert (s.read_delays() == pb["k_max"]).all()
+
+
+@pytest.mark.parametrize("path", ["stage", "persistent"])
+def test_homogeneous_ignition_at_error_stays_at_pe_edges(path):
+    """The separable AT-error check on the GPU: a homogeneous igniting gas
+    under AT equals the synchronous run bit for bit while the start-up clamp
+    holds every delay at 0 (steps 0..q), then, at the first delayed step,
+    moves only within S H points of a PE edge; and it matches the oracle."""
+    from paper_2204_01133_gb300.api import Solver
+    prm = W.rns_prm()
+    n, B, T0, q, S, H = 128, 32, 6.0, 3, 4, 3
+    rho = 1.0 / T0
+    u0 = W.rns_conserved(np.full(n, rho), np.zeros(n), np.full(n, T0), np.ones(n), prm)
+
+    def pb(mode):
+        return W.base_problem(pde="rns", order=6, rk="rk4", n=n, pe_size=B, dx=1.0, dt=0.08, prm=prm, mode=mode,
+                              k_max=2, dist="table", prob=[0.0, 0.0, 1.0])
+    at, sync = Solver(pb("at"), u0, path=path), Solver(pb("sync"), u0, path=path)
+    at.run(q + 1)
+    sync.run(q + 1)
+    assert np.array_equal(at.read_state(), sync.read_state())
+    at.run(1)
+    sync.run(1)
+    dev = np.abs(at.read_state() - sync.read_state()).max(axis=0)
+    j = np.arange(n) % B
+    dist = np.minimum(j, B - 1 - j)
+    assert (dev[dist >= S * H] == 0.0).all()
+    assert (dev[dist < H] > 1e-13).all()
+    parity(pb("at"), u0, q + 2, what="homogeneous ignition AT, %s" % path)

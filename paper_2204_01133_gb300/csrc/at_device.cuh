@@ -326,41 +326,39 @@ struct Phys<EULER> {
     __device__ static void derive(const StageArgs& a, const double* Q, double* g)
     {
         const double u = Q[1] * at_rcp3(Q[0]);
+        const double uh = 0.5 * u;
         const double p = pressure(a, Q, u);
         g[0] = 0.5 * Q[1];
         g[1] = 0.5 * fma(Q[1], u, p);
-        g[2] = 0.5 * (u * (Q[2] + p));
-        g[3] = 0.5 * (Q[3] * u);
+        g[2] = uh * (Q[2] + p);  // = (u (E + p)) / 2 exactly
+        g[3] = Q[3] * uh;
         g[4] = Q[0];
         g[5] = Q[1];
         g[6] = Q[2];
         g[7] = Q[3];
     }
-    __device__ static double speed(const StageArgs& a, const double* Q)
-    {
-        const double rinv = at_rcp3(Q[0]);
-        const double u = Q[1] * rinv;
-        const double p = pressure(a, Q, u);
-        return fabs(u) + sqrt(a.prm[0] * p * rinv);
-    }
-    // derive() and speed() of one point at once (1/rho, u and p formed once,
-    // by the same operations), and with ARR the Arrhenius factor
-    // exp(-Ea rho / p) of the point's reaction source
+    // derive() and half the wave speed, (|u| + c) / 2, of one point at once
+    // (1/rho, u and p formed once, by the same operations), and with ARR the
+    // Arrhenius factor exp(-Ea rho / p) of the point's reaction source.
+    // Halving is exact, so g[2] = (u/2)(E + p), g[3] = rho Y (u/2) and the half
+    // speed |u/2| + sqrt(gamma p / (4 rho)) equal the halved products and the
+    // halved speed bit for bit (sqrt is correctly rounded).
     template <bool ARR>
-    __device__ static void derive_weno(const StageArgs& a, const double* Q, double* g, double& sp, double& arr)
+    __device__ static void derive_weno(const StageArgs& a, const double* Q, double* g, double& sph, double& arr)
     {
         const double rinv = at_rcp3(Q[0]);
         const double u = Q[1] * rinv;
+        const double uh = 0.5 * u;
         const double p = pressure(a, Q, u);
         g[0] = 0.5 * Q[1];
         g[1] = 0.5 * fma(Q[1], u, p);
-        g[2] = 0.5 * (u * (Q[2] + p));
-        g[3] = 0.5 * (Q[3] * u);
+        g[2] = uh * (Q[2] + p);
+        g[3] = Q[3] * uh;
         g[4] = Q[0];
         g[5] = Q[1];
         g[6] = Q[2];
         g[7] = Q[3];
-        sp = fabs(u) + sqrt(a.prm[0] * p * rinv);
+        sph = fabs(uh) + sqrt((0.25 * a.prm[0]) * p * rinv);
         if constexpr (ARR) arr = at_exp(-a.prm[2] * Q[0] * at_rcp3(p));
     }
 };
@@ -374,16 +372,15 @@ struct Phys<ADV_WENO> {
         g[0] = 0.5 * a.prm[0] * Q[0];
         g[1] = Q[0];
     }
-    __device__ static double speed(const StageArgs& a, const double*) { return fabs(a.prm[0]); }
     template <bool ARR>
-    __device__ static void derive_weno(const StageArgs& a, const double* Q, double* g, double& sp, double&)
+    __device__ static void derive_weno(const StageArgs& a, const double* Q, double* g, double& sph, double&)
     {
         derive(a, Q, g);
-        sp = speed(a, Q);
+        sph = 0.5 * fabs(a.prm[0]);  // half the wave speed
     }
 };
 
-// Inviscid Burgers, WENO form: g = [u^2 / 4, u] (C/2 with C = u^2/2); speed |u|.
+// Inviscid Burgers, WENO form: g = [u^2 / 4, u] (C/2 with C = u^2/2); wave speed |u|.
 template <>
 struct Phys<BURGERS> {
     static constexpr int NV = 1, ND = 2;
@@ -392,12 +389,11 @@ struct Phys<BURGERS> {
         g[0] = 0.5 * (0.5 * Q[0] * Q[0]);
         g[1] = Q[0];
     }
-    __device__ static double speed(const StageArgs&, const double* Q) { return fabs(Q[0]); }
     template <bool ARR>
-    __device__ static void derive_weno(const StageArgs& a, const double* Q, double* g, double& sp, double&)
+    __device__ static void derive_weno(const StageArgs& a, const double* Q, double* g, double& sph, double&)
     {
         derive(a, Q, g);
-        sp = speed(a, Q);
+        sph = 0.5 * fabs(Q[0]);  // half the wave speed |u|
     }
 };
 
@@ -459,8 +455,8 @@ __device__ __forceinline__ int64_t place_rank(const StageArgs& a)
 // WENO5-JS reconstruction at the right edge of f[2] from f[0..4]
 // (candidates of Eq. atRecon at k = 0, ideal weights {1/10, 3/5, 3/10},
 // indicators of Eq. betaS, weights of Eq. omg with power 2), taken from the
-// first differences a_k = f[k] - f[k-1] (k = 1..4) and f[2], and arranged
-// for few FP64 instructions without changing the mathematics:
+// first differences a_k = f[k] - f[k-1] (k = 1..4), and arranged for few
+// FP64 instructions without changing the mathematics:
 //  * the second differences s_i (centred on f[i+1]) are s_0 = a_2 - a_1,
 //    s_1 = a_3 - a_2, s_2 = a_4 - a_3, and the first-difference terms of the
 //    indicators r_0 = f0 - 4 f1 + 3 f2 = s_0 + 2 a_2, r_1 = f1 - f3 =
@@ -473,18 +469,21 @@ __device__ __forceinline__ int64_t place_rank(const StageArgs& a)
 //    p_0 - p_1 = (s_0 - s_1) / 3 and p_2 - p_1 = (s_1 - s_2) / 6, so
 //    sum omega_i p_i = p_1 + omega_0 (p_0 - p_1) + omega_2 (p_2 - p_1);
 //  * alpha_i ~ gamma_i / D_i^2 times the common factor D_0^2 D_1^2 D_2^2, and
-//    numerator and denominator scaled by 10 (ideal weights 1 : 6 : 3):
-//      num = E_1 (E_2 (s_0 - s_1) / 3 + E_0 (s_1 - s_2) / 2),
-//      den = E_1 (E_2 + 3 E_0) + 6 E_0 E_2,  E_i = D_i^2,
-//    so the reconstruction is p_1 + num / den.
-// The parts (num, den, p_1) are returned, so that the two reconstructions of
-// an edge share one reciprocal.  eps4 = 4 eps.
+//    numerator and denominator scaled by 10 (ideal weights 1 : 6 : 3); with
+//    E_i = D_i^2, A = 3 E_0 and B = 2 E_2,
+//      num = E_1 (B (s_0 - s_1) + A (s_1 - s_2))   (6 times the corrections'
+//            numerator E_1 (E_2 (s_0 - s_1) / 3 + E_0 (s_1 - s_2) / 2)),
+//      den = E_1 (A + E_2) + A B                   (= E_1 (3 E_0 + E_2) + 6 E_0 E_2),
+//    so the reconstruction is p_1 + num / (6 den).
+// Returned: num, den and s_1 (the caller forms p_1 of both signs at once and
+// shares one reciprocal between the two reconstructions of an edge).
+// eps4 = 4 eps.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void weno5d(double a1, double a2, double a3, double a4, double f2, double eps4,
-                                       double& num, double& den, double& p1)
+__device__ __forceinline__ void weno5d(double a1, double a2, double a3, double a4, double eps4, double& num,
+                                       double& den, double& s1)
 {
     const double s0 = a2 - a1;
-    const double s1 = a3 - a2;
+    s1 = a3 - a2;
     const double s2 = a4 - a3;
     const double r0 = fma(2.0, a2, s0);   // f0 - 4 f1 + 3 f2
     const double r1 = a2 + a3;            // f3 - f1
@@ -493,35 +492,41 @@ __device__ __forceinline__ void weno5d(double a1, double a2, double a3, double a
     const double d1 = fma((13.0 / 3.0) * s1, s1, fma(r1, r1, eps4));
     const double d2 = fma((13.0 / 3.0) * s2, s2, fma(r2, r2, eps4));
     const double e0 = d0 * d0, e1 = d1 * d1, e2 = d2 * d2;
-    num = e1 * fma(e2, (s0 - s1) * (1.0 / 3.0), e0 * ((s1 - s2) * 0.5));
-    den = fma(e1, fma(3.0, e0, e2), 6.0 * (e0 * e2));
-    p1 = fma(1.0 / 6.0, a2, fma(1.0 / 3.0, a3, f2));  // (-f1 + 5 f2 + 2 f3) / 6
+    const double A = 3.0 * e0, B = 2.0 * e2;
+    num = e1 * fma(B, s0 - s1, A * (s1 - s2));
+    den = fma(e1, A + e2, A * B);
 }
 
 // The LLF-split WENO5 flux at the edge left of column c of a row: the
 // reconstruction of f+ = C + hl Q from columns c-3..c+1 plus that of
 // f- = C - hl Q from columns c+2..c-2 (mirrored), hl half the edge's wave
 // speed (Eq. Csplit).  The split fluxes' first differences are those of C
-// and Q combined, dC(j) +- hl dQ(j) with dC(j) = C[j] - C[j-1], so they come
-// from the rows' own first differences, formed once per column and shared
-// by every edge and both signs; dC(j), dQ(j) are callables returning them.
-// The flux p+ + p- + num+ / den+ + num- / den- is formed as
-// p+ + p- + (num+ den- + num- den+) / (den+ den-), one reciprocal for both
-// (den is at least 6 (4 eps)^4 ~ 1.5e-21 with eps = 1e-6 and grows with the
-// fourth power of the differences, so the product stays far inside the
-// double range for the states these PDEs carry).
+// and Q combined, P(j) = dC(j) + hl dQ(j) and M(j) = hl dQ(j) - dC(j) with
+// dC(j) = C[j] - C[j-1], so they come from the rows' own first differences,
+// formed once per column and shared by every edge and both signs; dC(j),
+// dQ(j) are callables returning them.
+// The two middle candidates add up to a centred value: p+ = f+(c-1) +
+// P(c-1)/6 + P(c)/3 and p- = f-(c) + M(c+1)/6 + M(c)/3, and with
+// f+(c-1) + f-(c) = C[c-1] + C[c] - hl dQ(c) and P(c) + M(c) = 2 hl dQ(c),
+//   p+ + p- = C[c-1] + C[c] + (P(c-1) - P(c) + M(c+1) - M(c)) / 6
+//           = C[c-1] + C[c] - (s1+ + s1-) / 6,
+// s1+ = P(c) - P(c-1) and s1- = M(c) - M(c+1) being the two
+// reconstructions' middle second differences.  The corrections
+// num+ / (6 den+) + num- / (6 den-) share one reciprocal,
+// (num+ den- + num- den+) / (6 den+ den-), and the 1/6 of both parts is
+// applied once (den is at least 6 (4 eps)^4 ~ 1.5e-21 with eps = 1e-6 and
+// grows with the fourth power of the differences, so the product stays far
+// inside the double range for the states these PDEs carry).
 template <class DC, class DQ>
-__device__ __forceinline__ double weno_flux(const double* C, const double* Q, DC dC, DQ dQ, int c, double hl,
-                                            double eps4)
+__device__ __forceinline__ double weno_flux(const double* C, DC dC, DQ dQ, int c, double hl, double eps4)
 {
-    double np, dp, pp, nm, dm, pm;
+    double np, dp, s1p, nm, dm, s1m;
     weno5d(fma(hl, dQ(c - 2), dC(c - 2)), fma(hl, dQ(c - 1), dC(c - 1)), fma(hl, dQ(c), dC(c)),
-           fma(hl, dQ(c + 1), dC(c + 1)), fma(hl, Q[c - 1], C[c - 1]), eps4, np, dp, pp);
-    // mirrored: a_k of f- is -(dC - hl dQ) at columns c+2, c+1, c, c-1
+           fma(hl, dQ(c + 1), dC(c + 1)), eps4, np, dp, s1p);
+    // mirrored: a_k of f- is M at columns c+2, c+1, c, c-1
     weno5d(fma(hl, dQ(c + 2), -dC(c + 2)), fma(hl, dQ(c + 1), -dC(c + 1)), fma(hl, dQ(c), -dC(c)),
-           fma(hl, dQ(c - 1), -dC(c - 1)), fma(-hl, Q[c], C[c]), eps4, nm, dm, pm);
-    // both corrections over one reciprocal
-    return fma(fma(np, dm, nm * dp), at_rcp3(dp * dm), pp + pm);
+           fma(hl, dQ(c - 1), -dC(c - 1)), eps4, nm, dm, s1m);
+    return fma(1.0 / 6.0, fma(fma(np, dm, nm * dp), at_rcp3(dp * dm), -(s1p + s1m)), C[c - 1] + C[c]);
 }
 
 // ---------------------------------------------------------------------------

@@ -93,7 +93,7 @@ __device__ __forceinline__ void fill_window(const StageArgs& a, const Cx& cx, do
 #pragma unroll
                 for (int v = 0; v < NV; ++v) Q[v] = src[v];
                 if constexpr (WENO) {
-                    if (l == 0) {  // the wave speed at level n-k, not extrapolated
+                    if (l == 0) {  // the (half) wave speed at level n-k, not extrapolated
                         double sp, unused;
                         P::template derive_weno<false>(a, Q, g, sp, unused);
                         SP[side == 0 ? h : W2 - R0 + h] = sp;
@@ -415,7 +415,7 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
     fill_window<PDE, true>(a, cx, G, SP, HS, pe, chunk, t0, W2, threadIdx.x, blockDim.x, ARR);
     __syncthreads();
     for (int e = threadIdx.x; e < E; e += blockDim.x)
-        LAM[e] = 0.5 * fmax(SP[e - 1 + H], SP[e + H]);  // half the edge's local wave speed
+        LAM[e] = fmax(SP[e - 1 + H], SP[e + H]);  // half the edge's local wave speed (SP: half speeds)
     for (int it = threadIdx.x; it < ND * (W2 - 1); it += blockDim.x) {
         const int d = it / (W2 - 1);
         const int j = 1 + it - d * (W2 - 1);
@@ -428,7 +428,7 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
         const int e = it - v * E;
         const double* dC = DG + v * W2;
         const double* dQ = DG + (NV + v) * W2;
-        FL[it] = weno_flux(G + v * W2, G + (NV + v) * W2, [&](int j) { return dC[j]; },
+        FL[it] = weno_flux(G + v * W2, [&](int j) { return dC[j]; },
                            [&](int j) { return dQ[j]; }, e + H, LAM[e], eps4);
     }
     __syncthreads();
@@ -509,7 +509,7 @@ __device__ __forceinline__ void weno_interp_window(const StageArgs& a, const Cx&
     fill_window<PDE, true>(a, cx, G, SP, HS, pe, chunk, t0, W2, threadIdx.x, blockDim.x, ARR);
     __syncthreads();
     for (int t = threadIdx.x; t < E; t += blockDim.x)
-        LAM[t] = 0.5 * fmax(SP[t + 2], SP[t + 3]);
+        LAM[t] = fmax(SP[t + 2], SP[t + 3]);  // SP holds half speeds
     __syncthreads();
     const double eps4 = 4.0 * ((PDE == EULER) ? a.prm[4] : a.prm[1]);
     const int items = NV * 2 * E;

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256) tile_fused(const StageArgs a, const doubl
 // Shared memory (doubles), E = Tw + 2 D; row 1 has RC = E + 2 H columns,
 // rows 0 and 2 (strips) RS = D + 2 H; a quantity of row r sits at the row's
 // base with the row's stride:
-//   G [ND] per row, SP, ARR, LAM one per row   derived, wave speed,
+//   G [ND] per row, SP, ARR, LAM one per row   derived, half wave speed,
 //                                             Arrhenius factor, edge speed;
 //                                             the derived quantities NV..2NV-1
 //                                             are the state itself, so the
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
                 if (w == 1) log_delay(a, n, s, pe, side, k);
             }
         }
-        // own points where X is known: derived quantities, wave speed, Arrhenius factor
+        // own points where X is known: derived quantities, half wave speed, Arrhenius factor
         for (int i = threadIdx.x + lo; i < hi; i += blockDim.x) {
             const int r = row_of(i), c = col_of(i);
             double Q[NV], g[ND], sp, arr;
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
             const int r = t < ne[0] ? 0 : (t < ne[0] + ne[1] ? 1 : 2);
             const int e = t - (r == 0 ? 0 : (r == 1 ? ne[0] : ne[0] + ne[1]));
             const int c = H + ka[r] + e - row_lo(r);  // column of the point right of the edge
-            LAM[roff(r) + c] = 0.5 * fmax(SP[roff(r) + c - 1], SP[roff(r) + c]);
+            LAM[roff(r) + c] = fmax(SP[roff(r) + c - 1], SP[roff(r) + c]);  // SP holds half speeds
         }
         __syncthreads();
         const double eps4 = 4.0 * ((PDE == EULER) ? a.prm[4] : a.prm[1]);
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
             // the rows' first differences formed where they are used: the same
             // operations, so the same values, as the per-stage kernels' stored ones
             REC[NV * roff(r) + v * rstride(r) + c] =
-                weno_flux(Cr, Qr, [&](int j) { return Cr[j] - Cr[j - 1]; }, [&](int j) { return Qr[j] - Qr[j - 1]; }, c,
+                weno_flux(Cr, [&](int j) { return Cr[j] - Cr[j - 1]; }, [&](int j) { return Qr[j] - Qr[j - 1]; }, c,
                           LAM[roff(r) + c], eps4);
         }
         __syncthreads();

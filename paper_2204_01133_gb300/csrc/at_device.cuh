@@ -460,11 +460,13 @@ __device__ __forceinline__ int64_t place_rank(const StageArgs& a)
 //  * the second differences s_i (centred on f[i+1]) are s_0 = a_2 - a_1,
 //    s_1 = a_3 - a_2, s_2 = a_4 - a_3, and the first-difference terms of the
 //    indicators r_0 = f0 - 4 f1 + 3 f2 = s_0 + 2 a_2, r_1 = f1 - f3 =
-//    -(a_2 + a_3), r_2 = 3 f2 - 4 f3 + f4 = s_2 - 2 a_3; then
-//    beta_i = (13 s_i^2 + 3 r_i^2) / 12, so D_i = 4 (eps + beta_i) =
-//    (13/3) s_i^2 + r_i^2 + 4 eps; the weights omega_i = alpha_i / sum alpha
-//    do not change when every eps + beta_i is scaled by the same 4;
-//  * the middle candidate p_1 = (-f1 + 5 f2 + 2 f3) / 6 = f2 + a_2/6 + a_3/3,
+//    -(a_2 + a_3) = -(s_1 + 2 a_2), r_2 = 3 f2 - 4 f3 + f4 = s_2 - 2 a_3;
+//    then beta_i = (13 s_i^2 + 3 r_i^2) / 12, and with r_i expanded
+//      D_0 = eps + beta_0 = s_0 ((4/3) s_0 + a_2) + a_2^2 + eps,
+//      D_1 = eps + beta_1 = s_1 ((4/3) s_1 + a_2) + a_2^2 + eps,
+//      D_2 = eps + beta_2 = s_2 ((4/3) s_2 - a_3) + a_3^2 + eps
+//    (each a positive definite form in (s_i, a), so the sum does not
+//    cancel), D_0 and D_1 sharing a_2^2 + eps;//  * the middle candidate p_1 = (-f1 + 5 f2 + 2 f3) / 6 = f2 + a_2/6 + a_3/3,
 //    and the others differ from it by third differences,
 //    p_0 - p_1 = (s_0 - s_1) / 3 and p_2 - p_1 = (s_1 - s_2) / 6, so
 //    sum omega_i p_i = p_1 + omega_0 (p_0 - p_1) + omega_2 (p_2 - p_1);
@@ -477,20 +479,17 @@ __device__ __forceinline__ int64_t place_rank(const StageArgs& a)
 //    so the reconstruction is p_1 + num / (6 den).
 // Returned: num, den and s_1 (the caller forms p_1 of both signs at once and
 // shares one reciprocal between the two reconstructions of an edge).
-// eps4 = 4 eps.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void weno5d(double a1, double a2, double a3, double a4, double eps4, double& num,
+__device__ __forceinline__ void weno5d(double a1, double a2, double a3, double a4, double eps, double& num,
                                        double& den, double& s1)
 {
     const double s0 = a2 - a1;
     s1 = a3 - a2;
     const double s2 = a4 - a3;
-    const double r0 = fma(2.0, a2, s0);   // f0 - 4 f1 + 3 f2
-    const double r1 = a2 + a3;            // f3 - f1
-    const double r2 = fma(-2.0, a3, s2);  // 3 f2 - 4 f3 + f4
-    const double d0 = fma((13.0 / 3.0) * s0, s0, fma(r0, r0, eps4));
-    const double d1 = fma((13.0 / 3.0) * s1, s1, fma(r1, r1, eps4));
-    const double d2 = fma((13.0 / 3.0) * s2, s2, fma(r2, r2, eps4));
+    const double t2 = fma(a2, a2, eps);
+    const double d0 = fma(s0, fma(4.0 / 3.0, s0, a2), t2);
+    const double d1 = fma(s1, fma(4.0 / 3.0, s1, a2), t2);
+    const double d2 = fma(s2, fma(4.0 / 3.0, s2, -a3), fma(a3, a3, eps));
     const double e0 = d0 * d0, e1 = d1 * d1, e2 = d2 * d2;
     const double A = 3.0 * e0, B = 2.0 * e2;
     num = e1 * fma(B, s0 - s1, A * (s1 - s2));
@@ -514,18 +513,18 @@ __device__ __forceinline__ void weno5d(double a1, double a2, double a3, double a
 // reconstructions' middle second differences.  The corrections
 // num+ / (6 den+) + num- / (6 den-) share one reciprocal,
 // (num+ den- + num- den+) / (6 den+ den-), and the 1/6 of both parts is
-// applied once (den is at least 6 (4 eps)^4 ~ 1.5e-21 with eps = 1e-6 and
-// grows with the fourth power of the differences, so the product stays far
-// inside the double range for the states these PDEs carry).
+// applied once (den is at least 10 eps^4 ~ 1e-23 with eps = 1e-6 and grows
+// with the fourth power of the differences, so the product stays far inside
+// the double range for the states these PDEs carry).
 template <class DC, class DQ>
-__device__ __forceinline__ double weno_flux(const double* C, DC dC, DQ dQ, int c, double hl, double eps4)
+__device__ __forceinline__ double weno_flux(const double* C, DC dC, DQ dQ, int c, double hl, double eps)
 {
     double np, dp, s1p, nm, dm, s1m;
     weno5d(fma(hl, dQ(c - 2), dC(c - 2)), fma(hl, dQ(c - 1), dC(c - 1)), fma(hl, dQ(c), dC(c)),
-           fma(hl, dQ(c + 1), dC(c + 1)), eps4, np, dp, s1p);
+           fma(hl, dQ(c + 1), dC(c + 1)), eps, np, dp, s1p);
     // mirrored: a_k of f- is M at columns c+2, c+1, c, c-1
     weno5d(fma(hl, dQ(c + 2), -dC(c + 2)), fma(hl, dQ(c + 1), -dC(c + 1)), fma(hl, dQ(c), -dC(c)),
-           fma(hl, dQ(c - 1), -dC(c - 1)), eps4, nm, dm, s1m);
+           fma(hl, dQ(c - 1), -dC(c - 1)), eps, nm, dm, s1m);
     return fma(1.0 / 6.0, fma(fma(np, dm, nm * dp), at_rcp3(dp * dm), -(s1p + s1m)), C[c - 1] + C[c]);
 }
 

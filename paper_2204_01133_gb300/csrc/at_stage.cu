@@ -422,14 +422,14 @@ __device__ __forceinline__ void weno_window(const StageArgs& a, const Cx& cx, in
         DG[d * W2 + j] = G[d * W2 + j] - G[d * W2 + j - 1];
     }
     __syncthreads();
-    const double eps4 = 4.0 * ((PDE == EULER) ? a.prm[4] : a.prm[1]);
+    const double eps = (PDE == EULER) ? a.prm[4] : a.prm[1];
     for (int it = threadIdx.x; it < NV * E; it += blockDim.x) {
         const int v = it / E;
         const int e = it - v * E;
         const double* dC = DG + v * W2;
         const double* dQ = DG + (NV + v) * W2;
         FL[it] = weno_flux(G + v * W2, [&](int j) { return dC[j]; },
-                           [&](int j) { return dQ[j]; }, e + H, LAM[e], eps4);
+                           [&](int j) { return dQ[j]; }, e + H, LAM[e], eps);
     }
     __syncthreads();
     const double rdx = a.k0;  // 1 / dx

@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
             LAM[roff(r) + c] = fmax(SP[roff(r) + c - 1], SP[roff(r) + c]);  // SP holds half speeds
         }
         __syncthreads();
-        const double eps4 = 4.0 * ((PDE == EULER) ? a.prm[4] : a.prm[1]);
+        const double eps = (PDE == EULER) ? a.prm[4] : a.prm[1];
         const int nrec = NV * (ne[0] + ne[1] + ne[2]);
         for (int it = threadIdx.x; it < nrec; it += blockDim.x) {
             const int t = it % (ne[0] + ne[1] + ne[2]);
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(256) tile_fused_weno(const StageArgs a, const 
             // operations, so the same values, as the per-stage kernels' stored ones
             REC[NV * roff(r) + v * rstride(r) + c] =
                 weno_flux(Cr, [&](int j) { return Cr[j] - Cr[j - 1]; }, [&](int j) { return Qr[j] - Qr[j - 1]; }, c,
-                          LAM[roff(r) + c], eps4);
+                          LAM[roff(r) + c], eps);
         }
         __syncthreads();
         const double rdx = a.k0;

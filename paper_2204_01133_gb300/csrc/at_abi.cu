@@ -330,6 +330,16 @@ atk::StageArgs build_args(const at_problem* pb, const at_delays* dl, const Layou
             a.k1 = 2.0 / 3.0 * mu;
             a.k2 = lam;
             a.k3 = lam / (cp * Le);
+            // the diffusion rows carry u, the energy term over lambda and Y; the
+            // constants go into the taps (without viscosity every row term is 0)
+            const bool visc = a.k2 != 0.0;
+            for (int o = 0; o <= 2 * L.H; ++o) {
+                a.c2v[0][o] = a.c2[o] * a.k0;
+                a.c2v[1][o] = visc ? a.c2[o] * a.k2 : 0.0;
+                a.c2v[2][o] = a.c2[o] * a.k3;
+            }
+            a.kd1 = visc ? a.k1 / a.k2 : 0.0;
+            a.kd3 = visc ? pb->prm[6] * a.k3 / a.k2 : 0.0;
         }
     } else {
         a.k0 = 1.0 / dx;

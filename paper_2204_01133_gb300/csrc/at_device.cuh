@@ -47,6 +47,11 @@ struct StageArgs {
     double cm[2 * AT_HMAX + 1];               // merged advection-diffusion taps
     double prm[16];                           // physics constants (see at.h)
     double k0, k1, k2, k3;                    // derived physics constants
+    // reacting flow: the diffusion rows are u, the energy term over lambda and
+    // Y, with the constants in the taps: c2v[v-1][m] = c2[m] times (4/3) mu,
+    // lambda, lambda / (cp Le) for v = 1, 2, 3; kd1 = k1 / k2, kd3 = qc k3 / k2
+    double c2v[3][2 * AT_HMAX + 1];
+    double kd1, kd3;
     // persistent path only
     int64_t* done;       // per PE: stages completed, as the index n*S + s + 1 [P]
     double* gring;       // derived quantities of the edge windows [R][S][P][2][H][ND]
@@ -260,8 +265,9 @@ struct Phys<ADVDIFF> {
 };
 
 // Reacting Navier-Stokes: g = [rho u, rho u^2 + p, u (rho E + p), rho u Y,
-// (4/3) mu u, (2/3) mu u^2 + lam T + q_c rhoD Y, rhoD Y, T].
-// k0 = (4/3) mu, k1 = (2/3) mu, k2 = lam, k3 = rhoD.
+// u, ((2/3) mu u^2 + lam T + q_c rhoD Y) / lam, Y, T]; the diffusion rows
+// 4..6 are differentiated with the taps c2v, which carry their constants
+// (4/3) mu, lam and rhoD.  k0 = (4/3) mu, k1 = (2/3) mu, k2 = lam, k3 = rhoD.
 template <>
 struct Phys<RNS> {
     static constexpr int NV = 4, ND = 8;
@@ -277,9 +283,9 @@ struct Phys<RNS> {
         g[1] = fma(Q[1], u, p);
         g[2] = u * (Q[2] + p);
         g[3] = Q[3] * u;
-        g[4] = a.k0 * u;
-        g[5] = fma(a.k1 * u, u, fma(a.k2, T, qc * a.k3 * Y));
-        g[6] = a.k3 * Y;
+        g[4] = u;                                      // times (4/3) mu in the taps
+        g[5] = fma(a.kd1 * u, u, fma(a.kd3, Y, T));    // (k1 u^2 + k2 T + qc k3 Y) / k2; times k2 in the taps
+        g[6] = Y;                                      // times k3 in the taps
         g[7] = T;
     }
     // the temperature exactly as derive() forms it (same operations, same rounding)

@@ -77,7 +77,7 @@ __device__ __forceinline__ double point_update(const StageArgs& a, int s, int v,
         if (v > 0) {
             const double* D = G + (3 + v) * W2;
 #pragma unroll
-            for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[c + o], K);
+            for (int o = -H; o <= H; ++o) K = fma(a.c2v[v - 1][o + H], D[c + o], K);
         }
         if (v == 3) K = fma(-a.prm[4] * x, E[jl], K);
     }

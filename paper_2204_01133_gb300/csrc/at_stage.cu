@@ -305,9 +305,9 @@ __device__ __forceinline__ void central_window(const StageArgs& a, const Cx& cx,
             for (int o = -H; o <= H; ++o)
                 if (o != 0) K = fma(a.c1[o + H], F[c + o], K);
             if (v > 0) {
-                const double* D = G + (3 + v) * W2;  // (4/3) mu u | energy diffusion | rhoD Y
+                const double* D = G + (3 + v) * W2;  // u | energy diffusion / lambda | Y (constants in the taps)
 #pragma unroll
-                for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[c + o], K);
+                for (int o = -H; o <= H; ++o) K = fma(a.c2v[v - 1][o + H], D[c + o], K);
             }
             if (v == 3) K = fma(-a.prm[4] * x, at_exp(-a.prm[5] * at_rcp3(G[7 * W2 + c])), K);
         }
@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(128) ring_recompute(const StageArgs a, const d
                     if (v > 0) {
                         const double* D = G + (3 + v) * W;
 #pragma unroll
-                        for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], D[lane + o], K);
+                        for (int o = -H; o <= H; ++o) K = fma(a.c2v[v - 1][o + H], D[lane + o], K);
                     }
                     if (v == 3) K = fma(-a.prm[4] * x[v], at_exp(-a.prm[5] * at_rcp3(G[7 * W + lane])), K);
                 }

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256) tile_fused(const StageArgs a, const doubl
                 if (v > 0) {
                     const double* Dq = Gr + (3 + v) * RW;
 #pragma unroll
-                    for (int o = -H; o <= H; ++o) K = fma(a.c2[o + H], Dq[c + o], K);
+                    for (int o = -H; o <= H; ++o) K = fma(a.c2v[v - 1][o + H], Dq[c + o], K);
                 }
                 if (v == 3) K = fma(-a.prm[4] * x, at_exp(-a.prm[5] * at_rcp3(Gr[7 * RW + c])), K);
             }

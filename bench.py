@@ -66,13 +66,13 @@ NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal, at 2070 M
 # instruction sequences of exp and the reciprocals, so achieved / peak is the
 # share of the FP64 roof the kernel's own arithmetic uses.
 FLOPS_PER_POINT_STAGE = {
-    ("rns", "stage"): 170.3,         # central6 + AT6, 4 variables (RK4 stage 1 counted)
-    ("rns", "persistent"): 170.3,    # same work, all K steps of one launch
+    ("rns", "stage"): 165.7,         # central6 + AT6, 4 variables (RK4 stage 1 counted)
+    ("rns", "persistent"): 165.8,    # same work, all K steps of one launch
     ("detonation", "stage"): 500.3,  # WENO5 + AT-WENO5, 8 reconstructions per edge (RK3 stage 0)
     ("advdiff", "stage"): 13.56,     # 5-tap merged stencil + RK4 update, mean of the 4 stages
     ("advdiff", "persistent"): 13.56,
     ("advdiff", "fused"): 13.56,     # the method's work only (13.65 as executed, with the recomputed edge points)
-    ("rns", "fused"): 170.3,         # the method's work only (the tile-fused kernel also recomputes the strips)
+    ("rns", "fused"): 165.7,         # the method's work only (the tile-fused kernel also recomputes the strips)
     ("detonation", "fused"): 500.3,  # likewise: the per-stage kernel's count
 }
 # The method's own FP64 work per point per stage, by operation count (a
@@ -95,21 +95,21 @@ BYTES_PER_POINT_STAGE_FUSED = {"advdiff": 2 * 8 / 4, "rns": 2 * 4 * 8 / 4, "deto
 # workload and path; the advection-diffusion kernels were captured at
 # N = 2^25 and are scaled by 4 for N = 2^27.
 TRAFFIC_PER_LAUNCH = {
-    ("rns-flame-n16384", "persistent"): 2.5500e+06,  # state and rings read once, writes stay in L2
-    ("rns-flame-n16777216", "stage"): 2 * (8.3167e+08 + 5.2060e+08),  # captured at N = 2^23, x2
-    ("rns-flame-n8388608", "stage"): 8.3167e+08 + 5.2060e+08,
-    ("detonation-n8388608", "stage"): 2.7207e+08 + 2.2566e+08,
-    ("detonation-n16777216", "stage"): 2 * (2.7207e+08 + 2.2566e+08),  # captured at N = 2^23, x2
-    ("advdiff-n134217728", "stage"): 4 * (8.7082e+08 + 5.1210e+08),
-    ("advdiff-n33554432", "stage"): 8.7082e+08 + 5.1210e+08,
-    ("advdiff-n134217728", "fused"): 4 * (4.6999e+08 + 3.0204e+08),  # one step: u^n, u^{n+1}, the ring
-    ("advdiff-n33554432", "fused"): 4.6999e+08 + 3.0204e+08,
-    ("advdiff-n2048", "persistent"): 7.8080e+04,  # one-cluster launch: state and ring read once
-    ("advdiff-n16384", "fused"): 2.8954e+05,  # cooperative fused launch: state and ring read once
-    ("rns-flame-n16777216", "fused"): 2 * (2.6869e+08 + 3.1820e+08),  # tile-fused step, captured at N = 2^23, x2
-    ("rns-flame-n8388608", "fused"): 2.6869e+08 + 3.1820e+08,
-    ("detonation-n16777216", "fused"): 2 * (2.7746e+08 + 2.3309e+08),  # tile-fused step, captured at N = 2^23, x2
-    ("detonation-n8388608", "fused"): 2.7746e+08 + 2.3309e+08,
+    ("rns-flame-n16384", "persistent"): 2.5541e+06,  # state and rings read once, writes stay in L2
+    ("rns-flame-n16777216", "stage"): 2 * (8.3054e+08 + 5.2048e+08),  # captured at N = 2^23, x2
+    ("rns-flame-n8388608", "stage"): 8.3054e+08 + 5.2048e+08,
+    ("detonation-n8388608", "stage"): 2.7371e+08 + 2.2617e+08,
+    ("detonation-n16777216", "stage"): 2 * (2.7371e+08 + 2.2617e+08),  # captured at N = 2^23, x2
+    ("advdiff-n134217728", "stage"): 4 * (8.7076e+08 + 5.1195e+08),
+    ("advdiff-n33554432", "stage"): 8.7076e+08 + 5.1195e+08,
+    ("advdiff-n134217728", "fused"): 4 * (4.6988e+08 + 3.0293e+08),  # one step: u^n, u^{n+1}, the ring
+    ("advdiff-n33554432", "fused"): 4.6988e+08 + 3.0293e+08,
+    ("advdiff-n2048", "persistent"): 8.0384e+04,  # one-cluster launch: state and ring read once
+    ("advdiff-n16384", "fused"): 2.8877e+05,  # cooperative fused launch: state and ring read once
+    ("rns-flame-n16777216", "fused"): 2 * (2.6860e+08 + 3.1804e+08),  # tile-fused step, captured at N = 2^23, x2
+    ("rns-flame-n8388608", "fused"): 2.6860e+08 + 3.1804e+08,
+    ("detonation-n16777216", "fused"): 2 * (2.7574e+08 + 2.3274e+08),  # tile-fused step, captured at N = 2^23, x2
+    ("detonation-n8388608", "fused"): 2.7574e+08 + 2.3274e+08,
 }
 
 
@@ -123,9 +123,9 @@ KERNEL_FILES = {
     "persistent": ("at_cluster.cu", "at_device.cuh", "at_persist.cu"),
     "fused": ("at_device.cuh", "at_fused.cu", "at_tilefused.cu"),
 }
-_SHA_STAGE = "2587d78824f0c55f275813891ac11990433ae4ed556bf40d85673135b37bad7a"
-_SHA_PERSISTENT = "962c891f305b67aee7a64ee113a5c495bf5b20d95cc6dfcb3f92fc4a9a2d4e84"
-_SHA_FUSED = "5e34a5b978ad77f838401038630fb61919f6306895065451669bf5e91f1ea1be"
+_SHA_STAGE = "0cecc1445fec100af6a8261ff949636d13abda82401f91c538bf46eea741a1e2"
+_SHA_PERSISTENT = "b9e03fe76cc5c2182917044ff8965c8a015a4d4ab02a7bc7eaf4e2134e28dab4"
+_SHA_FUSED = "ec36d6c3395c55e85546f641189d941abc7c206c5373b137cce2035fad616f1a"
 PROFILED_SHA256 = {
     ("detonation-n16777216", "stage"): _SHA_STAGE,
     ("detonation-n8388608", "stage"): _SHA_STAGE,

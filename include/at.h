@@ -384,9 +384,10 @@ int at_batch_destroy(at_batch* b);
  * status word) lives in one file-scope device array of
  * AT_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
  * the process exits.  Problems whose at_workspace_bytes() exceeds it are
- * rejected with AT_ENOMEM before anything is enqueued.  The first call on a
- * device looks the array's device address up (cudaGetSymbolAddress), so make
- * that first call before any stream capture.  The address is kept for the
+ * rejected with AT_ENOMEM before anything is enqueued.  The call ends by
+ * synchronising its stream, as at_run does, so it cannot be made inside a
+ * stream capture.  The first call on a device looks the array's device
+ * address up (cudaGetSymbolAddress).  The address is kept for the
  * life of the process: after cudaDeviceReset on a device the kept address is
  * stale, so do not call at_run_noalloc on that device again in that process.
  * Each call clears the parts of
